@@ -1,0 +1,577 @@
+/*
+ * CPU oracle for the Barnes-Hut potential on an octree AMR mesh.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path links,
+ * loads or calls this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA library: it is a plain, slow, separately written statement of what the
+ * method computes, in FP64.
+ *
+ * What it computes (paper = Lukat & Banerjee, "A GPU accelerated Barnes-Hut
+ * tree code for FLASH4"):
+ *   - The octree (Sec. 2; Sec. 3.2.2): one cube holds the whole box and is
+ *     split recursively into 8 sub-cubes until every sub-cube holds one item.
+ *     The items are the AMR cells (footnote in Sec. 2: cells are the
+ *     "particles"); because the leaf blocks tile the box, the recursion meets
+ *     every leaf block as a node and continues inside it down to single cells
+ *     (the FLASH tree solver's "extension of the AMR mesh tree down to the
+ *     individual cells", Sec. 1).  Children are kept in octant order
+ *     o = ox + 2*oy + 4*oz.
+ *   - Node moments (Sec. 3.2.3, Eq. 5): M = sum of the children's masses,
+ *     R = (1/M) sum m_i r_i over the children in octant order, and delta =
+ *     |R - geometric centre| (Sec. 2, Fig. opening_angles).  Leaf mass is
+ *     rho * cell volume, leaf position the cell centre.
+ *   - The walk (Sec. 2, Eqs. 3-4; Sec. 3.3): from the root, a node is
+ *     accepted for target t when d > l/theta + delta (d = |r_t - R|, l = node
+ *     side) and contributes -G M / d; otherwise its 8 children are visited.
+ *     A leaf cell other than t always contributes -G m / d.
+ *   - Direct sum (Eq. 2) without the printed factor 1/2 (that factor belongs
+ *     to the total-energy sum, not to the potential at one cell).
+ *   - Paper mode (Sec. 3.3): 32 neighbouring cells (a 4x4x2 brick of a block)
+ *     walk together and a node is accepted only if all 32 accept it
+ *     (warp vote all()).
+ *
+ * Readings where the paper is silent (each also stated in the design notes):
+ *   - Positions are taken in box units u = (x - lo)/L, so Phi = -(G/L) sum M/|du|.
+ *   - The acceptance test is evaluated in IEEE binary32 with this fixed order
+ *     of operations, so that any implementation that evaluates it in binary32
+ *     reaches the same decision (the interaction sum itself stays FP64 here):
+ *       inv = (float)(1/theta)          l = (float)2^-level
+ *       s   = fl(fl(l*inv) + (float)delta)
+ *       s2  = fl(s*s)
+ *       P   = (float)R,  t = (float)u_t (exact: cell centres are dyadic)
+ *       dx  = fl(t.x - P.x), ...
+ *       d2  = fma(dz,dz, fma(dy,dy, fl(dx*dx)))
+ *       accept  <=>  d2 > s2
+ *     This file is compiled with -ffp-contract=off so that every fl() above
+ *     is a single rounding.
+ *   - A node of zero mass has R = its geometric centre (delta = 0).
+ *   - Sums over accepted terms use Neumaier's compensated summation in FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_GEOMETRY 2
+#define OR_ERR_OOM 3
+
+#define MAX_BLOCK_LEVEL 18
+
+typedef struct {
+  int level;          /* 0 = the whole box */
+  int64_t ijk[3];     /* integer position of the cube at its level */
+  int child[8];       /* node index per octant, or -1 for a leaf */
+  int64_t cell;       /* caller cell index b*512 + cz*64 + cy*8 + cx (leaves) */
+  int parent;
+  double M;           /* mass */
+  double R[3];        /* centre of mass, box units */
+  double delta;       /* |R - geometric centre|, box units */
+} onode;
+
+typedef struct {
+  int nblocks;
+  double lo[3], L;
+  int64_t nnodes, cap;
+  onode *node;
+  int64_t *leaf_of_cell; /* caller cell index -> node index */
+  /* build scratch */
+  const int *blevel;
+  const int *bijk;
+  const double *rho;
+  uint64_t *bkey;      /* corner keys of blocks, sorted */
+  int *border;         /* block index, in key order */
+  int used_blocks;
+  int err;
+} otree;
+
+/* ---------------------------------------------------------------- keys -- */
+static uint64_t spread3(uint64_t v) {
+  uint64_t r = 0;
+  for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+  return r;
+}
+/* Morton key of the lower corner of cube (level, i, j, k) on the level-21
+ * lattice.  Octant order o = ox + 2 oy + 4 oz gives x the lowest bit. */
+static uint64_t corner_key(int level, int64_t i, int64_t j, int64_t k) {
+  int sh = 21 - level;
+  return spread3((uint64_t)i << sh) | (spread3((uint64_t)j << sh) << 1) |
+         (spread3((uint64_t)k << sh) << 2);
+}
+
+static otree *g_sort_tree;
+static int cmp_block(const void *a, const void *b) {
+  int x = *(const int *)a, y = *(const int *)b;
+  uint64_t kx = g_sort_tree->bkey[x], ky = g_sort_tree->bkey[y];
+  return kx < ky ? -1 : kx > ky ? 1 : (x - y);
+}
+
+/* First position in key order whose key is >= k. */
+static int lower_bound_key(const otree *t, const uint64_t *sorted, uint64_t k) {
+  int a = 0, b = t->nblocks;
+  while (a < b) {
+    int m = (a + b) / 2;
+    if (sorted[m] < k) a = m + 1; else b = m;
+  }
+  return a;
+}
+
+/* ---------------------------------------------------------------- build -- */
+static int new_node(otree *t, int level, int64_t i, int64_t j, int64_t k, int parent) {
+  if (t->nnodes == t->cap) {
+    int64_t nc = t->cap ? 2 * t->cap : 1024;
+    onode *p = (onode *)realloc(t->node, (size_t)nc * sizeof(onode));
+    if (!p) { t->err = OR_ERR_OOM; return -1; }
+    t->node = p;
+    t->cap = nc;
+  }
+  int id = (int)t->nnodes++;
+  onode *n = &t->node[id];
+  memset(n, 0, sizeof(*n));
+  n->level = level;
+  n->ijk[0] = i; n->ijk[1] = j; n->ijk[2] = k;
+  for (int o = 0; o < 8; ++o) n->child[o] = -1;
+  n->cell = -1;
+  n->parent = parent;
+  return id;
+}
+
+/* Subtree of the cube (level, i,j,k) that lies inside block b (depth d in
+ * the block: 0 = the block itself, 3 = a single cell). */
+static int make_in_block(otree *t, int b, int d, int level, int64_t i, int64_t j,
+                         int64_t k, int parent) {
+  int id = new_node(t, level, i, j, k, parent);
+  if (id < 0) return -1;
+  if (d == 3) {
+    int64_t cx = i - 8 * (int64_t)t->bijk[3 * b + 0];
+    int64_t cy = j - 8 * (int64_t)t->bijk[3 * b + 1];
+    int64_t cz = k - 8 * (int64_t)t->bijk[3 * b + 2];
+    t->node[id].cell = (int64_t)b * 512 + cz * 64 + cy * 8 + cx;
+    return id;
+  }
+  for (int o = 0; o < 8; ++o) {
+    int c = make_in_block(t, b, d + 1, level + 1, 2 * i + (o & 1), 2 * j + ((o >> 1) & 1),
+                          2 * k + ((o >> 2) & 1), id);
+    if (c < 0) return -1;
+    t->node[id].child[o] = c;
+  }
+  return id;
+}
+
+static const uint64_t *g_sorted_keys;
+
+/* Cube (level, i,j,k): it is either exactly one leaf block, or it is covered
+ * by finer blocks and split into 8 children. */
+static int make_cube(otree *t, int level, int64_t i, int64_t j, int64_t k, int parent) {
+  uint64_t k0 = corner_key(level, i, j, k);
+  uint64_t span = 1ull << (3 * (21 - level)); /* level 0: 2^63, fits */
+  int a = lower_bound_key(t, g_sorted_keys, k0);
+  int e = (k0 + span == 0) ? t->nblocks : lower_bound_key(t, g_sorted_keys, k0 + span);
+  if (level == 0) e = t->nblocks;
+  if (a >= e) { t->err = OR_ERR_GEOMETRY; return -1; } /* gap */
+  int b0 = t->border[a];
+  if (g_sorted_keys[a] == k0 && t->blevel[b0] <= level) {
+    /* a block starts here at this level or coarser */
+    if (t->blevel[b0] != level || e - a != 1) { t->err = OR_ERR_GEOMETRY; return -1; }
+    t->used_blocks++;
+    return make_in_block(t, b0, 0, level, i, j, k, parent);
+  }
+  if (level >= MAX_BLOCK_LEVEL) { t->err = OR_ERR_GEOMETRY; return -1; }
+  int id = new_node(t, level, i, j, k, parent);
+  if (id < 0) return -1;
+  for (int o = 0; o < 8; ++o) {
+    int c = make_cube(t, level + 1, 2 * i + (o & 1), 2 * j + ((o >> 1) & 1),
+                      2 * k + ((o >> 2) & 1), id);
+    if (c < 0) return -1;
+    t->node[id].child[o] = c;
+  }
+  return id;
+}
+
+/* Moments, Eq. 5.  Node indices are in pre-order (children after parents),
+ * so one pass over decreasing index sees every child before its parent. */
+static void compute_moments(otree *t) {
+  for (int64_t id = t->nnodes - 1; id >= 0; --id) {
+    onode *n = &t->node[id];
+    double side = ldexp(1.0, -n->level);                /* box units */
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = ((double)n->ijk[a] + 0.5) * side;
+    if (n->child[0] < 0) {
+      /* leaf: m = rho * cell volume (physical), position = cell centre */
+      int64_t cell = n->cell;
+      double h = t->L * ldexp(1.0, -n->level);
+      double vol = h * h * h;
+      n->M = t->rho[cell] * vol;
+      for (int a = 0; a < 3; ++a) n->R[a] = c[a];
+      n->delta = 0.0;
+      continue;
+    }
+    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+    for (int o = 0; o < 8; ++o) {
+      const onode *ch = &t->node[n->child[o]];
+      M = M + ch->M;
+      for (int a = 0; a < 3; ++a) S[a] = S[a] + ch->M * ch->R[a];
+    }
+    n->M = M;
+    if (M > 0.0) {
+      for (int a = 0; a < 3; ++a) n->R[a] = S[a] / M;
+    } else {
+      for (int a = 0; a < 3; ++a) n->R[a] = c[a];
+    }
+    double o0 = n->R[0] - c[0], o1 = n->R[1] - c[1], o2 = n->R[2] - c[2];
+    n->delta = sqrt((o0 * o0 + o1 * o1) + o2 * o2);
+  }
+}
+
+int or_build(int nblocks, const int *level, const int *ijk, const double *density,
+             const double *lo, double L, void **out) {
+  *out = NULL;
+  if (nblocks <= 0 || !level || !ijk || !density || !lo || !(L > 0.0)) return OR_ERR_ARG;
+  for (int b = 0; b < nblocks; ++b) {
+    if (level[b] < 0 || level[b] > MAX_BLOCK_LEVEL) return OR_ERR_GEOMETRY;
+    int64_t n = (int64_t)1 << level[b];
+    for (int a = 0; a < 3; ++a)
+      if (ijk[3 * b + a] < 0 || ijk[3 * b + a] >= n) return OR_ERR_GEOMETRY;
+  }
+  for (int64_t c = 0; c < (int64_t)nblocks * 512; ++c)
+    if (!(density[c] >= 0.0) || !isfinite(density[c])) return OR_ERR_ARG;
+  otree *t = (otree *)calloc(1, sizeof(otree));
+  if (!t) return OR_ERR_OOM;
+  t->nblocks = nblocks;
+  for (int a = 0; a < 3; ++a) t->lo[a] = lo[a];
+  t->L = L;
+  t->blevel = level;
+  t->bijk = ijk;
+  t->rho = density;
+  t->bkey = (uint64_t *)malloc(sizeof(uint64_t) * nblocks);
+  t->border = (int *)malloc(sizeof(int) * nblocks);
+  uint64_t *sk = (uint64_t *)malloc(sizeof(uint64_t) * nblocks);
+  if (!t->bkey || !t->border || !sk) { free(sk); free(t->bkey); free(t->border); free(t); return OR_ERR_OOM; }
+  for (int b = 0; b < nblocks; ++b) {
+    t->bkey[b] = corner_key(level[b], ijk[3 * b], ijk[3 * b + 1], ijk[3 * b + 2]);
+    t->border[b] = b;
+  }
+  g_sort_tree = t;
+  qsort(t->border, nblocks, sizeof(int), cmp_block);
+  for (int p = 0; p < nblocks; ++p) sk[p] = t->bkey[t->border[p]];
+  g_sorted_keys = sk;
+  t->err = OR_OK;
+  make_cube(t, 0, 0, 0, 0, -1);
+  if (t->err == OR_OK && t->used_blocks != nblocks) t->err = OR_ERR_GEOMETRY;
+  free(sk);
+  g_sorted_keys = NULL;
+  int err = t->err;
+  if (err == OR_OK) {
+    t->leaf_of_cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)nblocks * 512);
+    if (!t->leaf_of_cell) err = OR_ERR_OOM;
+  }
+  if (err != OR_OK) {
+    free(t->node); free(t->bkey); free(t->border); free(t->leaf_of_cell); free(t);
+    return err;
+  }
+  for (int64_t id = 0; id < t->nnodes; ++id)
+    if (t->node[id].child[0] < 0) t->leaf_of_cell[t->node[id].cell] = id;
+  compute_moments(t);
+  t->rho = NULL; t->blevel = NULL; t->bijk = NULL;
+  *out = t;
+  return OR_OK;
+}
+
+void or_free(void *p) {
+  otree *t = (otree *)p;
+  if (!t) return;
+  free(t->node); free(t->bkey); free(t->border); free(t->leaf_of_cell); free(t);
+}
+
+int64_t or_num_nodes(const void *p) { return ((const otree *)p)->nnodes; }
+
+/* Node table in pre-order: level, ijk[3], is_leaf, cell, M, R[3], delta,
+ * parent.  Any output pointer may be NULL. */
+int or_export(const void *p, int32_t *level, int64_t *ijk, int32_t *is_leaf, int64_t *cell,
+              double *M, double *R, double *delta, int32_t *parent) {
+  const otree *t = (const otree *)p;
+  for (int64_t id = 0; id < t->nnodes; ++id) {
+    const onode *n = &t->node[id];
+    if (level) level[id] = n->level;
+    if (ijk) for (int a = 0; a < 3; ++a) ijk[3 * id + a] = n->ijk[a];
+    if (is_leaf) is_leaf[id] = n->child[0] < 0;
+    if (cell) cell[id] = n->cell;
+    if (M) M[id] = n->M;
+    if (R) for (int a = 0; a < 3; ++a) R[3 * id + a] = n->R[a];
+    if (delta) delta[id] = n->delta;
+    if (parent) parent[id] = n->parent;
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------ the walk -- */
+typedef struct { double s, c; } neumaier;
+static void nm_add(neumaier *a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double nm_value(const neumaier *a) { return a->s + a->c; }
+
+/* The binary32 acceptance test of Eq. 4 (rounding spelled out in the header). */
+static int accept_f32(const onode *n, const float t[3], float inv_theta) {
+  float l = (float)ldexp(1.0, -n->level);
+  float s = l * inv_theta;
+  s = s + (float)n->delta;
+  float s2 = s * s;
+  float dx = t[0] - (float)n->R[0];
+  float dy = t[1] - (float)n->R[1];
+  float dz = t[2] - (float)n->R[2];
+  float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  return d2 > s2;
+}
+
+static double dist64(const double a[3], const double b[3]) {
+  double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+  return sqrt((x * x + y * y) + z * z);
+}
+
+typedef struct {
+  const otree *t;
+  int64_t self;
+  float tf[3];
+  double tu[3];
+  float inv_theta;
+  neumaier sum;
+  int64_t n_int, n_test;
+  int64_t *list; int64_t list_n, list_cap;   /* optional accepted-set record */
+} walk_state;
+
+static void record(walk_state *w, int64_t id) {
+  if (w->list && w->list_n < w->list_cap) w->list[w->list_n] = id;
+  w->list_n++;
+}
+
+static void walk_node(walk_state *w, int64_t id) {
+  const onode *n = &w->t->node[id];
+  if (n->child[0] < 0) {                      /* a leaf cell */
+    if (id != w->self) {
+      nm_add(&w->sum, n->M / dist64(w->tu, n->R));
+      w->n_int++;
+      record(w, id);
+    }
+    return;
+  }
+  w->n_test++;
+  if (accept_f32(n, w->tf, w->inv_theta)) {   /* Eq. 4: far enough */
+    nm_add(&w->sum, n->M / dist64(w->tu, n->R));
+    w->n_int++;
+    record(w, id);
+    return;
+  }
+  for (int o = 0; o < 8; ++o) walk_node(w, n->child[o]);   /* opened */
+}
+
+static void target_position(const otree *t, int64_t leaf, double tu[3], float tf[3]) {
+  const onode *n = &t->node[leaf];
+  double side = ldexp(1.0, -n->level);
+  for (int a = 0; a < 3; ++a) {
+    tu[a] = ((double)n->ijk[a] + 0.5) * side;
+    tf[a] = (float)tu[a];
+  }
+}
+
+static int check_theta(double theta) { return theta > 0.0 && theta <= 1.0; }
+
+/* Per-cell walk for the given caller cell indices. */
+int or_walk(const void *p, double theta, double G, int64_t ntargets, const int64_t *targets,
+            double *phi, int64_t *n_int, int64_t *n_test, int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || !isfinite(G)) return OR_ERR_ARG;
+  int64_t ncell = (int64_t)t->nblocks * 512;
+  for (int64_t q = 0; q < ntargets; ++q)
+    if (targets[q] < 0 || targets[q] >= ncell) return OR_ERR_ARG;
+  float inv_theta = (float)(1.0 / theta);
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < ntargets; ++q) {
+    walk_state w;
+    memset(&w, 0, sizeof(w));
+    w.t = t;
+    w.self = t->leaf_of_cell[targets[q]];
+    w.inv_theta = inv_theta;
+    target_position(t, w.self, w.tu, w.tf);
+    walk_node(&w, 0);
+    phi[q] = scale * nm_value(&w.sum);
+    if (n_int) n_int[q] = w.n_int;
+    if (n_test) n_test[q] = w.n_test;
+  }
+  return OR_OK;
+}
+
+/* Accepted set of one target: node indices (pre-order) of every accepted
+ * internal node and every leaf it interacts with.  Returns the count (the
+ * list holds the first `cap` of them), or -1 on bad arguments. */
+int64_t or_walk_list(const void *p, double theta, int64_t target, int64_t *list, int64_t cap) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || target < 0 || target >= (int64_t)t->nblocks * 512) return -1;
+  walk_state w;
+  memset(&w, 0, sizeof(w));
+  w.t = t;
+  w.self = t->leaf_of_cell[target];
+  w.inv_theta = (float)(1.0 / theta);
+  target_position(t, w.self, w.tu, w.tf);
+  w.list = list;
+  w.list_cap = cap;
+  walk_node(&w, 0);
+  return w.list_n;
+}
+
+/* ------------------------------------------------------ paper mode walk -- */
+/* A brick is 32 neighbouring cells of one block: local Morton indices
+ * 32q .. 32q+31 (a 4x4x2 set).  All 32 walk together; a node is accepted
+ * only when every one of them accepts it (Sec. 3.3, all() vote). */
+typedef struct {
+  const otree *t;
+  int64_t self[32];
+  float tf[32][3];
+  double tu[32][3];
+  float inv_theta;
+  neumaier sum[32];
+  int64_t n_int[32], n_test[32];
+} brick_state;
+
+static void walk_brick(brick_state *w, int64_t id) {
+  const onode *n = &w->t->node[id];
+  if (n->child[0] < 0) {
+    for (int l = 0; l < 32; ++l) {
+      if (id == w->self[l]) continue;
+      nm_add(&w->sum[l], n->M / dist64(w->tu[l], n->R));
+      w->n_int[l]++;
+    }
+    return;
+  }
+  int all = 1;
+  for (int l = 0; l < 32; ++l) {
+    w->n_test[l]++;
+    if (!accept_f32(n, w->tf[l], w->inv_theta)) all = 0;
+  }
+  if (all) {
+    for (int l = 0; l < 32; ++l) {
+      nm_add(&w->sum[l], n->M / dist64(w->tu[l], n->R));
+      w->n_int[l]++;
+    }
+    return;
+  }
+  for (int o = 0; o < 8; ++o) walk_brick(w, n->child[o]);
+}
+
+static int64_t local_morton_to_cell(int64_t b, int m) {
+  int cx = 0, cy = 0, cz = 0;
+  for (int bit = 0; bit < 3; ++bit) {
+    cx |= ((m >> (3 * bit)) & 1) << bit;
+    cy |= ((m >> (3 * bit + 1)) & 1) << bit;
+    cz |= ((m >> (3 * bit + 2)) & 1) << bit;
+  }
+  return b * 512 + cz * 64 + cy * 8 + cx;
+}
+
+/* bricks[q] = caller block index * 16 + brick number (0..15); phi, n_int and
+ * n_test get 32 entries per brick in local Morton order of the cells. */
+int or_walk_vote(const void *p, double theta, double G, int64_t nbricks, const int64_t *bricks,
+                 double *phi, int64_t *n_int, int64_t *n_test, int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || !isfinite(G)) return OR_ERR_ARG;
+  for (int64_t q = 0; q < nbricks; ++q)
+    if (bricks[q] < 0 || bricks[q] >= (int64_t)t->nblocks * 16) return OR_ERR_ARG;
+  float inv_theta = (float)(1.0 / theta);
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < nbricks; ++q) {
+    brick_state *w = (brick_state *)calloc(1, sizeof(brick_state));
+    w->t = t;
+    w->inv_theta = inv_theta;
+    int64_t b = bricks[q] / 16;
+    int br = (int)(bricks[q] % 16);
+    for (int l = 0; l < 32; ++l) {
+      w->self[l] = t->leaf_of_cell[local_morton_to_cell(b, 32 * br + l)];
+      target_position(t, w->self[l], w->tu[l], w->tf[l]);
+    }
+    walk_brick(w, 0);
+    for (int l = 0; l < 32; ++l) {
+      phi[32 * q + l] = scale * nm_value(&w->sum[l]);
+      if (n_int) n_int[32 * q + l] = w->n_int[l];
+      if (n_test) n_test[32 * q + l] = w->n_test[l];
+    }
+    free(w);
+  }
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------- direct sum -- */
+/* Eq. 2 without the 1/2: Phi_t = -G sum_{j != t} m_j / |r_t - r_j|. */
+int or_direct(const void *p, double G, int64_t ntargets, const int64_t *targets, double *phi,
+              int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!isfinite(G)) return OR_ERR_ARG;
+  int64_t ncell = (int64_t)t->nblocks * 512;
+  for (int64_t q = 0; q < ntargets; ++q)
+    if (targets[q] < 0 || targets[q] >= ncell) return OR_ERR_ARG;
+  /* leaves in pre-order */
+  int64_t *leaf = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+  if (!leaf) return OR_ERR_OOM;
+  int64_t nl = 0;
+  for (int64_t id = 0; id < t->nnodes; ++id)
+    if (t->node[id].child[0] < 0) leaf[nl++] = id;
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < ntargets; ++q) {
+    int64_t self = t->leaf_of_cell[targets[q]];
+    const double *tu = t->node[self].R;
+    neumaier s = {0.0, 0.0};
+    for (int64_t j = 0; j < nl; ++j) {
+      if (leaf[j] == self) continue;
+      const onode *n = &t->node[leaf[j]];
+      nm_add(&s, n->M / dist64(tu, n->R));
+    }
+    phi[q] = scale * nm_value(&s);
+  }
+  free(leaf);
+  return OR_OK;
+}
+
+/* Direct sum over an arbitrary set of point masses (positions in any unit):
+ * Phi_i = -G sum_{j != i} m_j / |r_i - r_j| for the requested targets. */
+int or_direct_points(int64_t n, const double *pos, const double *m, double G,
+                     int64_t ntargets, const int64_t *targets, double *phi) {
+  for (int64_t q = 0; q < ntargets; ++q) {
+    int64_t i = targets[q];
+    if (i < 0 || i >= n) return OR_ERR_ARG;
+    neumaier s = {0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      nm_add(&s, m[j] / dist64(pos + 3 * i, pos + 3 * j));
+    }
+    phi[q] = -G * nm_value(&s);
+  }
+  return OR_OK;
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
