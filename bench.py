@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark: Barnes-Hut potential at every cell of an AMR mesh on GB300.
+
+One step = the whole hot path on one synthetic field already resident in HBM:
+bh_build (block keys, tree topology, FP64 moments) + bh_potential (opening
+radii for theta, walk).  Default workload: the Maclaurin spheroid
+(eccentricity 0.9, 2,039,808 cells, 3 AMR levels at the surface), theta 0.5,
+binary32 walk with Kahan sum, FP64 moments.
+
+Prints one JSON line (rank 0).  `value` is cells/s of the device-resident
+step over all ranks; `e2e` the same through bh_solve_host with pinned host
+buffers (copies inside the timed region); `roofline` puts the walk against
+the FP32 ALU peak (128 FP32 lanes/SM x SMs x measured SM clock), counting the
+algorithmic FP32 operations of the per-cell walk (8 per interaction, 7 per
+opening test; counted by the library's own counting walk);
+`cpu_baseline` times the CPU oracle on a bounded sample of targets.
+
+--impl reference times the CPU oracle alone (the reference arm).
+With torchrun, every rank solves its own copy of the field (replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+FLOP_PER_INTERACTION = 8
+FLOP_PER_TEST = 7
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="maclaurin",
+                    choices=["maclaurin", "cloud_core", "uniform_sphere"])
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1509_07370_gb300 import meshgen as mg
+    if name == "maclaurin":
+        return mg.maclaurin()
+    if name == "cloud_core":
+        return mg.cloud_core()
+    return mg.uniform_sphere()
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+def oracle_leg(w, theta, cpu_seconds, phi_gpu=None):
+    """Times the CPU oracle (tree + FP64 moments in full, walk on a sample of
+    targets) and extrapolates to cells/s for the whole field."""
+    from oracle import oracle as O
+    rho = w.density.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    tree = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(1234)
+    n = w.ncells
+    probe = rng.choice(n, min(n, 2000), replace=False)
+    t0 = time.perf_counter()
+    tree.walk(theta, targets=probe)
+    per = (time.perf_counter() - t0) / len(probe)
+    k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
+    tg = np.sort(rng.choice(n, k, replace=False))
+    t0 = time.perf_counter()
+    ref, ni, nt = tree.walk(theta, targets=tg)
+    t_walk = time.perf_counter() - t0
+    t_step = t_build + t_walk * (n / k)
+    out = {"value": n / t_step, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
+           "sample": f"tree+FP64 moments of all {n} cells; per-cell walk of {k} random cells "
+                     f"(seed 1234) extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s"}
+    if phi_gpu is not None:
+        m = min(k, 2000)
+        d = tree.direct(targets=tg[:m])
+        out["accuracy"] = {
+            "max_rel_vs_oracle_walk": float(np.max(np.abs(phi_gpu[tg] / ref - 1.0))),
+            "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[tg[:m]] / d - 1.0))),
+            "oracle_walk_max_rel_vs_direct": float(np.max(np.abs(ref[:m] / d - 1.0))),
+            "cells_compared": int(k), "cells_vs_direct": int(m)}
+    return out
+
+
+def reference_arm(args):
+    """The reference arm: the CPU oracle, on the host cores, same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    from oracle import oracle as O
+    rho = w.density.astype(np.float32).astype(np.float64)
+    n = w.ncells
+    rng = np.random.default_rng(99)
+    tree = O.Tree(w.mesh.level, w.mesh.ijk, rho)
+    probe = rng.choice(n, 500, replace=False)
+    t0 = time.perf_counter()
+    tree.walk(args.theta, targets=probe)
+    per = (time.perf_counter() - t0) / 500
+    budget = 150.0 / max(1, args.steps + args.warmup)       # whole run within minutes
+    k = int(min(n, max(500, budget / max(per, 1e-9))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        tg = rng.choice(n, k, replace=False)
+        t0 = time.perf_counter()
+        tr = O.Tree(w.mesh.level, w.mesh.ijk, rho)
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        tr.walk(args.theta, targets=tg)
+        tw = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(tb + tw * n / k)
+    t = float(np.sum(times))
+    value = n * args.steps / t
+    line = {"impl": "reference", "metric": "cell potentials/sec", "value": value,
+            "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": n, "theta": args.theta},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": O.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"per step: full tree build + walk of {k} random cells "
+                                       f"extrapolated to {n}"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm --
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1509_07370_gb300 import bhgrav as bh
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = workload(args.workload)
+    n = w.ncells
+    mesh = w.mesh
+    rho32 = np.ascontiguousarray(w.density.reshape(-1), dtype=np.float32)
+    stream = torch.cuda.Stream(dev)
+    solver = bh.Solver(device=local, stream=stream)
+    d_rho = torch.as_tensor(rho32, device=dev)
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        solver.build(mesh.level, mesh.ijk, d_rho)
+        solver.potential(args.theta, 1.0, out=out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        stream.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                solver.build(mesh.level, mesh.ijk, d_rho)
+                ev[k][1].record(stream)
+                solver.potential(args.theta, 1.0, out=out)
+                ev[k][2].record(stream)
+            stream.synchronize()
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    build_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    walk_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms * 1e-3)
+
+    # algorithmic work of the walk (untimed): per-cell counts from the library
+    ni, nt = solver.walk_counts(args.theta)
+    n_int = int(ni.sum(dtype=torch.int64).item())
+    n_test = int(nt.sum(dtype=torch.int64).item())
+    flops = FLOP_PER_INTERACTION * n_int + FLOP_PER_TEST * n_test
+    walk_s = float(np.mean(walk_ms)) * 1e-3
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
+    peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
+    phi_gpu = out.double().cpu().numpy()
+    _, nn, maxlev = solver.tree_size()
+    launches_per_step = 6 + (maxlev - 3) + 2
+
+    # end to end through the host-memory entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        pinned = (torch.from_numpy(rho32).pin_memory(),
+                  torch.empty(n, dtype=torch.float32).pin_memory())
+        h_rho, h_out = pinned[0].numpy(), pinned[1].numpy()
+        host_solver = bh.Solver(device=local, stream=stream)
+        for _ in range(max(1, args.warmup)):
+            host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.sum(ts))
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n * args.steps / e2e_s, "unit": "cells/s",
+               "h2d_bytes_per_step": int(rho32.nbytes + mesh.level.nbytes + mesh.ijk.nbytes),
+               "d2h_bytes_per_step": int(h_out.nbytes)}
+        host_solver.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_leg(w, args.theta, args.cpu_seconds, phi_gpu)
+
+    if rank == 0:
+        line = {
+            "metric": "cell potentials/sec", "value": value, "unit": "cells/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "cells": n, "nodes": nn, "theta": args.theta,
+                       "walk": "binary32, Kahan sum, per-cell opening test",
+                       "moments": "f64", "density_input": "f32",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms))},
+            "walk_work": {"interactions": n_int, "tests": n_test,
+                          "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n},
+            "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",
+                         "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
+                         "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": None,
+                         "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
+                                       f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz "
+                                       "(median SM clock measured during the timed region)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * bhgrav -- Barnes-Hut gravitational potential at every cell centre of an
+ * octree AMR mesh, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the GPU Barnes-Hut tree solver of Lukat & Banerjee,
+ * "A GPU accelerated Barnes-Hut tree code for FLASH4":
+ *   - the octree is the AMR block tree extended down to single cells
+ *     (Sec. 1; Sec. 2; Sec. 3.2.2);
+ *   - every node carries its mass M, centre of mass R (Eq. 5) and the offset
+ *     delta = |R - geometric centre| (Sec. 3.2.3, Fig. opening_angles);
+ *   - the potential of a cell is the sum of -G M / d over the nodes accepted
+ *     by the opening test d > l/theta + delta (Eq. 4) and -G m / d over the
+ *     other cells reached (Sec. 3.3); theta is the runtime parameter
+ *     grv_bh_gpuLimAngle, 0 < theta <= 1 (App. B).
+ *
+ * Calling convention (all entry points):
+ *   - Block geometry (level, ijk) is passed in HOST memory.  Densities, the
+ *     potential and every other array argument are DEVICE pointers on the
+ *     context's device, owned by the caller.  The library owns its tree
+ *     buffers from bh_build until the next bh_build or bh_destroy.
+ *   - Work is issued on the context's CUDA stream.  bh_build returns after
+ *     the tree is complete and validated (it synchronises the stream once to
+ *     report geometry and density errors).  bh_potential only enqueues: the
+ *     output is ready once the stream reaches that point.
+ *   - No exceptions cross this boundary.  Every call returns a bh_status;
+ *     bh_last_error() gives a one-line reason for the last failure on that
+ *     context.  A context must not be used from two threads at once;
+ *     separate contexts are independent.
+ *
+ * Mesh layout:
+ *   - The box is the cube [box_lo, box_lo + box_len)^3.
+ *   - Block b has level[b] in [0, 18] and integer coordinates ijk[3b..3b+2]
+ *     in [0, 2^level[b]); it covers a cube of side box_len / 2^level[b] and
+ *     holds 8^3 cells of side box_len / 2^(level[b]+3).  The leaf blocks must
+ *     tile the box exactly (no gaps, no overlaps); they may come in any order.
+ *     A 2:1 level balance is not required.
+ *   - Cell arrays (density, potential) are [nblocks][8][8][8] in the caller's
+ *     block order, indexed [b][cz][cy][cx], x fastest.
+ */
+#ifndef BHGRAV_H
+#define BHGRAV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bh_ctx bh_ctx;
+
+typedef enum {
+  BH_OK = 0,
+  BH_ERR_ARG = 1,             /* bad argument: null pointer, theta, G, negative/NaN density */
+  BH_ERR_GEOMETRY = 2,        /* blocks do not tile the box, or a level/coordinate is out of range */
+  BH_ERR_OOM = 3,             /* device allocation failed */
+  BH_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+  BH_ERR_DEVICE_TIMEOUT = 5,  /* reserved: a bounded device wait gave up */
+  BH_ERR_STATE = 6            /* call out of order (e.g. bh_potential before bh_build) */
+} bh_status;
+
+/* Arithmetic of the walk.  Node moments are always FP64 (Sec. 3.2.3). */
+enum { BH_PREC_F32 = 0, BH_PREC_F64 = 1 };
+/* Opening test scope: per target cell (the recursive definition of Sec. 2),
+ * or the paper's warp vote (Sec. 3.3): 32 neighbouring cells (a 4x4x2 brick
+ * of a block) accept a node only if all 32 accept it. */
+enum { BH_CRIT_PER_CELL = 0, BH_CRIT_WARP_VOTE = 1 };
+
+typedef struct {
+  int precision;  /* BH_PREC_F32 (default): binary32 interaction arithmetic;
+                     BH_PREC_F64: binary64 interaction arithmetic */
+  int criterion;  /* BH_CRIT_PER_CELL (default) or BH_CRIT_WARP_VOTE */
+  int kahan;      /* F32 only: 1 (default) compensated (Kahan) summation, 0 plain */
+  int reserved[5];
+} bh_options;
+
+/* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation. */
+void bh_default_options(bh_options *opt);
+
+/* Creates a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * opt may be NULL for the defaults.  On success *out owns the context. */
+bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_stream);
+
+/* Builds the octree of the mesh and its FP64 moments (Sec. 3.1.1 "collect
+ * cell data", Sec. 3.2.2 tree build, Sec. 3.2.3 centres of gravity, Eq. 5).
+ *   nblocks          number of leaf blocks (>= 1)
+ *   level, ijk       HOST arrays [nblocks] and [nblocks][3], see "Mesh layout"
+ *   box_lo, box_len  HOST double[3] lower corner and the side (> 0) of the box
+ *   density          DEVICE array of nblocks*512 values, float (density_is_fp64
+ *                    = 0) or double (1); every value finite and >= 0.  Cell
+ *                    mass is density * cell volume.  Read only during the call.
+ * Errors: BH_ERR_ARG, BH_ERR_GEOMETRY (nothing usable is kept: a later
+ * bh_potential returns BH_ERR_STATE), BH_ERR_OOM, BH_ERR_CUDA. */
+bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
+                   const double *box_lo, double box_len, const void *density,
+                   int density_is_fp64);
+
+/* Potential at every cell centre (Sec. 3.3; Eq. 4 opening test, Eq. 2 terms
+ * without the printed 1/2 of the energy sum):
+ *   Phi_t = -G * ( sum over accepted nodes n of M_n / |r_t - R_n|
+ *                + sum over the other cells c reached of m_c / |r_t - r_c| ).
+ *   theta   opening parameter, 0 < theta <= 1
+ *   G       gravitational constant (finite)
+ *   out     DEVICE array of nblocks*512 values in the density layout: float
+ *           for BH_PREC_F32, double for BH_PREC_F64.
+ * The opening test is evaluated in binary32 (round to nearest) in box units
+ * with this fixed order, so that any binary32 implementation of it reaches
+ * the same decisions:
+ *   s  = fl(fl(l * fl(1/theta)) + fl(delta)),  s2 = fl(s * s)
+ *   dx = fl(t.x - fl(R.x)), dy, dz likewise
+ *   d2 = fma(dz, dz, fma(dy, dy, fl(dx * dx)));  accept iff d2 > s2.
+ * The interaction sum is binary32 with Kahan compensation or binary64 per
+ * the context options.
+ * Errors: BH_ERR_STATE (no tree), BH_ERR_ARG, BH_ERR_CUDA. */
+bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out);
+
+/* Same walk as bh_potential, but instead of the potential it writes, per
+ * cell in the density layout, the number of interactions n_int (accepted
+ * nodes plus other cells reached) and of opening tests n_test (internal
+ * nodes examined).  n_int and n_test are DEVICE int32 arrays of
+ * nblocks*512 entries.  Used to count the algorithmic work of a walk. */
+bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test);
+
+/* Sizes of the current tree: leaf cells, all nodes (cells + internal), and
+ * the deepest cell level.  Any pointer may be NULL.  BH_ERR_STATE if no tree. */
+bh_status bh_tree_size(const bh_ctx *ctx, int64_t *n_cells, int64_t *n_nodes, int *max_level);
+
+/* Copies the node table (pre-order of a depth-first visit in octant order
+ * o = ox + 2 oy + 4 oz, children after their parent) to DEVICE arrays of
+ * n_nodes entries (any pointer may be NULL):
+ *   M      double   node mass
+ *   R      double*3 centre of mass in box units u = (x - box_lo)/box_len
+ *   delta  float    |R - geometric centre| in box units, rounded to binary32
+ *   skip   int32    index of the first node after this node's subtree
+ *   level  int32    node level (0 = the box)
+ * For inspection and tests; not needed to compute the potential. */
+bh_status bh_export_nodes(const bh_ctx *ctx, double *M, double *R, float *delta, int32_t *skip,
+                          int32_t *level);
+
+/* One-call form for callers whose data live in HOST memory: copies the
+ * density (float or double per density_is_fp64) to the device, builds the
+ * tree, walks it and copies the potential back to out_host (float or double
+ * per the context precision), then synchronises the stream.  Host buffers
+ * should be pinned for full copy bandwidth.  Same errors as the calls it
+ * makes. */
+bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
+                        const double *box_lo, double box_len, const void *density_host,
+                        int density_is_fp64, double theta, double G, void *out_host);
+
+/* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
+const char *bh_last_error(const bh_ctx *ctx);
+
+/* Releases the context and every buffer the library allocated.  NULL is a no-op. */
+void bh_destroy(bh_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BHGRAV_H */

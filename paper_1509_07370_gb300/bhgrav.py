@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libbhgrav (the C-ABI declared in include/bhgrav.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names; device arrays are passed as torch CUDA
+tensors (their data pointers), host arrays as numpy arrays.  There is no CPU
+fallback: if the library cannot be built or loaded, or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+BH_OK, BH_ERR_ARG, BH_ERR_GEOMETRY, BH_ERR_OOM, BH_ERR_CUDA, BH_ERR_DEVICE_TIMEOUT, \
+    BH_ERR_STATE = range(7)
+BH_PREC_F32, BH_PREC_F64 = 0, 1
+BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
+
+EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_potential", "bh_walk_counts",
+            "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_last_error",
+            "bh_destroy")
+
+
+class bh_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("criterion", ctypes.c_int),
+                ("kahan", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class BHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[bh status {status}] {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libbhgrav.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libbhgrav not built ({path} missing)")
+        lib = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.bh_default_options.argtypes = [ctypes.POINTER(bh_options)]
+        lib.bh_default_options.restype = None
+        lib.bh_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(bh_options), I, P]
+        lib.bh_build.argtypes = [P, I, P, P, P, D, P, I]
+        lib.bh_potential.argtypes = [P, D, D, P]
+        lib.bh_walk_counts.argtypes = [P, D, P, P]
+        lib.bh_tree_size.argtypes = [P, P, P, P]
+        lib.bh_export_nodes.argtypes = [P, P, P, P, P, P]
+        lib.bh_solve_host.argtypes = [P, I, P, P, P, D, P, I, D, D, P]
+        lib.bh_last_error.argtypes = [P]
+        lib.bh_last_error.restype = ctypes.c_char_p
+        lib.bh_destroy.argtypes = [P]
+        lib.bh_destroy.restype = None
+        for name in ("bh_create", "bh_build", "bh_potential", "bh_walk_counts",
+                     "bh_tree_size", "bh_export_nodes", "bh_solve_host"):
+            getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def _check(ctx, st: int, what: str):
+    if st != BH_OK:
+        msg = load().bh_last_error(ctx).decode() if ctx else ""
+        raise BHError(st, f"{what}: {msg}")
+
+
+def _dev_ptr(t, dtype=None) -> int:
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- C names --
+def bh_default_options() -> bh_options:
+    o = bh_options()
+    load().bh_default_options(ctypes.byref(o))
+    return o
+
+
+def bh_create(opt: bh_options | None = None, device: int = 0, stream: int = 0):
+    h = ctypes.c_void_p()
+    st = load().bh_create(ctypes.byref(h), ctypes.byref(opt) if opt is not None else None,
+                          int(device), ctypes.c_void_p(int(stream)))
+    _check(None, st, "bh_create")
+    return h
+
+
+def bh_build(ctx, level, ijk, box_lo, box_len, density) -> None:
+    """level, ijk: host int arrays; density: CUDA float32/float64 tensor."""
+    import torch
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    if density.dtype not in (torch.float32, torch.float64):
+        raise ValueError("density must be float32 or float64")
+    if density.numel() != 512 * level.shape[0]:
+        raise ValueError("density must hold 512 values per block")
+    st = load().bh_build(ctx, int(level.shape[0]), _np_ptr(level), _np_ptr(ijk), _np_ptr(lo),
+                         float(box_len), ctypes.c_void_p(_dev_ptr(density)),
+                         int(density.dtype == torch.float64))
+    _check(ctx, st, "bh_build")
+
+
+def bh_potential(ctx, theta: float, G: float, out) -> None:
+    st = load().bh_potential(ctx, float(theta), float(G), ctypes.c_void_p(_dev_ptr(out)))
+    _check(ctx, st, "bh_potential")
+
+
+def bh_walk_counts(ctx, theta: float, n_int, n_test) -> None:
+    import torch
+    st = load().bh_walk_counts(ctx, float(theta),
+                               ctypes.c_void_p(_dev_ptr(n_int, torch.int32)),
+                               ctypes.c_void_p(_dev_ptr(n_test, torch.int32)))
+    _check(ctx, st, "bh_walk_counts")
+
+
+def bh_tree_size(ctx):
+    nc, nn, ml = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    st = load().bh_tree_size(ctx, ctypes.byref(nc), ctypes.byref(nn), ctypes.byref(ml))
+    _check(ctx, st, "bh_tree_size")
+    return nc.value, nn.value, ml.value
+
+
+def bh_export_nodes(ctx, M=None, R=None, delta=None, skip=None, level=None) -> None:
+    def p(t):
+        return ctypes.c_void_p(_dev_ptr(t)) if t is not None else None
+    st = load().bh_export_nodes(ctx, p(M), p(R), p(delta), p(skip), p(level))
+    _check(ctx, st, "bh_export_nodes")
+
+
+def bh_solve_host(ctx, level, ijk, box_lo, box_len, density_host: np.ndarray, theta: float,
+                  G: float, out_host: np.ndarray) -> None:
+    """Host-memory form: density_host and out_host are (ideally pinned) host
+    arrays; copies to and from the device happen inside the call."""
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    if not (density_host.flags.c_contiguous and out_host.flags.c_contiguous):
+        raise ValueError("host buffers must be C-contiguous")
+    if density_host.dtype not in (np.float32, np.float64):
+        raise ValueError("density must be float32 or float64")
+    st = load().bh_solve_host(ctx, int(level.shape[0]), _np_ptr(level), _np_ptr(ijk),
+                              _np_ptr(lo), float(box_len), _np_ptr(density_host),
+                              int(density_host.dtype == np.float64), float(theta), float(G),
+                              _np_ptr(out_host))
+    _check(ctx, st, "bh_solve_host")
+
+
+def bh_last_error(ctx) -> str:
+    return load().bh_last_error(ctx).decode()
+
+
+def bh_destroy(ctx) -> None:
+    if ctx:
+        load().bh_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience --
+class Solver:
+    """Owns one bh_ctx.  Example::
+
+        s = Solver(precision=BH_PREC_F32)
+        s.build(mesh.level, mesh.ijk, density_cuda)       # tree + FP64 moments
+        phi = s.potential(theta=0.5, G=1.0)               # CUDA tensor, density layout
+    """
+
+    def __init__(self, precision=BH_PREC_F32, criterion=BH_CRIT_PER_CELL, kahan=True,
+                 device=0, stream=None):
+        import torch
+        o = bh_default_options()
+        o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
+        self.options = o
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self._ctx = bh_create(o, device, stream.cuda_stream)
+        self.ncells = 0
+
+    def build(self, level, ijk, density, box_lo=(0.0, 0.0, 0.0), box_len=1.0):
+        bh_build(self._ctx, level, ijk, box_lo, box_len, density)
+        self.ncells = 512 * len(level)
+        return self
+
+    def potential(self, theta: float, G: float = 1.0, out=None):
+        import torch
+        if out is None:
+            dt = torch.float64 if self.options.precision == BH_PREC_F64 else torch.float32
+            out = torch.empty(self.ncells, dtype=dt, device=self.device)
+        bh_potential(self._ctx, theta, G, out)
+        return out
+
+    def walk_counts(self, theta: float):
+        import torch
+        ni = torch.empty(self.ncells, dtype=torch.int32, device=self.device)
+        nt = torch.empty(self.ncells, dtype=torch.int32, device=self.device)
+        bh_walk_counts(self._ctx, theta, ni, nt)
+        return ni, nt
+
+    def tree_size(self):
+        return bh_tree_size(self._ctx)
+
+    def export_nodes(self):
+        import torch
+        _, n, _ = self.tree_size()
+        d = self.device
+        out = dict(M=torch.empty(n, dtype=torch.float64, device=d),
+                   R=torch.empty((n, 3), dtype=torch.float64, device=d),
+                   delta=torch.empty(n, dtype=torch.float32, device=d),
+                   skip=torch.empty(n, dtype=torch.int32, device=d),
+                   level=torch.empty(n, dtype=torch.int32, device=d))
+        bh_export_nodes(self._ctx, **out)
+        return out
+
+    def solve_host(self, level, ijk, density_host, theta, G=1.0, out_host=None,
+                   box_lo=(0.0, 0.0, 0.0), box_len=1.0):
+        if out_host is None:
+            dt = np.float64 if self.options.precision == BH_PREC_F64 else np.float32
+            out_host = np.empty(512 * len(level), dtype=dt)
+        bh_solve_host(self._ctx, level, ijk, box_lo, box_len, density_host, theta, G, out_host)
+        self.ncells = 512 * len(level)
+        return out_host
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            bh_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

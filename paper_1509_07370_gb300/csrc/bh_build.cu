@@ -1,0 +1,479 @@
+// Tree construction and FP64 moments for the Barnes-Hut AMR solver.
+//
+// The paper builds its octree by inserting cells one at a time under locks
+// (Sec. 3.2.2) and sums the node moments bottom-up with threads that wait on
+// children still marked by a negative mass (Sec. 3.2.3).  Here neither locks
+// nor spin waits are used.  Because the leaf blocks of an AMR mesh tile the
+// box, the octree is fully determined by the block list: every cube that
+// holds more than one block is split into 8, every block is an 8^3 subtree.
+// So:
+//   1. each block gets the Morton key of its lower corner on the level-21
+//      lattice (k_block_keys) and blocks are put in key order (k_sort_blocks,
+//      only if the caller's order is not already sorted);
+//   2. consecutive keys must abut exactly (k_tile_and_count): this checks that
+//      the blocks tile the box, and the trailing zero bits of a block's key
+//      tell how many internal "top" nodes (cubes above the blocks) start at it
+//      in pre-order;
+//   3. an exclusive scan gives every block the pre-order index of its first
+//      node (k_prestart_scan), from which top nodes get their skip pointers
+//      (k_top_nodes);
+//   4. one CTA per block reduces its 512 cells to 64, 8 and 1 nodes in shared
+//      memory (k_blocks), and one short launch per level reduces the top
+//      nodes, deepest level first (k_top_moments).
+// Moments follow Eq. 5 with the children summed in octant order, in FP64 with
+// explicitly rounded operations (no contraction), so results are
+// reproducible bit for bit.
+#include "bh_internal.cuh"
+
+namespace bhg {
+namespace {
+
+__device__ __forceinline__ unsigned long long key_span(int level) {
+  return 1ull << (3 * (kKeyLevels - level));  // volume of a level cube in level-21 cells
+}
+
+__device__ __forceinline__ unsigned long long block_key(int lb, int i, int j, int k) {
+  const int sh = kKeyLevels - lb;
+  return spread3((unsigned long long)i << sh) | (spread3((unsigned long long)j << sh) << 1) |
+         (spread3((unsigned long long)k << sh) << 2);
+}
+
+// Returns true when (lb, ijk) is a valid block; raises error bits otherwise.
+__device__ __forceinline__ bool valid_block(int lb, int i, int j, int k, unsigned *flags) {
+  if (lb < 0 || lb > kMaxBlockLevel) {
+    atomicOr(flags, kErrLevel);
+    return false;
+  }
+  const int n = 1 << lb;
+  if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) {
+    atomicOr(flags, kErrCoord);
+    return false;
+  }
+  return true;
+}
+
+__global__ void k_block_keys(int nb, const int *__restrict__ level, const int *__restrict__ ijk,
+                             unsigned long long *__restrict__ key, int *__restrict__ idx,
+                             unsigned *flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int lb = level[b];
+  const int i = ijk[3 * b], j = ijk[3 * b + 1], k = ijk[3 * b + 2];
+  unsigned long long kb = ~0ull;
+  if (valid_block(lb, i, j, k, flags)) kb = block_key(lb, i, j, k);
+  key[b] = kb;
+  idx[b] = b;
+  // is the caller's order already the key order?  (compare with block b+1)
+  if (b + 1 < nb) {
+    const int l2 = level[b + 1];
+    unsigned long long k2 = ~0ull;
+    if (l2 >= 0 && l2 <= kMaxBlockLevel) k2 = block_key(l2, ijk[3 * b + 3], ijk[3 * b + 4], ijk[3 * b + 5]);
+    if (!(kb < k2)) atomicOr(flags + 1, 1u);
+  }
+}
+
+// Stable LSD radix sort of (key, idx) in one CTA, 4 bits per pass, 16
+// passes, result back in buffer 0.  Block lists are small (a 16M-cell mesh
+// has ~32k blocks), and the sort only runs when the caller's block order is
+// not already the Morton order.
+constexpr int kSortThreads = 512;
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_blocks(int n, unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
+                  const unsigned *flags) {
+  if (flags[1] == 0u) return;  // already sorted
+  __shared__ int hist[16 * kSortThreads];
+  __shared__ int part[kSortThreads];
+  const int t = threadIdx.x;
+  const int per = (n + kSortThreads - 1) / kSortThreads;
+  const int beg = min(t * per, n), end = min(beg + per, n);
+  unsigned long long *kin = k0, *kout = k1;
+  int *vin = v0, *vout = v1;
+  for (int pass = 0; pass < 16; ++pass) {
+    const int sh = 4 * pass;
+    int cnt[16];
+#pragma unroll
+    for (int d = 0; d < 16; ++d) cnt[d] = 0;
+    for (int i = beg; i < end; ++i) cnt[(kin[i] >> sh) & 15]++;
+#pragma unroll
+    for (int d = 0; d < 16; ++d) hist[d * kSortThreads + t] = cnt[d];
+    __syncthreads();
+    int s = 0;
+    for (int j = 0; j < 16; ++j) s += hist[16 * t + j];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < kSortThreads; off <<= 1) {
+      const int v = t >= off ? part[t - off] : 0;
+      __syncthreads();
+      part[t] += v;
+      __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int j = 0; j < 16; ++j) {
+      const int c = hist[16 * t + j];
+      hist[16 * t + j] = run;
+      run += c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < 16; ++d) cnt[d] = hist[d * kSortThreads + t];
+    for (int i = beg; i < end; ++i) {
+      const unsigned long long kk = kin[i];
+      const int pos = cnt[(kk >> sh) & 15]++;
+      kout[pos] = kk;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    unsigned long long *tk = kin; kin = kout; kout = tk;
+    int *tv = vin; vin = vout; vout = tv;
+  }
+}
+
+__device__ __forceinline__ int top_start_level(unsigned long long key) {
+  // smallest level j such that the key is aligned to a level-j cube
+  const int tz = key ? __ffsll((long long)key) - 1 : 64;
+  return max(0, kKeyLevels - tz / 3);
+}
+
+__global__ void k_tile_and_count(int nb, const unsigned long long *__restrict__ key,
+                                 const int *__restrict__ idx, const int *__restrict__ level,
+                                 const int *__restrict__ ijk, int *__restrict__ count,
+                                 int4 *__restrict__ blk, int *__restrict__ orig,
+                                 unsigned *flags) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nb) return;
+  const int b = idx[p];
+  const int lb = level[b];
+  const unsigned long long kp = key[p];
+  int cnt = 0;
+  if (kp != ~0ull && lb >= 0 && lb <= kMaxBlockLevel) {
+    bool ok = true;
+    if (p == 0) {
+      ok = ok && kp == 0ull;
+    } else {
+      const int lprev = level[idx[p - 1]];
+      const unsigned long long kprev = key[p - 1];
+      ok = ok && kprev != ~0ull && lprev >= 0 && lprev <= kMaxBlockLevel &&
+           kprev + key_span(lprev) == kp;
+    }
+    if (p == nb - 1) ok = ok && kp + key_span(lb) == (1ull << 63);
+    if (!ok) atomicOr(flags, kErrTiling);
+    cnt = max(0, lb - top_start_level(kp));
+  }
+  count[p] = cnt;
+  blk[p] = make_int4(lb, ijk[3 * b], ijk[3 * b + 1], ijk[3 * b + 2]);
+  orig[p] = b;
+}
+
+// prestart[p] = 585 p + sum_{q<p} count[q]: pre-order index of the first node
+// that belongs to block p (its first top node, else its root).  One CTA.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads)
+    k_prestart_scan(int nb, const int *__restrict__ count, int *__restrict__ prestart,
+                    unsigned *flags) {
+  __shared__ int part[kScanThreads];
+  const int t = threadIdx.x;
+  const int per = (nb + kScanThreads - 1) / kScanThreads;
+  const int beg = min(t * per, nb), end = min(beg + per, nb);
+  int s = 0;
+  for (int i = beg; i < end; ++i) s += count[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    const int v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - s;
+  for (int i = beg; i < end; ++i) {
+    prestart[i] = kNodesPerBlock * i + run;
+    run += count[i];
+  }
+  if (t == kScanThreads - 1) flags[2] = (unsigned)part[t];
+}
+
+__device__ __forceinline__ float pow2f(int e) {  // 2^e for -126 <= e <= 127, exact
+  return __int_as_float((127 + e) << 23);
+}
+__device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023, exact
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+__global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
+                            const int4 *__restrict__ blk, const int *__restrict__ count,
+                            const int *__restrict__ prestart, int64_t n_nodes,
+                            float2 *__restrict__ rec1, float2 *__restrict__ aux,
+                            uint8_t *__restrict__ lvl, unsigned *flags) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nb) return;
+  const int cnt = count[p];
+  if (cnt == 0) return;
+  const int lb = blk[p].x;
+  const int j0 = lb - cnt;
+  const unsigned long long kp = key[p];
+  for (int k = j0; k < lb; ++k) {
+    const int64_t id = (int64_t)prestart[p] + (k - j0);
+    // first block whose key lies beyond this cube: its first node follows the subtree
+    const unsigned long long lim = kp + (1ull << (3 * (kKeyLevels - k)));
+    int a = p + 1, e = nb;
+    while (a < e) {
+      const int m = (a + e) >> 1;
+      if (key[m] < lim) a = m + 1; else e = m;
+    }
+    const int64_t skip = a < nb ? (int64_t)prestart[a] : n_nodes;
+    if (id < 0 || id >= n_nodes || skip > n_nodes) {
+      atomicOr(flags, kErrIndex);
+      continue;
+    }
+    rec1[id] = make_float2(0.0f, __int_as_float((int)skip));
+    aux[id] = make_float2(pow2f(-k), 0.0f);
+    lvl[id] = (uint8_t)k;
+  }
+}
+
+// Moments of one internal node from its 8 children (Eq. 5), children in
+// octant order, every operation rounded once.  c = geometric centre.
+struct Moment {
+  double x, y, z, m, delta;
+};
+__device__ __forceinline__ void accumulate(double &M, double &Sx, double &Sy, double &Sz,
+                                           double m, double x, double y, double z) {
+  M = __dadd_rn(M, m);
+  Sx = __dadd_rn(Sx, __dmul_rn(m, x));
+  Sy = __dadd_rn(Sy, __dmul_rn(m, y));
+  Sz = __dadd_rn(Sz, __dmul_rn(m, z));
+}
+__device__ __forceinline__ Moment finish(double M, double Sx, double Sy, double Sz, double cx,
+                                         double cy, double cz) {
+  Moment r;
+  r.m = M;
+  if (M > 0.0) {
+    r.x = __ddiv_rn(Sx, M);
+    r.y = __ddiv_rn(Sy, M);
+    r.z = __ddiv_rn(Sz, M);
+  } else {  // a massless node sits at its geometric centre
+    r.x = cx;
+    r.y = cy;
+    r.z = cz;
+  }
+  const double ox = __dsub_rn(r.x, cx), oy = __dsub_rn(r.y, cy), oz = __dsub_rn(r.z, cz);
+  r.delta = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz)));
+  return r;
+}
+
+__device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int level,
+                                               const Moment &r, double4_32a *mom, float4 *rec0,
+                                               float2 *rec1, float2 *aux, uint8_t *lvl) {
+  mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
+  rec0[id] = make_float4(__double2float_rn(r.x), __double2float_rn(r.y), __double2float_rn(r.z),
+                         __double2float_rn(r.m));
+  rec1[id] = make_float2(0.0f, __int_as_float((int)skip));
+  aux[id] = make_float2(pow2f(-level), __double2float_rn(r.delta));
+  if (lvl) lvl[id] = (uint8_t)level;
+}
+
+constexpr int kBlockThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_blocks(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
+             const int *__restrict__ count, const int *__restrict__ prestart,
+             const T *__restrict__ density, double L, int64_t n_nodes, double4_32a *__restrict__ mom,
+             float4 *__restrict__ rec0, float2 *__restrict__ rec1, float2 *__restrict__ aux,
+             uint8_t *__restrict__ lvl, unsigned *flags) {
+  __shared__ double cm[512], cxs[512], cys[512], czs[512];  // cells, local Morton order
+  __shared__ double gm[64], gx[64], gy[64], gz[64];         // level lb+2 nodes
+  __shared__ double pm[8], px[8], py[8], pz[8];             // level lb+1 nodes
+  const int p = blockIdx.x;
+  const int t = threadIdx.x;
+  const int4 B = blk[p];
+  const int lb = B.x;
+  if (lb < 0 || lb > kMaxBlockLevel) return;  // flagged earlier
+  const int64_t root = (int64_t)prestart[p] + count[p];
+  if (root < 0 || root + kNodesPerBlock > n_nodes) {
+    if (t == 0) atomicOr(flags, kErrIndex);
+    return;
+  }
+  const int lc = lb + 3;
+  const double hs = pow2d(-lc);               // cell side, box units
+  const double h = __dmul_rn(L, hs);          // cell side, physical
+  const double vol = __dmul_rn(__dmul_rn(h, h), h);
+  const T *rho = density + (int64_t)orig[p] * kCellsPerBlock;
+  bool bad = false;
+  for (int i = t; i < kCellsPerBlock; i += kBlockThreads) {
+    const double r = (double)rho[i];
+    if (!(r >= 0.0) || isinf(r)) bad = true;
+    const int cx = i & 7, cy = (i >> 3) & 7, cz = i >> 6;
+    const int m = (int)(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
+    const double ux = __dmul_rn((double)(8 * B.y + cx) + 0.5, hs);
+    const double uy = __dmul_rn((double)(8 * B.z + cy) + 0.5, hs);
+    const double uz = __dmul_rn((double)(8 * B.w + cz) + 0.5, hs);
+    const double mass = __dmul_rn(r, vol);
+    cm[m] = mass;
+    cxs[m] = ux;
+    cys[m] = uy;
+    czs[m] = uz;
+    const int64_t id = root + cell_offset(m);
+    mom[id] = make_double4_32a(ux, uy, uz, mass);
+    rec0[id] = make_float4(__double2float_rn(ux), __double2float_rn(uy), __double2float_rn(uz),
+                           __double2float_rn(mass));
+    rec1[id] = make_float2(0.0f, __int_as_float((int)(id + 1)));
+    aux[id] = make_float2(0.0f, 0.0f);
+    lvl[id] = (uint8_t)lc;
+  }
+  if (bad) atomicOr(flags, kErrDensity);
+  __syncthreads();
+  if (t < 64) {  // nodes at level lb+2: q = 8p + r, children = cells 8q..8q+7
+    const int q = t;
+    const int qx = (int)compact3(q), qy = (int)compact3(q >> 1), qz = (int)compact3(q >> 2);
+    const double hg = pow2d(-(lb + 2));
+    const double cx = __dmul_rn((double)(4 * B.y + qx) + 0.5, hg);
+    const double cy = __dmul_rn((double)(4 * B.z + qy) + 0.5, hg);
+    const double cz = __dmul_rn((double)(4 * B.w + qz) + 0.5, hg);
+    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+      accumulate(M, Sx, Sy, Sz, cm[8 * q + o], cxs[8 * q + o], cys[8 * q + o], czs[8 * q + o]);
+    const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
+    gm[q] = r.m;
+    gx[q] = r.x;
+    gy[q] = r.y;
+    gz[q] = r.z;
+    const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
+    store_internal(id, id + 9, lb + 2, r, mom, rec0, rec1, aux, lvl);
+  }
+  __syncthreads();
+  if (t < 8) {  // nodes at level lb+1
+    const int c = t;
+    const double hp = pow2d(-(lb + 1));
+    const double cx = __dmul_rn((double)(2 * B.y + (c & 1)) + 0.5, hp);
+    const double cy = __dmul_rn((double)(2 * B.z + ((c >> 1) & 1)) + 0.5, hp);
+    const double cz = __dmul_rn((double)(2 * B.w + ((c >> 2) & 1)) + 0.5, hp);
+    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+      accumulate(M, Sx, Sy, Sz, gm[8 * c + o], gx[8 * c + o], gy[8 * c + o], gz[8 * c + o]);
+    const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
+    pm[c] = r.m;
+    px[c] = r.x;
+    py[c] = r.y;
+    pz[c] = r.z;
+    const int64_t id = root + 1 + 73 * c;
+    store_internal(id, id + 73, lb + 1, r, mom, rec0, rec1, aux, lvl);
+  }
+  __syncthreads();
+  if (t == 0) {  // the block itself
+    const double hb = pow2d(-lb);
+    const double cx = __dmul_rn((double)B.y + 0.5, hb);
+    const double cy = __dmul_rn((double)B.z + 0.5, hb);
+    const double cz = __dmul_rn((double)B.w + 0.5, hb);
+    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
+    const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
+    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec0, rec1, aux, lvl);
+  }
+}
+
+// Top nodes of one level: children are top nodes one level down or block roots,
+// found by following skip pointers from the first child (the next node).
+__global__ void k_top_moments(int nb, int level, const unsigned long long *__restrict__ key,
+                              const int4 *__restrict__ blk, const int *__restrict__ count,
+                              const int *__restrict__ prestart, int64_t n_nodes,
+                              double4_32a *__restrict__ mom, float4 *__restrict__ rec0,
+                              float2 *__restrict__ rec1, float2 *__restrict__ aux,
+                              unsigned *flags) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nb) return;
+  const int cnt = count[p];
+  const int lb = blk[p].x;
+  const int j0 = lb - cnt;
+  if (cnt == 0 || level < j0 || level >= lb) return;
+  const int64_t id = (int64_t)prestart[p] + (level - j0);
+  const unsigned long long kp = key[p];
+  const int sh = kKeyLevels - level;
+  const double hl = pow2d(-level);
+  const double cx = __dmul_rn((double)(compact3(kp) >> sh) + 0.5, hl);
+  const double cy = __dmul_rn((double)(compact3(kp >> 1) >> sh) + 0.5, hl);
+  const double cz = __dmul_rn((double)(compact3(kp >> 2) >> sh) + 0.5, hl);
+  double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+  int64_t c = id + 1;
+  for (int o = 0; o < 8; ++o) {
+    if (c <= 0 || c >= n_nodes) {
+      atomicOr(flags, kErrIndex);
+      return;
+    }
+    const double4_32a ch = mom[c];
+    accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
+    c = __float_as_int(rec1[c].y);
+  }
+  const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
+  const int64_t skip = __float_as_int(rec1[id].y);
+  store_internal(id, skip, level, r, mom, rec0, rec1, aux, nullptr);
+}
+
+inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
+                              unsigned long long *key, int *idx, unsigned *flags) {
+  k_block_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, ijk, key, idx, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_blocks(cudaStream_t s, int nb, unsigned long long *key[2], int *idx[2],
+                               unsigned *flags, int *) {
+  k_sort_blocks<<<1, kSortThreads, 0, s>>>(nb, key[0], idx[0], key[1], idx[1], flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
+                                  const int *idx, const int *level, const int *ijk, int *count,
+                                  int4 *blk, int *orig, unsigned *flags) {
+  k_tile_and_count<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, idx, level, ijk, count, blk, orig,
+                                                      flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
+                                 unsigned *flags) {
+  k_prestart_scan<<<1, kScanThreads, 0, s>>>(nb, count, prestart, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
+                             const int4 *blk, const int *count, const int *prestart,
+                             int64_t n_nodes, float2 *rec1, float2 *aux, uint8_t *lvl,
+                             unsigned *flags) {
+  k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec1,
+                                                 aux, lvl, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
+                          const int *count, const int *prestart, const void *density,
+                          int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
+                          float4 *rec0, float2 *rec1, float2 *aux, uint8_t *lvl,
+                          unsigned *flags) {
+  if (density_is_fp64)
+    k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
+                                                   (const double *)density, L, n_nodes, mom,
+                                                   rec0, rec1, aux, lvl, flags);
+  else
+    k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
+                                                  (const float *)density, L, n_nodes, mom, rec0,
+                                                  rec1, aux, lvl, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
+                               const int4 *blk, const int *count, const int *prestart,
+                               int64_t n_nodes, double4_32a *mom, float4 *rec0, float2 *rec1,
+                               float2 *aux, unsigned *flags) {
+  k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
+                                                   n_nodes, mom, rec0, rec1, aux, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace bhg

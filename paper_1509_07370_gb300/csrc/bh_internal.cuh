@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of libbhgrav.
+//
+// Node storage (all arrays indexed by the node's pre-order position: a
+// depth-first visit of the octree in octant order o = ox + 2 oy + 4 oz, so a
+// node's first child sits right after it and its subtree is contiguous):
+//   mom  double4_32a {Rx, Ry, Rz, M}  FP64 centre of mass (box units) and mass
+//   rec0 float4  {Px, Py, Pz, M}  the same rounded to binary32 (walk record)
+//   rec1 float2  {s2, skip}       squared opening radius for the current
+//                                 theta (0 for cells) and, as raw int bits,
+//                                 the index of the first node after the subtree
+//   aux  float2  {l, delta}       node side and |R - centre| in binary32
+//                                 (both 0 for cells)
+//   lvl  uint8                    node level
+// Leaf blocks are renumbered in Morton order of their lower corner ("sorted
+// position" p); blk[p] = {level, bi, bj, bk}, orig[p] = caller block index.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bhgrav.h"
+
+namespace bhg {
+
+constexpr int kCellsPerBlock = 512;
+constexpr int kNodesPerBlock = 585;  // 1 + 8 + 64 + 512
+constexpr int kMaxBlockLevel = 18;   // cells at level <= 21: 63-bit Morton keys
+constexpr int kKeyLevels = 21;
+
+// Error bits raised by device-side validation.
+enum : unsigned {
+  kErrLevel = 1u,        // level outside [0, 18]
+  kErrCoord = 2u,        // coordinate outside [0, 2^level)
+  kErrTiling = 4u,       // sorted blocks leave a gap or overlap
+  kErrDensity = 8u,      // negative or non-finite density
+  kErrIndex = 16u,       // a node index fell outside the allocation
+};
+
+struct Tree {
+  // block arrays (capacity nb_cap)
+  int *d_level = nullptr, *d_ijk = nullptr;
+  unsigned long long *d_key[2] = {nullptr, nullptr};
+  int *d_idx[2] = {nullptr, nullptr};
+  int *d_count = nullptr, *d_prestart = nullptr;
+  int4 *d_blk = nullptr;
+  int *d_orig = nullptr;
+  unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total
+  unsigned *h_flags = nullptr;  // pinned mirror of d_flags
+  int64_t nb_cap = 0;
+  // node arrays (capacity node_cap)
+  double4_32a *d_mom = nullptr;
+  float4 *d_rec0 = nullptr;
+  float2 *d_rec1 = nullptr;
+  float2 *d_aux = nullptr;
+  uint8_t *d_lvl = nullptr;
+  int64_t node_cap = 0;
+  // host staging for the density of bh_solve_host
+  void *d_stage_in = nullptr, *d_stage_out = nullptr;
+  int64_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // current tree
+  int nb = 0;
+  int max_block_level = 0;
+  int64_t n_nodes = 0;
+  double lo[3] = {0, 0, 0};
+  double L = 1.0;
+  bool built = false;
+  float s2_inv_theta = -1.0f;  // inverse theta the s2 field was prepared for
+};
+
+// ---- build kernels (bh_build.cu) -------------------------------------------
+// Every launcher returns the cudaError_t of its launch.
+cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
+                              unsigned long long *key, int *idx, unsigned *flags);
+cudaError_t launch_sort_blocks(cudaStream_t s, int nb, unsigned long long *key[2], int *idx[2],
+                               unsigned *flags, int *which_out_host_unused);
+cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
+                                  const int *idx, const int *level, const int *ijk,
+                                  int *count, int4 *blk, int *orig, unsigned *flags);
+cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
+                                 unsigned *flags);
+cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
+                             const int4 *blk, const int *count, const int *prestart,
+                             int64_t n_nodes, float2 *rec1, float2 *aux, uint8_t *lvl,
+                             unsigned *flags);
+cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
+                          const int *count, const int *prestart, const void *density,
+                          int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
+                          float4 *rec0, float2 *rec1, float2 *aux, uint8_t *lvl,
+                          unsigned *flags);
+cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
+                               const int4 *blk, const int *count, const int *prestart,
+                               int64_t n_nodes, double4_32a *mom, float4 *rec0, float2 *rec1,
+                               float2 *aux, unsigned *flags);
+
+// ---- walk kernels (bh_walk.cu) ---------------------------------------------
+cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, float2 *rec1,
+                              float inv_theta);
+// out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
+cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
+                        const float4 *rec0, const float2 *rec1, const double4_32a *mom,
+                        const int4 *blk, const int *orig, double scale, void *out,
+                        int32_t *n_int, int32_t *n_test);
+
+// ---- small device helpers ---------------------------------------------------
+// Spread the low 21 bits of v so bit b lands at bit 3b.
+__host__ __device__ inline unsigned long long spread3(unsigned long long v) {
+  v &= 0x1FFFFFull;
+  v = (v | (v << 32)) & 0x1F00000000FFFFull;
+  v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+  v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+  v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+// Inverse of spread3.
+__host__ __device__ inline unsigned long long compact3(unsigned long long v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10C30C30C30C30C3ull;
+  v = (v ^ (v >> 4)) & 0x100F00F00F00F00Full;
+  v = (v ^ (v >> 8)) & 0x1F0000FF0000FFull;
+  v = (v ^ (v >> 16)) & 0x1F00000000FFFFull;
+  v = (v ^ (v >> 32)) & 0x1FFFFFull;
+  return v;
+}
+
+// Position of a node inside its block's 585-node pre-order subtree.
+//   block root 0; child p (0..7) at 1 + 73p; grandchild (p, r) at 2 + 73p + 9r;
+//   cell with local Morton index m = 64p + 8r + s at 3 + 73p + 9r + s.
+__host__ __device__ inline int cell_offset(int m) {
+  return 3 + 73 * (m >> 6) + 9 * ((m >> 3) & 7) + (m & 7);
+}
+
+}  // namespace bhg

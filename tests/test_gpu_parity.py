@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Bars, as written in each test:
+  * tree and moments: bit-exact (same pre-order, levels, skips; FP64 masses
+    and centres of mass identical; delta identical after rounding to binary32);
+  * opening decisions: bit-exact, checked through the per-cell counts of
+    interactions and tests;
+  * potential, binary32 walk: max relative difference 1e-5 per cell; binary64
+    walk: 1e-12 per cell.
+Small meshes are compared cell by cell in full; the 2.0M-cell Maclaurin mesh
+(the benchmark workload, same launch configuration) and the 16.3M-cell cloud
+core are compared on sampled cells, where the oracle computes each one alone.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_1509_07370_gb300 import bhgrav as B  # noqa: E402
+from paper_1509_07370_gb300 import meshgen as mg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+F64_TOL = 1e-12
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+def _solver(prec=B.BH_PREC_F32, crit=B.BH_CRIT_PER_CELL, kahan=True):
+    return B.Solver(precision=prec, criterion=crit, kahan=kahan)
+
+
+def _build(s, mesh, rho, dtype=torch.float64):
+    s.build(mesh.level, mesh.ijk, _cuda(rho.reshape(-1), dtype), mesh.box_lo, mesh.box_len)
+    return s
+
+
+def _oracle(mesh, rho):
+    return O.Tree(mesh.level, mesh.ijk, rho, mesh.box_lo, mesh.box_len)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a, np.float64) / np.asarray(b, np.float64) - 1.0)
+
+
+def _subtree_end(parent):
+    n = len(parent)
+    end = np.arange(1, n + 1)
+    for i in range(n - 1, 0, -1):
+        end[parent[i]] = max(end[parent[i]], end[i])
+    return end
+
+
+MESHES = {}
+
+
+def _mesh(name):
+    if name not in MESHES:
+        if name == "c1":
+            w = mg.uniform_sphere()
+            MESHES[name] = (w.mesh, w.density)
+        elif name == "maclaurin_small":
+            w = mg.maclaurin(base_level=2, extra_levels=2)
+            MESHES[name] = (w.mesh, w.density)
+        elif name == "maclaurin":
+            w = mg.maclaurin()
+            MESHES[name] = (w.mesh, w.density)
+        elif name == "cloud_core":
+            w = mg.cloud_core()
+            MESHES[name] = (w.mesh, w.density)
+        elif name.endswith("_shuffled"):
+            m, r = _mesh(name[: -len("_shuffled")])
+            MESHES[name] = mg.shuffled(m, r, seed=11)
+        else:
+            m = mg.tiny_meshes()[name]
+            MESHES[name] = (m, mg.random_density(m, seed=len(name)))
+    return MESHES[name]
+
+
+TINY = ["one_block", "eight_blocks", "refined_corner", "refined_twice", "diag_refined"]
+
+
+# ------------------------------------------------------------- the tree ---
+@pytest.mark.parametrize("name", TINY + ["c1", "diag_refined_shuffled", "maclaurin_small"])
+def test_tree_and_moments_bit_exact(name):
+    mesh, rho = _mesh(name)
+    s = _build(_solver(), mesh, rho)
+    e = _oracle(mesh, rho).export()
+    nc, nn, ml = s.tree_size()
+    assert nc == mesh.ncells and nn == len(e["M"]) and ml == int(mesh.level.max()) + 3
+    g = {k: v.cpu().numpy() for k, v in s.export_nodes().items()}
+    assert np.array_equal(g["level"], e["level"])
+    assert np.array_equal(g["skip"], _subtree_end(e["parent"]))
+    assert np.array_equal(g["M"], e["M"])
+    assert np.array_equal(g["R"], e["R"])
+    assert np.array_equal(g["delta"], e["delta"].astype(np.float32))
+
+
+def test_density_fp32_input_equals_rounded_fp64_input():
+    mesh, rho = _mesh("refined_corner")
+    r32 = rho.astype(np.float32)
+    a = _build(_solver(), mesh, r32, torch.float32).export_nodes()["M"].cpu().numpy()
+    b = _build(_solver(), mesh, r32.astype(np.float64)).export_nodes()["M"].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------- the decisions ----
+@pytest.mark.parametrize("name", TINY + ["c1", "diag_refined_shuffled"])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 1.0])
+def test_opening_decisions_bit_exact(name, theta):
+    mesh, rho = _mesh(name)
+    s = _build(_solver(), mesh, rho)
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(theta))
+    _, oi, ot = _oracle(mesh, rho).walk(theta)
+    assert np.array_equal(ni, oi) and np.array_equal(nt, ot)
+
+
+@pytest.mark.parametrize("name", ["refined_twice", "c1"])
+def test_paper_mode_decisions_bit_exact(name):
+    mesh, rho = _mesh(name)
+    s = _build(_solver(crit=B.BH_CRIT_WARP_VOTE), mesh, rho)
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+    _, oi, ot = _oracle(mesh, rho).walk_vote(0.6)
+    perm = _vote_to_caller(mesh)
+    assert np.array_equal(ni[perm], oi) and np.array_equal(nt[perm], ot)
+
+
+def _vote_to_caller(mesh):
+    """Caller cell index of each entry of the oracle's brick-ordered output."""
+    lm = O.local_morton_order()
+    b = np.arange(16 * mesh.nblocks)
+    return ((b[:, None] // 16) * 512 + lm[32 * (b[:, None] % 16) + np.arange(32)]).reshape(-1)
+
+
+# -------------------------------------------------------- the potential ---
+@pytest.mark.parametrize("name", TINY + ["c1", "diag_refined_shuffled"])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 1.0])
+def test_potential_f32_matches_oracle_walk(name, theta):
+    mesh, rho = _mesh(name)
+    s = _build(_solver(), mesh, rho)
+    phi = s.potential(theta, G=1.0).cpu().numpy()
+    ref, _, _ = _oracle(mesh, rho).walk(theta)
+    assert _rel(phi, ref).max() <= F32_TOL
+
+
+@pytest.mark.parametrize("name", ["refined_corner", "c1"])
+def test_potential_f64_matches_oracle_walk(name):
+    mesh, rho = _mesh(name)
+    s = _build(_solver(prec=B.BH_PREC_F64), mesh, rho)
+    phi = s.potential(0.5, G=1.0).cpu().numpy()
+    assert phi.dtype == np.float64
+    ref, _, _ = _oracle(mesh, rho).walk(0.5)
+    assert _rel(phi, ref).max() <= F64_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(B.BH_PREC_F32, F32_TOL), (B.BH_PREC_F64, F64_TOL)])
+def test_paper_mode_potential_matches_oracle(prec, tol):
+    mesh, rho = _mesh("c1")
+    s = _build(_solver(prec=prec, crit=B.BH_CRIT_WARP_VOTE), mesh, rho)
+    phi = s.potential(0.6, G=2.0).cpu().numpy()
+    ref, _, _ = _oracle(mesh, rho).walk_vote(0.6, G=2.0)
+    assert _rel(phi[_vote_to_caller(mesh)], ref).max() <= tol
+
+
+def test_theta_to_small_is_direct_sum():
+    mesh, rho = _mesh("refined_corner")
+    s = _build(_solver(prec=B.BH_PREC_F64), mesh, rho)
+    phi = s.potential(1e-6, G=1.0).cpu().numpy()
+    d = _oracle(mesh, rho).direct()
+    assert _rel(phi, d).max() <= F64_TOL
+
+
+def test_box_scaling_and_G():
+    mesh, rho = _mesh("refined_corner")
+    m4 = mg.Mesh(mesh.level, mesh.ijk, box_lo=(-3.0, 5.0, 0.25), box_len=4.0)
+    a = _build(_solver(prec=B.BH_PREC_F64), mesh, rho).potential(0.5, G=1.0).cpu().numpy()
+    b = _build(_solver(prec=B.BH_PREC_F64), m4, rho).potential(0.5, G=3.0).cpu().numpy()
+    assert _rel(b, 48.0 * a).max() <= F64_TOL
+
+
+def test_kahan_sum_not_worse_than_plain():
+    mesh, rho = _mesh("c1")
+    ref, _, _ = _oracle(mesh, rho).walk(0.3)
+    k = _build(_solver(kahan=True), mesh, rho).potential(0.3).cpu().numpy()
+    p = _build(_solver(kahan=False), mesh, rho).potential(0.3).cpu().numpy()
+    assert _rel(k, ref).max() <= F32_TOL
+    assert _rel(k, ref).mean() <= _rel(p, ref).mean()
+
+
+def test_deterministic_and_host_path_identical():
+    mesh, rho = _mesh("refined_twice")
+    s = _build(_solver(), mesh, rho)
+    a = s.potential(0.5).cpu().numpy()
+    b = s.potential(0.5).cpu().numpy()
+    assert np.array_equal(a, b)
+    h = _solver().solve_host(mesh.level, mesh.ijk, rho.reshape(-1).copy(), 0.5)
+    assert np.array_equal(a, h)
+
+
+# ----------------------------------------------------- full-size meshes ---
+def _sample(ncells, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(np.concatenate([rng.choice(ncells, k, replace=False),
+                                   [0, ncells - 1]]))
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+def test_maclaurin_full_size_sampled(theta):
+    """The benchmark workload (2,039,808 cells), benchmark launch config."""
+    mesh, rho = _mesh("maclaurin")
+    s = _build(_solver(), mesh, rho)
+    phi = s.potential(theta).cpu().numpy()
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(theta))
+    t = _oracle(mesh, rho)
+    tg = _sample(mesh.ncells, 3000, seed=int(theta * 100))
+    ref, oi, ot = t.walk(theta, targets=tg)
+    assert _rel(phi[tg], ref).max() <= F32_TOL
+    assert np.array_equal(ni[tg], oi) and np.array_equal(nt[tg], ot)
+    assert np.all(np.isfinite(phi)) and np.all(phi < 0)
+
+
+def test_cloud_core_full_size_sampled():
+    mesh, rho = _mesh("cloud_core")
+    s = _build(_solver(), mesh, rho.astype(np.float32), torch.float32)
+    phi = s.potential(0.5).cpu().numpy()
+    t = _oracle(mesh, rho.astype(np.float32).astype(np.float64))
+    tg = _sample(mesh.ncells, 1500, seed=5)
+    ref, _, _ = t.walk(0.5, targets=tg)
+    assert _rel(phi[tg], ref).max() <= F32_TOL
+    assert np.all(np.isfinite(phi)) and np.all(phi < 0)
+
+
+# --------------------------------------------------------------- errors ---
+def test_errors_reported():
+    mesh, rho = _mesh("eight_blocks")
+    s = _solver()
+    with pytest.raises(B.BHError) as e:
+        s.potential(0.5)                                   # no tree yet
+    assert e.value.status == B.BH_ERR_STATE
+    d = _cuda(rho.reshape(-1))
+    with pytest.raises(B.BHError) as e:                    # gap: 7 of 8 blocks
+        s.build(mesh.level[:7], mesh.ijk[:7], d[: 7 * 512])
+    assert e.value.status == B.BH_ERR_GEOMETRY
+    ij = mesh.ijk.copy()
+    ij[3] = ij[2]                                          # duplicate + gap
+    with pytest.raises(B.BHError) as e:
+        s.build(mesh.level, ij, d)
+    assert e.value.status == B.BH_ERR_GEOMETRY
+    lv = mesh.level.copy()
+    lv[0] = 2                                              # block moved to a finer level
+    with pytest.raises(B.BHError) as e:
+        s.build(lv, mesh.ijk, d)
+    assert e.value.status == B.BH_ERR_GEOMETRY
+    bad = d.clone()
+    bad[100] = -1.0
+    with pytest.raises(B.BHError) as e:
+        s.build(mesh.level, mesh.ijk, bad)
+    assert e.value.status == B.BH_ERR_ARG
+    bad[100] = float("nan")
+    with pytest.raises(B.BHError):
+        s.build(mesh.level, mesh.ijk, bad)
+    with pytest.raises(B.BHError) as e:                    # failed build leaves no tree
+        s.potential(0.5)
+    assert e.value.status == B.BH_ERR_STATE
+    s.build(mesh.level, mesh.ijk, d)
+    for th in (0.0, -0.5, 1.5, float("nan")):
+        with pytest.raises(B.BHError) as e:
+            s.potential(th)
+        assert e.value.status == B.BH_ERR_ARG
+    with pytest.raises(B.BHError) as e:
+        s.potential(0.5, G=float("inf"))
+    assert e.value.status == B.BH_ERR_ARG
+    assert np.all(np.isfinite(s.potential(0.5).cpu().numpy()))   # still usable
