@@ -108,7 +108,7 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
  * the same decisions:
  *   s  = fl(fl(l * fl(1/theta)) + fl(delta)),  s2 = fl(s * s)
  *   dx = fl(t.x - fl(R.x)), dy, dz likewise
- *   d2 = fma(dz, dz, fma(dy, dy, fl(dx * dx)));  accept iff d2 > s2.
+ *   d2 = fma(dx, dx, fma(dz, dz, fl(dy * dy)));  accept iff d2 > s2.
  * The interaction sum is binary32 with Kahan compensation or binary64 per
  * the context options.
  * Errors: BH_ERR_STATE (no tree), BH_ERR_ARG, BH_ERR_CUDA. */

@@ -41,7 +41,7 @@
  *       s2  = fl(s*s)
  *       P   = (float)R,  t = (float)u_t (exact: cell centres are dyadic)
  *       dx  = fl(t.x - P.x), ...
- *       d2  = fma(dz,dz, fma(dy,dy, fl(dx*dx)))
+ *       d2  = fma(dx,dx, fma(dz,dz, fl(dy*dy)))
  *       accept  <=>  d2 > s2
  *     This file is compiled with -ffp-contract=off so that every fl() above
  *     is a single rounding.
@@ -329,7 +329,7 @@ static int accept_f32(const onode *n, const float t[3], float inv_theta) {
   float dx = t[0] - (float)n->R[0];
   float dy = t[1] - (float)n->R[1];
   float dz = t[2] - (float)n->R[2];
-  float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  float d2 = fmaf(dx, dx, fmaf(dz, dz, dy * dy));
   return d2 > s2;
 }
 
