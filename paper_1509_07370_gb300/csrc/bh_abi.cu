@@ -59,8 +59,7 @@ void free_blocks(bhg::Tree &t) {
 
 void free_nodes(bhg::Tree &t) {
   release(t.d_mom);
-  release(t.d_rec0);
-  release(t.d_rec1);
+  release(t.d_rec);
   release(t.d_aux);
   release(t.d_lvl);
   t.node_cap = 0;
@@ -91,8 +90,7 @@ bh_status ensure_nodes(bh_ctx *ctx, int64_t n_nodes) {
   free_nodes(t);
   const size_t n = (size_t)n_nodes;
   BH_CUDA(cudaMalloc(&t.d_mom, n * sizeof(double4_32a)));
-  BH_CUDA(cudaMalloc(&t.d_rec0, n * sizeof(float4)));
-  BH_CUDA(cudaMalloc(&t.d_rec1, n * sizeof(float2)));
+  BH_CUDA(cudaMalloc(&t.d_rec, n * sizeof(bhg::WalkRec)));
   BH_CUDA(cudaMalloc(&t.d_aux, n * sizeof(float2)));
   BH_CUDA(cudaMalloc(&t.d_lvl, n * sizeof(uint8_t)));
   t.node_cap = n_nodes;
@@ -191,13 +189,13 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
                                      t.d_count, t.d_blk, t.d_orig, t.d_flags));
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
   BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
-                                t.d_rec1, t.d_aux, t.d_lvl, t.d_flags));
+                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags));
   BH_CUDA(bhg::launch_blocks(s, nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
-                             density_is_fp64, box_len, n_nodes, t.d_mom, t.d_rec0, t.d_rec1,
-                             t.d_aux, t.d_lvl, t.d_flags));
+                             density_is_fp64, box_len, n_nodes, t.d_mom, t.d_rec, t.d_aux,
+                             t.d_lvl, t.d_flags));
   for (int lev = max_level - 1; lev >= 0; --lev)
     BH_CUDA(bhg::launch_top_moments(s, nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
-                                    n_nodes, t.d_mom, t.d_rec0, t.d_rec1, t.d_aux, t.d_flags));
+                                    n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_flags));
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
   const unsigned e = t.h_flags[0];
@@ -229,7 +227,7 @@ static bh_status prepare(bh_ctx *ctx, double theta) {
   if (st != BH_OK) return st;
   const float inv_theta = (float)(1.0 / theta);
   if (inv_theta != t.s2_inv_theta) {
-    BH_CUDA(bhg::launch_prepare_s2(ctx->stream, t.n_nodes, t.d_aux, t.d_rec1, inv_theta));
+    BH_CUDA(bhg::launch_prepare_s2(ctx->stream, t.n_nodes, t.d_aux, t.d_rec, inv_theta));
     t.s2_inv_theta = inv_theta;
   }
   return BH_OK;
@@ -238,26 +236,28 @@ static bh_status prepare(bh_ctx *ctx, double theta) {
 bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
+  if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
   if (!out) return fail(ctx, BH_ERR_ARG, "bh_potential: out is null");
   if (!std::isfinite(G)) return fail(ctx, BH_ERR_ARG, "bh_potential: G must be finite");
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
   const double scale = -G / t.L;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec0, t.d_rec1, t.d_mom,
-                           t.d_blk, t.d_orig, scale, out, nullptr, nullptr));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_blk,
+                           t.d_orig, scale, out, nullptr, nullptr));
   return BH_OK;
 }
 
 bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
+  if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
   if (!n_int || !n_test) return fail(ctx, BH_ERR_ARG, "bh_walk_counts: null output");
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec0, t.d_rec1, t.d_mom,
-                           t.d_blk, t.d_orig, 0.0, nullptr, n_int, n_test));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_blk,
+                           t.d_orig, 0.0, nullptr, n_int, n_test));
   return BH_OK;
 }
 
@@ -271,7 +271,7 @@ bh_status bh_tree_size(const bh_ctx *ctx, int64_t *n_cells, int64_t *n_nodes, in
 }
 
 namespace {
-__global__ void k_export(int64_t n, const double4_32a *mom, const float2 *rec1, const float2 *aux,
+__global__ void k_export(int64_t n, const double4_32a *mom, const bhg::WalkRec *rec, const float2 *aux,
                          const uint8_t *lvl, double *M, double *R, float *delta, int32_t *skip,
                          int32_t *level) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,7 +284,7 @@ __global__ void k_export(int64_t n, const double4_32a *mom, const float2 *rec1, 
     R[3 * i + 2] = m.z;
   }
   if (delta) delta[i] = aux[i].y;
-  if (skip) skip[i] = __float_as_int(rec1[i].y);
+  if (skip) skip[i] = (int32_t)rec[i].skip;
   if (level) level[i] = lvl[i];
 }
 }  // namespace
@@ -299,7 +299,7 @@ bh_status bh_export_nodes(const bh_ctx *cctx, double *M, double *R, float *delta
   const bhg::Tree &t = ctx->tree;
   const int threads = 256;
   k_export<<<(unsigned)((t.n_nodes + threads - 1) / threads), threads, 0, ctx->stream>>>(
-      t.n_nodes, t.d_mom, t.d_rec1, t.d_aux, t.d_lvl, M, R, delta, skip, level);
+      t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl, M, R, delta, skip, level);
   BH_CUDA(cudaGetLastError());
   return BH_OK;
 }

@@ -202,7 +202,7 @@ __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023,
 __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
                             const int4 *__restrict__ blk, const int *__restrict__ count,
                             const int *__restrict__ prestart, int64_t n_nodes,
-                            float2 *__restrict__ rec1, float2 *__restrict__ aux,
+                            WalkRec *__restrict__ rec, float2 *__restrict__ aux,
                             uint8_t *__restrict__ lvl, unsigned *flags) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
@@ -225,7 +225,7 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
       atomicOr(flags, kErrIndex);
       continue;
     }
-    rec1[id] = make_float2(0.0f, __int_as_float((int)skip));
+    rec[id].skip = (unsigned)skip;
     aux[id] = make_float2(pow2f(-k), 0.0f);
     lvl[id] = (uint8_t)k;
   }
@@ -261,13 +261,23 @@ __device__ __forceinline__ Moment finish(double M, double Sx, double Sy, double 
   return r;
 }
 
+__device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m,
+                                            int64_t skip) {
+  WalkRec w;
+  w.px = w.px2 = __double2float_rn(x);
+  w.py = __double2float_rn(y);
+  w.pz = __double2float_rn(z);
+  w.m = w.m2 = __double2float_rn(m);
+  w.s2 = 0.0f;
+  w.skip = (unsigned)skip;
+  return w;
+}
+
 __device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int level,
-                                               const Moment &r, double4_32a *mom, float4 *rec0,
-                                               float2 *rec1, float2 *aux, uint8_t *lvl) {
+                                               const Moment &r, double4_32a *mom, WalkRec *rec,
+                                               float2 *aux, uint8_t *lvl) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
-  rec0[id] = make_float4(__double2float_rn(r.x), __double2float_rn(r.y), __double2float_rn(r.z),
-                         __double2float_rn(r.m));
-  rec1[id] = make_float2(0.0f, __int_as_float((int)skip));
+  rec[id] = make_rec(r.x, r.y, r.z, r.m, skip);
   aux[id] = make_float2(pow2f(-level), __double2float_rn(r.delta));
   if (lvl) lvl[id] = (uint8_t)level;
 }
@@ -278,8 +288,8 @@ template <typename T>
 __global__ void __launch_bounds__(kBlockThreads)
     k_blocks(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
              const int *__restrict__ count, const int *__restrict__ prestart,
-             const T *__restrict__ density, double L, int64_t n_nodes, double4_32a *__restrict__ mom,
-             float4 *__restrict__ rec0, float2 *__restrict__ rec1, float2 *__restrict__ aux,
+             const T *__restrict__ density, double L, int64_t n_nodes,
+             double4_32a *__restrict__ mom, WalkRec *__restrict__ rec, float2 *__restrict__ aux,
              uint8_t *__restrict__ lvl, unsigned *flags) {
   __shared__ double cm[512], cxs[512], cys[512], czs[512];  // cells, local Morton order
   __shared__ double gm[64], gx[64], gy[64], gz[64];         // level lb+2 nodes
@@ -315,9 +325,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     czs[m] = uz;
     const int64_t id = root + cell_offset(m);
     mom[id] = make_double4_32a(ux, uy, uz, mass);
-    rec0[id] = make_float4(__double2float_rn(ux), __double2float_rn(uy), __double2float_rn(uz),
-                           __double2float_rn(mass));
-    rec1[id] = make_float2(0.0f, __int_as_float((int)(id + 1)));
+    rec[id] = make_rec(ux, uy, uz, mass, id + 1);
     aux[id] = make_float2(0.0f, 0.0f);
     lvl[id] = (uint8_t)lc;
   }
@@ -340,7 +348,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     gy[q] = r.y;
     gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec0, rec1, aux, lvl);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl);
   }
   __syncthreads();
   if (t < 8) {  // nodes at level lb+1
@@ -359,7 +367,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     py[c] = r.y;
     pz[c] = r.z;
     const int64_t id = root + 1 + 73 * c;
-    store_internal(id, id + 73, lb + 1, r, mom, rec0, rec1, aux, lvl);
+    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl);
   }
   __syncthreads();
   if (t == 0) {  // the block itself
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 #pragma unroll
     for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec0, rec1, aux, lvl);
+    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl);
   }
 }
 
@@ -380,9 +388,8 @@ __global__ void __launch_bounds__(kBlockThreads)
 __global__ void k_top_moments(int nb, int level, const unsigned long long *__restrict__ key,
                               const int4 *__restrict__ blk, const int *__restrict__ count,
                               const int *__restrict__ prestart, int64_t n_nodes,
-                              double4_32a *__restrict__ mom, float4 *__restrict__ rec0,
-                              float2 *__restrict__ rec1, float2 *__restrict__ aux,
-                              unsigned *flags) {
+                              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
+                              float2 *__restrict__ aux, unsigned *flags) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int cnt = count[p];
@@ -405,11 +412,11 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
     }
     const double4_32a ch = mom[c];
     accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
-    c = __float_as_int(rec1[c].y);
+    c = rec[c].skip;
   }
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-  const int64_t skip = __float_as_int(rec1[id].y);
-  store_internal(id, skip, level, r, mom, rec0, rec1, aux, nullptr);
+  const int64_t skip = rec[id].skip;
+  store_internal(id, skip, level, r, mom, rec, aux, nullptr);
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -444,9 +451,9 @@ cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *
 
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
-                             int64_t n_nodes, float2 *rec1, float2 *aux, uint8_t *lvl,
+                             int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
                              unsigned *flags) {
-  k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec1,
+  k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec,
                                                  aux, lvl, flags);
   return cudaGetLastError();
 }
@@ -454,25 +461,24 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
                           int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          float4 *rec0, float2 *rec1, float2 *aux, uint8_t *lvl,
-                          unsigned *flags) {
+                          WalkRec *rec, float2 *aux, uint8_t *lvl, unsigned *flags) {
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                    (const double *)density, L, n_nodes, mom,
-                                                   rec0, rec1, aux, lvl, flags);
+                                                   rec, aux, lvl, flags);
   else
     k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                  (const float *)density, L, n_nodes, mom, rec0,
-                                                  rec1, aux, lvl, flags);
+                                                  (const float *)density, L, n_nodes, mom, rec,
+                                                  aux, lvl, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
-                               int64_t n_nodes, double4_32a *mom, float4 *rec0, float2 *rec1,
-                               float2 *aux, unsigned *flags) {
+                               int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
+                               unsigned *flags) {
   k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
-                                                   n_nodes, mom, rec0, rec1, aux, flags);
+                                                   n_nodes, mom, rec, aux, flags);
   return cudaGetLastError();
 }
 

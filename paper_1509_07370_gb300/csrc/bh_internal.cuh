@@ -3,11 +3,14 @@
 // Node storage (all arrays indexed by the node's pre-order position: a
 // depth-first visit of the octree in octant order o = ox + 2 oy + 4 oz, so a
 // node's first child sits right after it and its subtree is contiguous):
-//   mom  double4_32a {Rx, Ry, Rz, M}  FP64 centre of mass (box units) and mass
-//   rec0 float4  {Px, Py, Pz, M}  the same rounded to binary32 (walk record)
-//   rec1 float2  {s2, skip}       squared opening radius for the current
-//                                 theta (0 for cells) and, as raw int bits,
-//                                 the index of the first node after the subtree
+//   mom  double4 {Rx, Ry, Rz, M}  FP64 centre of mass (box units) and mass
+//   rec  WalkRec (32 bytes)       what the walk reads, in one 256-bit load:
+//                                 the centre of mass and mass rounded to
+//                                 binary32 (Px and M stored twice so that they
+//                                 form ready-made pairs for packed f32x2
+//                                 arithmetic), the squared opening radius s2
+//                                 for the current theta (0 for cells), and the
+//                                 index of the first node after the subtree
 //   aux  float2  {l, delta}       node side and |R - centre| in binary32
 //                                 (both 0 for cells)
 //   lvl  uint8                    node level
@@ -36,6 +39,15 @@ enum : unsigned {
   kErrIndex = 16u,       // a node index fell outside the allocation
 };
 
+struct __align__(32) WalkRec {
+  float px, px2;   // Px twice
+  float py, pz;
+  float m, m2;     // M twice
+  float s2;        // (l/theta + delta)^2 in binary32; 0 for cells
+  unsigned skip;   // first node after this node's subtree
+};
+static_assert(sizeof(WalkRec) == 32, "walk record must be 32 bytes");
+
 struct Tree {
   // block arrays (capacity nb_cap)
   int *d_level = nullptr, *d_ijk = nullptr;
@@ -49,8 +61,7 @@ struct Tree {
   int64_t nb_cap = 0;
   // node arrays (capacity node_cap)
   double4_32a *d_mom = nullptr;
-  float4 *d_rec0 = nullptr;
-  float2 *d_rec1 = nullptr;
+  WalkRec *d_rec = nullptr;
   float2 *d_aux = nullptr;
   uint8_t *d_lvl = nullptr;
   int64_t node_cap = 0;
@@ -80,26 +91,25 @@ cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *
                                  unsigned *flags);
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
-                             int64_t n_nodes, float2 *rec1, float2 *aux, uint8_t *lvl,
+                             int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
                              unsigned *flags);
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
                           int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          float4 *rec0, float2 *rec1, float2 *aux, uint8_t *lvl,
-                          unsigned *flags);
+                          WalkRec *rec, float2 *aux, uint8_t *lvl, unsigned *flags);
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
-                               int64_t n_nodes, double4_32a *mom, float4 *rec0, float2 *rec1,
-                               float2 *aux, unsigned *flags);
+                               int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
+                               unsigned *flags);
 
 // ---- walk kernels (bh_walk.cu) ---------------------------------------------
-cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, float2 *rec1,
+cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
                               float inv_theta);
 // out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const float4 *rec0, const float2 *rec1, const double4_32a *mom,
-                        const int4 *blk, const int *orig, double scale, void *out,
-                        int32_t *n_int, int32_t *n_test);
+                        const WalkRec *rec, const double4_32a *mom, const int4 *blk,
+                        const int *orig, double scale, void *out, int32_t *n_int,
+                        int32_t *n_test);
 
 // ---- small device helpers ---------------------------------------------------
 // Spread the low 21 bits of v so bit b lands at bit 3b.

@@ -1,29 +1,38 @@
 // The Barnes-Hut walk: potential at every cell centre (Sec. 3.3).
 //
-// One warp owns one brick of 32 neighbouring cells of a block (a 4x4x2 set,
-// local Morton indices 32q .. 32q+31), as the paper groups its cells
-// (Sec. 3.1.1, Sec. 3.3).  The paper walks with a shared-memory stack pushed
-// by lane 0 and an all() vote on the opening test.  This walk needs no stack:
+// Traversal.  The paper walks with a shared-memory stack pushed by lane 0 and
+// an all() vote on the opening test (Sec. 3.3).  This walk needs no stack:
 // nodes are stored in pre-order, so a node's first child is the next node and
-// its subtree ends at its skip index.  Each lane keeps `next`, the first node
-// it still has to visit (0 = the root at the start).  At every step the warp
-// takes the smallest `next` over its lanes (one __reduce_min_sync), all lanes
-// load that node (one broadcast load), and the lanes whose `next` equals it
-// apply the opening test of Eq. 4:
+// its subtree ends at its skip index.  Every target cell keeps `next`, the
+// first node it still has to visit (0 = the root at the start).  At each step
+// the warp takes the smallest `next` over its lanes (one __reduce_min_sync),
+// all lanes load that node (one broadcast 256-bit load), and the targets whose
+// `next` equals it apply the opening test of Eq. 4:
 //   accepted -> add M / d, next = skip (the whole subtree is done)
 //   opened   -> next = node + 1 (descend into the first child)
-// Cells carry s2 = 0, so the test accepts every other cell (d2 > 0) and
-// rejects only the lane's own cell (d2 = 0), which contributes nothing; for a
-// cell node + 1 equals its skip, so no special case is needed.  Every lane
-// thus visits exactly the nodes of its own recursive walk, in pre-order, and
-// the result is the per-cell potential of the recursive definition; lanes
-// whose `next` is further ahead simply wait (masked) for the warp to get
-// there.  Each lane's `next` only grows, so the loop ends after at most
-// n_nodes steps.  With the warp vote (paper mode) all lanes share `next`.
+// Cells carry s2 = 0: the test accepts every other cell (d2 > 0) and rejects
+// only the target's own cell (d2 = 0), which then adds nothing; for a cell
+// node + 1 is its skip, so no special case is needed.  Each target thus
+// visits exactly the nodes of its own recursive walk, in pre-order, and gets
+// the per-cell result of the recursive definition; targets whose `next` lies
+// further ahead wait (masked) for the warp to get there.  `next` only grows,
+// so a walk ends after at most n_nodes steps.  With the warp vote (paper mode)
+// all lanes share `next`.
 //
-// The opening test is evaluated in binary32 with the exact operation order
-// stated in the public header; interactions use the same d2 (F32 mode, Kahan
-// sum) or recompute d in binary64 from the FP64 moments (F64 mode).
+// Work layout.
+//  * Per-cell binary32 walk (the default, k_walk_pair): one warp per 4x4x4
+//    octant of a block (64 cells, local Morton indices 64o .. 64o+63); lane l
+//    owns the two x-neighbours 64o+2l and 64o+2l+1.  They share ty, tz and
+//    so dy, dz; their dx, d2, 1/d products and Kahan sums run as packed
+//    f32x2 operations (two binary32 results per instruction, each rounded as
+//    its scalar counterpart).  A CTA of 8 warps is one whole block.
+//  * binary64 interactions and the paper's warp vote (k_walk_scalar): one
+//    warp per 32-cell brick (4x4x2, local Morton 32q .. 32q+31), one target
+//    per lane, as the paper groups its cells (Sec. 3.1.1, Sec. 3.3).
+//
+// The opening test is evaluated in binary32 with the operation order stated
+// in the public header; the interaction uses the same d2 (binary32, Kahan
+// sum) or recomputes d in binary64 from the FP64 moments.
 #include "bh_internal.cuh"
 
 namespace bhg {
@@ -32,27 +41,156 @@ namespace {
 constexpr int kWalkThreads = 256;
 constexpr int kWarpsPerCta = kWalkThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
+typedef unsigned long long u64;
 
-__global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, float2 *__restrict__ rec1,
+__global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, WalkRec *__restrict__ rec,
                              float inv_theta) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float2 a = aux[i];
-  float2 r = rec1[i];
   const float s = __fadd_rn(__fmul_rn(a.x, inv_theta), a.y);  // l/theta + delta
-  r.x = __fmul_rn(s, s);
-  rec1[i] = r;
+  rec[i].s2 = __fmul_rn(s, s);
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
+// ---- packed binary32 pairs and raw loads (inline PTX) -----------------------
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// 1/sqrt(x) on the special-function unit.  Only called where the value is
+// used for x >= 2^-44 (an accepted node or another cell), so flushing
+// subnormal inputs changes nothing.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// One 32-byte walk record as four 64-bit lanes:
+//   q0 = {Px, Px}, q1 = {Py, Pz}, q2 = {M, M}, q3 = {s2, skip}
+__device__ __forceinline__ void load_rec(const WalkRec *p, u64 &q0, u64 &q1, u64 &q2, u64 &q3) {
+  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+      : "l"(p));
+}
+
+// ---- per-cell binary32 walk, two x-neighbour targets per lane ---------------
+template <bool KAHAN, bool COUNTS>
+__global__ void __launch_bounds__(kWalkThreads)
+    k_walk_pair(int nwarps, unsigned n_nodes, const WalkRec *__restrict__ rec,
+                const int4 *__restrict__ blk, const int *__restrict__ orig, float scale,
+                float *__restrict__ out, int32_t *__restrict__ n_int,
+                int32_t *__restrict__ n_test) {
+  const int warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= nwarps) return;  // whole warps only
+  const int p = warp >> 3;     // sorted block
+  const int ma = ((warp & 7) << 6) | (lane << 1);  // local Morton index, even: x bit 0
+  const int4 B = blk[p];
+  const int cx = (int)compact3(ma), cy = (int)compact3(ma >> 1), cz = (int)compact3(ma >> 2);
+  const int lc = B.x + 3;
+  // cell centres in box units, exact in binary32: (2 i + 1) * 2^-(lc+1)
+  const float hh = pow2f(-(lc + 1));
+  const float txa = __fmul_rn((float)(2 * (8 * B.y + cx) + 1), hh);
+  const float txb = __fmul_rn((float)(2 * (8 * B.y + cx) + 3), hh);
+  const float ty = __fmul_rn((float)(2 * (8 * B.z + cy) + 1), hh);
+  const float tz = __fmul_rn((float)(2 * (8 * B.w + cz) + 1), hh);
+  const u64 tx2 = pk(txa, txb);
+
+  u64 sum = 0ull, comp = 0ull;  // (+0.0f, +0.0f) pairs
+  int nia = 0, nib = 0, nta = 0, ntb = 0;
+  unsigned next_a = 0, next_b = 0;
+  unsigned node = 0;
+  while (node < n_nodes) {
+    u64 q0, q1, q2, q3;
+    load_rec(rec + node, q0, q1, q2, q3);
+    float py, pz, s2, skf;
+    upk(q1, py, pz);
+    upk(q3, s2, skf);
+    const unsigned skip = __float_as_uint(skf);
+    // d2 = fma(dx, dx, fma(dz, dz, dy*dy)): the (dy, dz) part is shared
+    const u64 dx2 = sub2(tx2, q0);
+    const float dy = __fsub_rn(ty, py);
+    const float dz = __fsub_rn(tz, pz);
+    const float h = __fmaf_rn(dz, dz, __fmul_rn(dy, dy));
+    float d2a, d2b;
+    upk(fma2(dx2, dx2, pk(h, h)), d2a, d2b);
+    const bool mine_a = next_a == node, mine_b = next_b == node;
+    const bool take_a = mine_a && d2a > s2;
+    const bool take_b = mine_b && d2b > s2;
+    const unsigned n1 = node + 1;
+    next_a = max(next_a, take_a ? skip : n1);
+    next_b = max(next_b, take_b ? skip : n1);
+    if (COUNTS) {
+      const bool internal = s2 > 0.0f;
+      nia += take_a;
+      nib += take_b;
+      nta += mine_a && internal;
+      ntb += mine_b && internal;
+    } else {
+      float ra = rsqrt_approx(d2a), rb = rsqrt_approx(d2b);
+      ra = take_a ? ra : 0.0f;
+      rb = take_b ? rb : 0.0f;
+      const u64 term = mul2(q2, pk(ra, rb));
+      if (KAHAN) {
+        const u64 y = sub2(term, comp);
+        const u64 t = add2(sum, y);
+        comp = sub2(sub2(t, sum), y);
+        sum = t;
+      } else {
+        sum = add2(sum, term);
+      }
+    }
+    node = __reduce_min_sync(kFull, min(next_a, next_b));
+  }
+  const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx;
+  if (COUNTS) {
+    n_int[cell] = nia;
+    n_int[cell + 1] = nib;
+    n_test[cell] = nta;
+    n_test[cell + 1] = ntb;
+  } else {
+    if (KAHAN) sum = sub2(sum, comp);
+    float sa, sb;
+    upk(sum, sa, sb);
+    out[cell] = __fmul_rn(sa, scale);
+    out[cell + 1] = __fmul_rn(sb, scale);
+  }
+}
+
+// ---- one target per lane: binary64 interactions and/or the warp vote --------
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS>
 __global__ void __launch_bounds__(kWalkThreads)
-    k_walk(int nbricks, unsigned n_nodes, const float4 *__restrict__ rec0,
-           const float2 *__restrict__ rec1, const double4_32a *__restrict__ mom,
-           const int4 *__restrict__ blk, const int *__restrict__ orig, float scale_f,
-           double scale_d, void *__restrict__ out, int32_t *__restrict__ n_int,
-           int32_t *__restrict__ n_test) {
+    k_walk_scalar(int nbricks, unsigned n_nodes, const WalkRec *__restrict__ rec,
+                  const double4_32a *__restrict__ mom, const int4 *__restrict__ blk,
+                  const int *__restrict__ orig, float scale_f, double scale_d,
+                  void *__restrict__ out, int32_t *__restrict__ n_int,
+                  int32_t *__restrict__ n_test) {
   const int warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= nbricks) return;  // whole warps only
@@ -61,63 +199,63 @@ __global__ void __launch_bounds__(kWalkThreads)
   const int4 B = blk[p];
   const int cx = (int)compact3(m), cy = (int)compact3(m >> 1), cz = (int)compact3(m >> 2);
   const int lc = B.x + 3;
-  // cell centre in box units, exact in binary32: (2 i + 1) * 2^-(lc+1)
   const float hh = pow2f(-(lc + 1));
   const float tx = __fmul_rn((float)(2 * (8 * B.y + cx) + 1), hh);
   const float ty = __fmul_rn((float)(2 * (8 * B.z + cy) + 1), hh);
   const float tz = __fmul_rn((float)(2 * (8 * B.w + cz) + 1), hh);
-  double txd = 0.0, tyd = 0.0, tzd = 0.0;
-  if (F64) {
-    txd = (double)tx;
-    tyd = (double)ty;
-    tzd = (double)tz;
-  }
 
   float sum = 0.0f, comp = 0.0f;
   double sumd = 0.0;
   int ni = 0, nt = 0;
   unsigned next = 0;
-  while (true) {
-    const unsigned node = VOTE ? next : __reduce_min_sync(kFull, next);
-    if (node >= n_nodes) break;
-    const float4 a = __ldg(&rec0[node]);
-    const float2 r = __ldg(&rec1[node]);
-    const float dx = __fsub_rn(tx, a.x);
-    const float dy = __fsub_rn(ty, a.y);
-    const float dz = __fsub_rn(tz, a.z);
-    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const bool internal = r.x > 0.0f;
-    bool take;
-    bool mine = true;
+  unsigned node = 0;
+  while (node < n_nodes) {
+    u64 q0, q1, q2, q3;
+    load_rec(rec + node, q0, q1, q2, q3);
+    float px, px2, py, pz, mf, mf2, s2, skf;
+    upk(q0, px, px2);
+    upk(q1, py, pz);
+    upk(q2, mf, mf2);
+    upk(q3, s2, skf);
+    const unsigned skip = __float_as_uint(skf);
+    const float dx = __fsub_rn(tx, px);
+    const float dy = __fsub_rn(ty, py);
+    const float dz = __fsub_rn(tz, pz);
+    const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dz, dz, __fmul_rn(dy, dy)));
+    const bool internal = s2 > 0.0f;
+    bool mine = true, take;
     if (VOTE) {
-      const bool acc = d2 > r.x;
+      const bool acc = d2 > s2;
       take = internal ? (__all_sync(kFull, acc) != 0) : acc;
-      next = (internal && !take) ? node + 1 : __float_as_uint(r.y);
+      next = (internal && !take) ? node + 1 : skip;
     } else {
-      mine = (next == node);
-      take = mine && (d2 > r.x);
-      if (mine) next = take ? __float_as_uint(r.y) : node + 1;
+      mine = next == node;
+      take = mine && d2 > s2;
+      next = max(next, take ? skip : node + 1);
     }
     if (COUNTS) {
       nt += (mine && internal) ? 1 : 0;
       ni += take ? 1 : 0;
-    } else if (take) {
-      if (F64) {
+    } else if (F64) {
+      if (take) {
         const double4_32a md = mom[node];
-        const double ex = txd - md.x, ey = tyd - md.y, ez = tzd - md.z;
+        const double ex = (double)tx - md.x, ey = (double)ty - md.y, ez = (double)tz - md.z;
         sumd += md.w / sqrt(ex * ex + ey * ey + ez * ez);
+      }
+    } else {
+      float r = rsqrt_approx(d2);
+      r = take ? r : 0.0f;
+      const float term = __fmul_rn(mf, r);
+      if (KAHAN) {
+        const float y = __fsub_rn(term, comp);
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
       } else {
-        const float term = __fmul_rn(a.w, rsqrtf(d2));
-        if (KAHAN) {
-          const float y = __fsub_rn(term, comp);
-          const float s = __fadd_rn(sum, y);
-          comp = __fsub_rn(__fsub_rn(s, sum), y);
-          sum = s;
-        } else {
-          sum = __fadd_rn(sum, term);
-        }
+        sum = __fadd_rn(sum, term);
       }
     }
+    node = VOTE ? next : __reduce_min_sync(kFull, next);
   }
   const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx;
   if (COUNTS) {
@@ -131,55 +269,63 @@ __global__ void __launch_bounds__(kWalkThreads)
   }
 }
 
+template <bool KAHAN, bool COUNTS>
+cudaError_t go_pair(cudaStream_t s, int nb, unsigned n, const WalkRec *rec, const int4 *blk,
+                    const int *orig, double scale, void *out, int32_t *ni, int32_t *nt) {
+  const int nwarps = nb * 8;
+  const int grid = (nwarps + kWarpsPerCta - 1) / kWarpsPerCta;
+  k_walk_pair<KAHAN, COUNTS><<<grid, kWalkThreads, 0, s>>>(nwarps, n, rec, blk, orig,
+                                                          (float)scale, (float *)out, ni, nt);
+  return cudaGetLastError();
+}
+
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS>
-cudaError_t go(cudaStream_t s, int nbricks, unsigned n, const float4 *rec0, const float2 *rec1,
-               const double4_32a *mom, const int4 *blk, const int *orig, double scale, void *out,
-               int32_t *ni, int32_t *nt) {
+cudaError_t go_scalar(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
+                      const double4_32a *mom, const int4 *blk, const int *orig, double scale,
+                      void *out, int32_t *ni, int32_t *nt) {
+  const int nbricks = nb * 16;
   const int grid = (nbricks + kWarpsPerCta - 1) / kWarpsPerCta;
-  k_walk<F64, VOTE, KAHAN, COUNTS><<<grid, kWalkThreads, 0, s>>>(
-      nbricks, n, rec0, rec1, mom, blk, orig, (float)scale, scale, out, ni, nt);
+  k_walk_scalar<F64, VOTE, KAHAN, COUNTS><<<grid, kWalkThreads, 0, s>>>(
+      nbricks, n, rec, mom, blk, orig, (float)scale, scale, out, ni, nt);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, float2 *rec1,
+cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
                               float inv_theta) {
   const int threads = 256;
   const int64_t grid = (n_nodes + threads - 1) / threads;
-  k_prepare_s2<<<(unsigned)grid, threads, 0, s>>>(n_nodes, aux, rec1, inv_theta);
+  k_prepare_s2<<<(unsigned)grid, threads, 0, s>>>(n_nodes, aux, rec, inv_theta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const float4 *rec0, const float2 *rec1, const double4_32a *mom,
-                        const int4 *blk, const int *orig, double scale, void *out,
-                        int32_t *n_int, int32_t *n_test) {
-  const int nbricks = nb * 16;
+                        const WalkRec *rec, const double4_32a *mom, const int4 *blk,
+                        const int *orig, double scale, void *out, int32_t *n_int,
+                        int32_t *n_test) {
   const unsigned n = (unsigned)n_nodes;
   const bool vote = opt.criterion == BH_CRIT_WARP_VOTE;
-  if (n_int) {
-    return vote ? go<false, true, false, true>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                               out, n_int, n_test)
-                : go<false, false, false, true>(s, nbricks, n, rec0, rec1, mom, blk, orig,
-                                                scale, out, n_int, n_test);
+  if (n_int) {  // counting walk: same decisions as the walk of these options
+    return vote ? go_scalar<false, true, false, true>(s, nb, n, rec, mom, blk, orig, scale, out,
+                                                      n_int, n_test)
+                : go_pair<false, true>(s, nb, n, rec, blk, orig, scale, out, n_int, n_test);
   }
   if (opt.precision == BH_PREC_F64) {
-    return vote ? go<true, true, false, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                               out, nullptr, nullptr)
-                : go<true, false, false, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                                out, nullptr, nullptr);
+    return vote ? go_scalar<true, true, false, false>(s, nb, n, rec, mom, blk, orig, scale, out,
+                                                      nullptr, nullptr)
+                : go_scalar<true, false, false, false>(s, nb, n, rec, mom, blk, orig, scale,
+                                                       out, nullptr, nullptr);
   }
-  if (opt.kahan) {
-    return vote ? go<false, true, true, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                               out, nullptr, nullptr)
-                : go<false, false, true, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                                out, nullptr, nullptr);
+  if (vote) {
+    return opt.kahan ? go_scalar<false, true, true, false>(s, nb, n, rec, mom, blk, orig, scale,
+                                                           out, nullptr, nullptr)
+                     : go_scalar<false, true, false, false>(s, nb, n, rec, mom, blk, orig,
+                                                            scale, out, nullptr, nullptr);
   }
-  return vote ? go<false, true, false, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                              out, nullptr, nullptr)
-              : go<false, false, false, false>(s, nbricks, n, rec0, rec1, mom, blk, orig, scale,
-                                               out, nullptr, nullptr);
+  return opt.kahan ? go_pair<true, false>(s, nb, n, rec, blk, orig, scale, out, nullptr, nullptr)
+                   : go_pair<false, false>(s, nb, n, rec, blk, orig, scale, out, nullptr,
+                                           nullptr);
 }
 
 }  // namespace bhg
