@@ -40,7 +40,7 @@ FLOP_PER_TEST = 7
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maclaurin",
@@ -79,7 +79,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -115,6 +115,29 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------- captured traffic --
+def captured_traffic(workload_name, theta):
+    """DRAM bytes per walk launch from the committed ncu summary, if that
+    capture is of this workload and of the walk source as it is now."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "walk_pair_maclaurin_2M.md")).read()
+        src = open(os.path.join(ROOT, "paper_1509_07370_gb300", "csrc", "bh_walk.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256: ([0-9a-f]{64})", txt)
+    wl = re.search(r"workload: (\S+) theta=([0-9.]+)", txt)
+    tb = re.search(r"dram_bytes_per_launch: (\d+)", txt)
+    if not (sha and wl and tb):
+        return None
+    if sha.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    if wl.group(1) != workload_name or float(wl.group(2)) != float(theta):
+        return None
+    return int(tb.group(1))
 
 
 # ------------------------------------------------------------ CPU oracle --
@@ -269,6 +292,7 @@ def main():
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
     phi_gpu = out.double().cpu().numpy()
+    traffic = captured_traffic(w.name, args.theta)
     _, nn, maxlev = solver.tree_size()
     launches_per_step = 6 + (maxlev - 3) + 2
 
@@ -318,7 +342,8 @@ def main():
                           "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n},
             "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",
                          "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
-                         "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": traffic,
+                         "traffic_unit": "bytes per walk launch (ncu dram read+write)",
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz "
                                        "(median SM clock measured during the timed region)"},
