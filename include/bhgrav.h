@@ -147,6 +147,35 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
                         const double *box_lo, double box_len, const void *density_host,
                         int density_is_fp64, double theta, double G, void *out_host);
 
+/* Allocation-free solve of one small mesh.  (The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * e.g. a host code whose GPU memory is entirely reserved by its own pool
+ * allocator, or one that must not let a library enter cudaMalloc/cudaFree,
+ * which may synchronise the device.)
+ * Computes what bh_create (default options: binary32 per-cell walk with
+ * Kahan sum) + bh_build + bh_potential compute, on the CURRENT device and on
+ * `cuda_stream` (a cudaStream_t, NULL = legacy default stream), without any
+ * context and without allocating: the tree lives in one fixed array in device
+ * global memory (about 2.7 MB, held by every GPU that loads this library until
+ * the process exits).
+ *   nblocks        1 .. 64 blocks (at most 32,768 cells); more -> BH_ERR_ARG
+ *   level, ijk, box_lo, box_len, density, density_is_fp64: as bh_build
+ *   theta, G       as bh_potential
+ *   out            DEVICE float array of nblocks*512 values (density layout)
+ * The call synchronises the stream once, after the tree build, to check the
+ * geometry and the density; it returns with the walk enqueued on the stream.
+ * All calls share the fixed array and leave the last call's tree in it:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture on the device.
+ * Errors: BH_ERR_ARG, BH_ERR_GEOMETRY, BH_ERR_CUDA (no message string: there
+ * is no context). */
+bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const int32_t *ijk,
+                           const double *box_lo, double box_len, const void *density,
+                           int density_is_fp64, double theta, double G, float *out,
+                           void *cuda_stream);
+
 /* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
 const char *bh_last_error(const bh_ctx *ctx);
 

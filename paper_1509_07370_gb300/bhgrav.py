@@ -22,8 +22,8 @@ BH_PREC_F32, BH_PREC_F64 = 0, 1
 BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
 
 EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_potential", "bh_walk_counts",
-            "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_last_error",
-            "bh_destroy")
+            "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_solve_noalloc",
+            "bh_last_error", "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
@@ -65,12 +65,13 @@ def load(build_if_needed: bool = True):
         lib.bh_tree_size.argtypes = [P, P, P, P]
         lib.bh_export_nodes.argtypes = [P, P, P, P, P, P]
         lib.bh_solve_host.argtypes = [P, I, P, P, P, D, P, I, D, D, P]
+        lib.bh_solve_noalloc.argtypes = [I, P, P, P, D, P, I, D, D, P, P]
         lib.bh_last_error.argtypes = [P]
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
         lib.bh_destroy.restype = None
         for name in ("bh_create", "bh_build", "bh_potential", "bh_walk_counts",
-                     "bh_tree_size", "bh_export_nodes", "bh_solve_host"):
+                     "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_solve_noalloc"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -168,6 +169,25 @@ def bh_solve_host(ctx, level, ijk, box_lo, box_len, density_host: np.ndarray, th
                               int(density_host.dtype == np.float64), float(theta), float(G),
                               _np_ptr(out_host))
     _check(ctx, st, "bh_solve_host")
+
+
+def bh_solve_noalloc(level, ijk, box_lo, box_len, density, theta: float, G: float, out,
+                     stream: int = 0) -> None:
+    """Allocation-free solve of a mesh of at most 64 blocks, for callers that
+    cannot allocate device memory (the library keeps the tree in a fixed
+    device array).  density: CUDA float32/float64 tensor; out: CUDA float32
+    tensor; both on the current device.  Calls sharing the fixed array must
+    not overlap on the GPU."""
+    import torch
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    st = load().bh_solve_noalloc(int(level.shape[0]), _np_ptr(level), _np_ptr(ijk), _np_ptr(lo),
+                                 float(box_len), ctypes.c_void_p(_dev_ptr(density)),
+                                 int(density.dtype == torch.float64), float(theta), float(G),
+                                 ctypes.c_void_p(_dev_ptr(out, torch.float32)),
+                                 ctypes.c_void_p(int(stream)))
+    _check(None, st, "bh_solve_noalloc")
 
 
 def bh_last_error(ctx) -> str:
