@@ -139,6 +139,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
       cudaMallocHost(&ctx->tree.h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->tree.d_flags) cudaFree(ctx->tree.d_flags);
+    if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
     delete ctx;
     return BH_ERR_CUDA;
   }

@@ -21,7 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/bhgrav.h"
+#include "bhgrav.h"  // -I include
 
 namespace bhg {
 
