@@ -2,18 +2,22 @@
 """Benchmark: Barnes-Hut potential at every cell of an AMR mesh on GB300.
 
 One step = the whole hot path on one synthetic field already resident in HBM:
-bh_build (block keys, tree topology, FP64 moments) + bh_potential (opening
-radii for theta, walk).  Default workload: the Maclaurin spheroid
-(eccentricity 0.9, 2,039,808 cells, 3 AMR levels at the surface), theta 0.5,
-binary32 walk with Kahan sum, FP64 moments.
+bh_build (block keys, tree topology, FP64 moments and quadrupoles) +
+bh_potential (opening radii for theta, walk).  Default workload: the Maclaurin
+spheroid (eccentricity 0.9, 2,039,808 cells, 3 AMR levels at the surface),
+per-cell opening test at theta 0.7 with the quadrupole term, binary32 walk
+with Kahan sum -- the setting that keeps the max relative error against the
+direct sum below 1e-3 (measured in the CPU leg) with the least work.
 
 Prints one JSON line (rank 0).  `value` is cells/s of the device-resident
 step over all ranks; `e2e` the same through bh_solve_host with pinned host
-buffers (copies inside the timed region); `roofline` puts the walk against
-the FP32 ALU peak (128 FP32 lanes/SM x SMs x measured SM clock), counting the
-algorithmic FP32 operations of the per-cell walk (8 per interaction, 7 per
-opening test; counted by the library's own counting walk);
-`cpu_baseline` times the CPU oracle on a bounded sample of targets.
+buffers (copies inside the timed region); `vs_plain` the same step with the
+plain monopole walk at the theta where it reaches the same accuracy (0.3);
+`roofline` puts the walk against the FP32 ALU peak (128 FP32 lanes/SM x SMs x
+measured SM clock), counting algorithmic FP32 operations (8 per interaction
+with a cell or a monopole node, 20 per quadrupole node interaction, 7 per
+opening test; counted by the library's own counting walk); `cpu_baseline`
+times the CPU oracle on a bounded sample of targets.
 
 --impl reference times the CPU oracle alone (the reference arm).
 With torchrun, every rank solves its own copy of the field (replicas).
@@ -33,7 +37,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128
-FLOP_PER_INTERACTION = 8
+FLOP_PER_INTERACTION = 8        # 3 sub, 1 mul + 2 fma for d^2, 1 mul m*rsqrt, 1 add (+1 MUFU)
+FLOP_PER_QUAD_INTERACTION = 20  # the above, with 9 ops for d^T Q d / 2 and 3 more for
+                                # rinv (M + q rinv^4) in place of the m*rsqrt product
 FLOP_PER_TEST = 7
 
 
@@ -45,7 +51,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maclaurin",
                     choices=["maclaurin", "cloud_core", "uniform_sphere"])
-    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--theta", type=float, default=0.7)
+    ap.add_argument("--monopole", action="store_true",
+                    help="plain monopole nodes (default: with the quadrupole term)")
+    ap.add_argument("--vote", action="store_true",
+                    help="the paper's warp vote instead of the per-cell test")
+    ap.add_argument("--plain-theta", type=float, default=0.3,
+                    help="theta of the plain monopole walk timed for vs_plain")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -141,29 +154,32 @@ def captured_traffic(workload_name, theta):
 
 
 # ------------------------------------------------------------ CPU oracle --
-def oracle_leg(w, theta, cpu_seconds, phi_gpu=None):
+def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None):
     """Times the CPU oracle (tree + FP64 moments in full, walk on a sample of
     targets) and extrapolates to cells/s for the whole field."""
     from oracle import oracle as O
     rho = w.density.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     tree = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+    if quad:
+        tree.quadrupoles()
     t_build = time.perf_counter() - t0
     rng = np.random.default_rng(1234)
     n = w.ncells
     probe = rng.choice(n, min(n, 2000), replace=False)
     t0 = time.perf_counter()
-    tree.walk(theta, targets=probe)
+    tree.walk(theta, targets=probe, quad=quad)
     per = (time.perf_counter() - t0) / len(probe)
     k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
     tg = np.sort(rng.choice(n, k, replace=False))
     t0 = time.perf_counter()
-    ref, ni, nt = tree.walk(theta, targets=tg)
+    ref, ni, nt = tree.walk(theta, targets=tg, quad=quad)
     t_walk = time.perf_counter() - t0
     t_step = t_build + t_walk * (n / k)
     out = {"value": n / t_step, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
            "sample": f"tree+FP64 moments of all {n} cells; per-cell walk of {k} random cells "
-                     f"(seed 1234) extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s"}
+                     f"(seed 1234, {'quadrupole' if quad else 'monopole'}, theta {theta}) "
+                     f"extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s"}
     if phi_gpu is not None:
         m = min(k, 2000)
         d = tree.direct(targets=tg[:m])
@@ -172,6 +188,11 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None):
             "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[tg[:m]] / d - 1.0))),
             "oracle_walk_max_rel_vs_direct": float(np.max(np.abs(ref[:m] / d - 1.0))),
             "cells_compared": int(k), "cells_vs_direct": int(m)}
+        if plain is not None:
+            phi_plain, plain_theta = plain
+            out["accuracy"]["plain_max_rel_vs_direct"] = float(
+                np.max(np.abs(phi_plain[tg[:m]] / d - 1.0)))
+            out["accuracy"]["plain_theta"] = plain_theta
     return out
 
 
@@ -185,10 +206,11 @@ def reference_arm(args):
     rho = w.density.astype(np.float32).astype(np.float64)
     n = w.ncells
     rng = np.random.default_rng(99)
+    quad = not args.monopole
     tree = O.Tree(w.mesh.level, w.mesh.ijk, rho)
     probe = rng.choice(n, 500, replace=False)
     t0 = time.perf_counter()
-    tree.walk(args.theta, targets=probe)
+    tree.walk(args.theta, targets=probe, quad=quad)
     per = (time.perf_counter() - t0) / 500
     budget = 150.0 / max(1, args.steps + args.warmup)       # whole run within minutes
     k = int(min(n, max(500, budget / max(per, 1e-9))))
@@ -197,9 +219,11 @@ def reference_arm(args):
         tg = rng.choice(n, k, replace=False)
         t0 = time.perf_counter()
         tr = O.Tree(w.mesh.level, w.mesh.ijk, rho)
+        if quad:
+            tr.quadrupoles()
         tb = time.perf_counter() - t0
         t0 = time.perf_counter()
-        tr.walk(args.theta, targets=tg)
+        tr.walk(args.theta, targets=tg, quad=quad)
         tw = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(tb + tw * n / k)
@@ -209,7 +233,9 @@ def reference_arm(args):
             "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "cells": n, "theta": args.theta},
+            "config": {"workload": w.name, "cells": n, "theta": args.theta,
+                       "walk": "FP64, per-cell opening test"
+                               + (", quadrupole nodes" if quad else ", monopole nodes")},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": O.max_threads(),
                              "kind": "oracle",
                              "sample": f"per step: full tree build + walk of {k} random cells "
@@ -220,6 +246,36 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------- our arm --
+def timed_steps(solver, mesh, d_rho, theta, out, steps, warmup, flush, stream, clk=None):
+    """Warm-up, then `steps` timed steps (bh_build + bh_potential), each
+    bracketed by CUDA events on the library's stream, L2 flushed before each.
+    Returns per-step (step, build, potential) milliseconds."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.zero_()
+            solver.build(mesh.level, mesh.ijk, d_rho)
+            solver.potential(theta, 1.0, out=out)
+        stream.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        if clk is not None:
+            clk.__enter__()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            solver.build(mesh.level, mesh.ijk, d_rho)
+            ev[k][1].record(stream)
+            solver.potential(theta, 1.0, out=out)
+            ev[k][2].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        if clk is not None:
+            clk.__exit__()
+    return ([e[0].elapsed_time(e[2]) for e in ev], [e[0].elapsed_time(e[1]) for e in ev],
+            [e[1].elapsed_time(e[2]) for e in ev])
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -239,62 +295,76 @@ def main():
     w = workload(args.workload)
     n = w.ncells
     mesh = w.mesh
+    quad = not args.monopole
+    crit = bh.BH_CRIT_WARP_VOTE if args.vote else bh.BH_CRIT_PER_CELL
     rho32 = np.ascontiguousarray(w.density.reshape(-1), dtype=np.float32)
     stream = torch.cuda.Stream(dev)
-    solver = bh.Solver(device=local, stream=stream)
+    solver = bh.Solver(criterion=crit, quadrupole=quad, device=local, stream=stream)
     d_rho = torch.as_tensor(rho32, device=dev)
     out = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
-    def step():
-        solver.build(mesh.level, mesh.ijk, d_rho)
-        solver.potential(args.theta, 1.0, out=out)
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.zero_()
-            step()
-        stream.synchronize()
-        if world > 1:
-            dist.barrier()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            for k in range(args.steps):
-                flush.zero_()
-                ev[k][0].record(stream)
-                solver.build(mesh.level, mesh.ijk, d_rho)
-                ev[k][1].record(stream)
-                solver.potential(args.theta, 1.0, out=out)
-                ev[k][2].record(stream)
-            stream.synchronize()
-            torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    build_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    walk_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    step_ms, build_ms, walk_ms = timed_steps(solver, mesh, d_rho, args.theta, out, args.steps,
+                                             args.warmup, flush, stream, clk)
+    if world > 1:
+        dist.barrier()
     total_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * n * args.steps / (total_ms * 1e-3)
+    phi_gpu = out.double().cpu().numpy()
 
     # algorithmic work of the walk (untimed): per-cell counts from the library
-    ni, nt = solver.walk_counts(args.theta)
-    n_int = int(ni.sum(dtype=torch.int64).item())
-    n_test = int(nt.sum(dtype=torch.int64).item())
-    flops = FLOP_PER_INTERACTION * n_int + FLOP_PER_TEST * n_test
+    def work(s, theta, with_quad):
+        ni, nt, nc = s.walk_counts(theta, with_cells=True)
+        n_int = int(ni.sum(dtype=torch.int64).item())
+        n_test = int(nt.sum(dtype=torch.int64).item())
+        n_cell = int(nc.sum(dtype=torch.int64).item())
+        per_node = FLOP_PER_QUAD_INTERACTION if with_quad else FLOP_PER_INTERACTION
+        flops = FLOP_PER_INTERACTION * n_cell + per_node * (n_int - n_cell) + FLOP_PER_TEST * n_test
+        return n_int, n_test, n_cell, flops
+
+    n_int, n_test, n_cell, flops = work(solver, args.theta, quad)
     walk_s = float(np.mean(walk_ms)) * 1e-3
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
-    phi_gpu = out.double().cpu().numpy()
-    traffic = captured_traffic(w.name, args.theta)
+    traffic = captured_traffic(w.name, args.theta) if (quad, args.vote) == (False, False) else None
     _, nn, maxlev = solver.tree_size()
     launches_per_step = 6 + (maxlev - 3) + 2
+
+    # the plain walk (monopole, per-cell) at the theta of equal accuracy
+    plain = None
+    phi_plain = None
+    if not args.no_plain:
+        psolver = bh.Solver(device=local, stream=stream)
+        pout = torch.empty(n, dtype=torch.float32, device=dev)
+        psteps = max(5, args.steps // 3)
+        p_step, p_build, p_walk = timed_steps(psolver, mesh, d_rho, args.plain_theta, pout,
+                                              psteps, args.warmup, flush, stream)
+        p_total = float(np.sum(p_step))
+        if world > 1:
+            t = torch.tensor([p_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            p_total = float(t.item())
+        p_value = world * n * psteps / (p_total * 1e-3)
+        pi, pt, pc, pflops = work(psolver, args.plain_theta, False)
+        phi_plain = pout.double().cpu().numpy()
+        plain = {"theta": args.plain_theta, "walk": "binary32, Kahan sum, per-cell, monopole",
+                 "value": p_value, "unit": "cells/s", "steps": psteps,
+                 "ms_per_step": p_total / psteps,
+                 "phases_ms": {"build": float(np.mean(p_build)),
+                               "potential": float(np.mean(p_walk))},
+                 "interactions_per_cell": pi / n, "tests_per_cell": pt / n,
+                 "roofline_frac": pflops / (float(np.mean(p_walk)) * 1e-3) / peak,
+                 "speedup": value / p_value}
+        psolver.close()
 
     # end to end through the host-memory entry point (pinned buffers)
     e2e = None
@@ -302,7 +372,7 @@ def main():
         pinned = (torch.from_numpy(rho32).pin_memory(),
                   torch.empty(n, dtype=torch.float32).pin_memory())
         h_rho, h_out = pinned[0].numpy(), pinned[1].numpy()
-        host_solver = bh.Solver(device=local, stream=stream)
+        host_solver = bh.Solver(criterion=crit, quadrupole=quad, device=local, stream=stream)
         for _ in range(max(1, args.warmup)):
             host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
         ts = []
@@ -324,7 +394,8 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_leg(w, args.theta, args.cpu_seconds, phi_gpu)
+        cpu = oracle_leg(w, args.theta, args.cpu_seconds, phi_gpu, quad=quad,
+                         plain=(phi_plain, args.plain_theta) if phi_plain is not None else None)
 
     if rank == 0:
         line = {
@@ -333,12 +404,14 @@ def main():
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "cells": n, "nodes": nn, "theta": args.theta,
-                       "walk": "binary32, Kahan sum, per-cell opening test",
+                       "walk": "binary32, Kahan sum, "
+                               + ("warp vote (paper)" if args.vote else "per-cell opening test")
+                               + (", quadrupole nodes" if quad else ", monopole nodes"),
                        "moments": "f64", "density_input": "f32",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms))},
-            "walk_work": {"interactions": n_int, "tests": n_test,
+            "walk_work": {"interactions": n_int, "cell_interactions": n_cell, "tests": n_test,
                           "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n},
             "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",
                          "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
@@ -347,6 +420,7 @@ def main():
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz "
                                        "(median SM clock measured during the timed region)"},
+            "vs_plain": plain,
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
         }

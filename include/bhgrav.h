@@ -70,10 +70,19 @@ typedef struct {
                      BH_PREC_F64: binary64 interaction arithmetic */
   int criterion;  /* BH_CRIT_PER_CELL (default) or BH_CRIT_WARP_VOTE */
   int kahan;      /* F32 only: 1 (default) compensated (Kahan) summation, 0 plain */
-  int reserved[5];
+  int quadrupole; /* 0 (default): monopole nodes, as in the paper.  1: every
+                     accepted node also adds its quadrupole term,
+                     -G (1/2) d^T Q d / |d|^5 with Q = sum m (3 x x^T - |x|^2 I)
+                     about the node's centre of mass (not in the paper: the
+                     next term of the multipole expansion; the opening test is
+                     unchanged).  Quadrupoles are reduced in binary32 for the
+                     binary32 walk and in FP64 for the FP64 walk; they cost 32
+                     (binary32) or 80 (FP64) more bytes per internal node. */
+  int reserved[4];
 } bh_options;
 
-/* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation. */
+/* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation,
+ * monopole nodes. */
 void bh_default_options(bh_options *opt);
 
 /* Creates a context on CUDA device `device` that issues all work on
@@ -116,10 +125,12 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out);
 
 /* Same walk as bh_potential, but instead of the potential it writes, per
  * cell in the density layout, the number of interactions n_int (accepted
- * nodes plus other cells reached) and of opening tests n_test (internal
- * nodes examined).  n_int and n_test are DEVICE int32 arrays of
- * nblocks*512 entries.  Used to count the algorithmic work of a walk. */
-bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test);
+ * nodes plus other cells reached), of opening tests n_test (internal nodes
+ * examined) and, if n_cell is not NULL, of the interactions that are with
+ * single cells (a subset of n_int).  DEVICE int32 arrays of nblocks*512
+ * entries.  Used to count the algorithmic work of a walk. */
+bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test,
+                         int32_t *n_cell);
 
 /* Sizes of the current tree: leaf cells, all nodes (cells + internal), and
  * the deepest cell level.  Any pointer may be NULL.  BH_ERR_STATE if no tree. */
@@ -136,6 +147,13 @@ bh_status bh_tree_size(const bh_ctx *ctx, int64_t *n_cells, int64_t *n_nodes, in
  * For inspection and tests; not needed to compute the potential. */
 bh_status bh_export_nodes(const bh_ctx *ctx, double *M, double *R, float *delta, int32_t *skip,
                           int32_t *level);
+
+/* Copies the quadrupole of every node (pre-order, 6 values per node:
+ * xx, yy, zz, xy, xz, yz, box units, about the node's centre of mass; zero
+ * for cells; FP64 values for an FP64 context, binary32 ones widened to double
+ * otherwise) to the DEVICE array Q of 6*n_nodes doubles.  BH_ERR_STATE if no
+ * tree or if the context was created without the quadrupole option. */
+bh_status bh_export_quadrupoles(const bh_ctx *ctx, double *Q);
 
 /* One-call form for callers whose data live in HOST memory: copies the
  * density (float or double per density_is_fp64) to the device, builds the

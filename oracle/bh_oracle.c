@@ -30,6 +30,12 @@
  *   - Paper mode (Sec. 3.3): 32 neighbouring cells (a 4x4x2 brick of a block)
  *     walk together and a node is accepted only if all 32 accept it
  *     (warp vote all()).
+ *   - Optional quadrupole term (not in the paper; the textbook next term of
+ *     the multipole expansion about the centre of mass): each node carries
+ *     its traceless quadrupole Q = sum over its cells of m (3 x x^T - |x|^2 I),
+ *     x = cell centre - R, computed here straight from that definition, and an
+ *     accepted node contributes -G (M/d + (1/2) d^T Q d / d^5), d = r_t - R.
+ *     The opening test is unchanged; cells carry no quadrupole.
  *
  * Readings where the paper is silent (each also stated in the design notes):
  *   - Positions are taken in box units u = (x - lo)/L, so Phi = -(G/L) sum M/|du|.
@@ -73,6 +79,7 @@ typedef struct {
   double M;           /* mass */
   double R[3];        /* centre of mass, box units */
   double delta;       /* |R - geometric centre|, box units */
+  double Q[6];        /* quadrupole about R: xx, yy, zz, xy, xz, yz (box units) */
 } onode;
 
 typedef struct {
@@ -89,6 +96,7 @@ typedef struct {
   int *border;         /* block index, in key order */
   int used_blocks;
   int err;
+  int have_quad;
 } otree;
 
 /* ---------------------------------------------------------------- keys -- */
@@ -310,6 +318,51 @@ int or_export(const void *p, int32_t *level, int64_t *ijk, int32_t *is_leaf, int
   return OR_OK;
 }
 
+/* Quadrupole of every internal node, from its definition: a sum over the
+ * cells of its subtree (a contiguous pre-order range).  Computed on demand. */
+int or_quadrupoles(void *p) {
+  otree *t = (otree *)p;
+  if (t->have_quad) return OR_OK;
+  int64_t *end = (int64_t *)malloc(sizeof(int64_t) * (size_t)t->nnodes);
+  if (!end) return OR_ERR_OOM;
+  for (int64_t id = 0; id < t->nnodes; ++id) end[id] = id + 1;
+  for (int64_t id = t->nnodes - 1; id > 0; --id) {
+    int64_t par = t->node[id].parent;
+    if (end[id] > end[par]) end[par] = end[id];
+  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+  for (int64_t id = 0; id < t->nnodes; ++id) {
+    onode *n = &t->node[id];
+    for (int a = 0; a < 6; ++a) n->Q[a] = 0.0;
+    if (n->child[0] < 0) continue;
+    for (int64_t k = id + 1; k < end[id]; ++k) {
+      const onode *c = &t->node[k];
+      if (c->child[0] >= 0) continue;
+      double x = c->R[0] - n->R[0], y = c->R[1] - n->R[1], z = c->R[2] - n->R[2];
+      double r2 = x * x + y * y + z * z;
+      n->Q[0] += c->M * (3.0 * x * x - r2);
+      n->Q[1] += c->M * (3.0 * y * y - r2);
+      n->Q[2] += c->M * (3.0 * z * z - r2);
+      n->Q[3] += c->M * (3.0 * x * y);
+      n->Q[4] += c->M * (3.0 * x * z);
+      n->Q[5] += c->M * (3.0 * y * z);
+    }
+  }
+  free(end);
+  t->have_quad = 1;
+  return OR_OK;
+}
+
+int or_export_quad(const void *p, double *Q) {
+  const otree *t = (const otree *)p;
+  if (!t->have_quad) return OR_ERR_ARG;
+  for (int64_t id = 0; id < t->nnodes; ++id)
+    for (int a = 0; a < 6; ++a) Q[6 * id + a] = t->node[id].Q[a];
+  return OR_OK;
+}
+
 /* ------------------------------------------------------------ the walk -- */
 typedef struct { double s, c; } neumaier;
 static void nm_add(neumaier *a, double x) {
@@ -338,12 +391,24 @@ static double dist64(const double a[3], const double b[3]) {
   return sqrt((x * x + y * y) + z * z);
 }
 
+/* M/d of an accepted node, plus (1/2) d^T Q d / d^5 with the quadrupole. */
+static double node_term(const onode *n, const double tu[3], int quad) {
+  double d = dist64(tu, n->R);
+  if (!quad) return n->M / d;
+  double x = tu[0] - n->R[0], y = tu[1] - n->R[1], z = tu[2] - n->R[2];
+  double q = n->Q[0] * x * x + n->Q[1] * y * y + n->Q[2] * z * z +
+             2.0 * (n->Q[3] * x * y + n->Q[4] * x * z + n->Q[5] * y * z);
+  double d2 = d * d;
+  return n->M / d + 0.5 * q / (d2 * d2 * d);
+}
+
 typedef struct {
   const otree *t;
   int64_t self;
   float tf[3];
   double tu[3];
   float inv_theta;
+  int quad;
   neumaier sum;
   int64_t n_int, n_test;
   int64_t *list; int64_t list_n, list_cap;   /* optional accepted-set record */
@@ -366,7 +431,7 @@ static void walk_node(walk_state *w, int64_t id) {
   }
   w->n_test++;
   if (accept_f32(n, w->tf, w->inv_theta)) {   /* Eq. 4: far enough */
-    nm_add(&w->sum, n->M / dist64(w->tu, n->R));
+    nm_add(&w->sum, node_term(n, w->tu, w->quad));
     w->n_int++;
     record(w, id);
     return;
@@ -386,10 +451,11 @@ static void target_position(const otree *t, int64_t leaf, double tu[3], float tf
 static int check_theta(double theta) { return theta > 0.0 && theta <= 1.0; }
 
 /* Per-cell walk for the given caller cell indices. */
-int or_walk(const void *p, double theta, double G, int64_t ntargets, const int64_t *targets,
-            double *phi, int64_t *n_int, int64_t *n_test, int nthreads) {
+int or_walk(const void *p, double theta, double G, int quad, int64_t ntargets,
+            const int64_t *targets, double *phi, int64_t *n_int, int64_t *n_test, int nthreads) {
   const otree *t = (const otree *)p;
   if (!check_theta(theta) || !isfinite(G)) return OR_ERR_ARG;
+  if (quad && !t->have_quad) return OR_ERR_ARG;
   int64_t ncell = (int64_t)t->nblocks * 512;
   for (int64_t q = 0; q < ntargets; ++q)
     if (targets[q] < 0 || targets[q] >= ncell) return OR_ERR_ARG;
@@ -405,6 +471,7 @@ int or_walk(const void *p, double theta, double G, int64_t ntargets, const int64
     w.t = t;
     w.self = t->leaf_of_cell[targets[q]];
     w.inv_theta = inv_theta;
+    w.quad = quad;
     target_position(t, w.self, w.tu, w.tf);
     walk_node(&w, 0);
     phi[q] = scale * nm_value(&w.sum);
@@ -442,6 +509,7 @@ typedef struct {
   float tf[32][3];
   double tu[32][3];
   float inv_theta;
+  int quad;
   neumaier sum[32];
   int64_t n_int[32], n_test[32];
 } brick_state;
@@ -463,7 +531,7 @@ static void walk_brick(brick_state *w, int64_t id) {
   }
   if (all) {
     for (int l = 0; l < 32; ++l) {
-      nm_add(&w->sum[l], n->M / dist64(w->tu[l], n->R));
+      nm_add(&w->sum[l], node_term(n, w->tu[l], w->quad));
       w->n_int[l]++;
     }
     return;
@@ -483,10 +551,12 @@ static int64_t local_morton_to_cell(int64_t b, int m) {
 
 /* bricks[q] = caller block index * 16 + brick number (0..15); phi, n_int and
  * n_test get 32 entries per brick in local Morton order of the cells. */
-int or_walk_vote(const void *p, double theta, double G, int64_t nbricks, const int64_t *bricks,
-                 double *phi, int64_t *n_int, int64_t *n_test, int nthreads) {
+int or_walk_vote(const void *p, double theta, double G, int quad, int64_t nbricks,
+                 const int64_t *bricks, double *phi, int64_t *n_int, int64_t *n_test,
+                 int nthreads) {
   const otree *t = (const otree *)p;
   if (!check_theta(theta) || !isfinite(G)) return OR_ERR_ARG;
+  if (quad && !t->have_quad) return OR_ERR_ARG;
   for (int64_t q = 0; q < nbricks; ++q)
     if (bricks[q] < 0 || bricks[q] >= (int64_t)t->nblocks * 16) return OR_ERR_ARG;
   float inv_theta = (float)(1.0 / theta);
@@ -499,6 +569,7 @@ int or_walk_vote(const void *p, double theta, double G, int64_t nbricks, const i
     brick_state *w = (brick_state *)calloc(1, sizeof(brick_state));
     w->t = t;
     w->inv_theta = inv_theta;
+    w->quad = quad;
     int64_t b = bricks[q] / 16;
     int br = (int)(bricks[q] % 16);
     for (int l = 0; l < 32; ++l) {

@@ -56,11 +56,15 @@ def _load():
             lib.or_num_nodes.restype = i64
             lib.or_export.argtypes = [P] + [P] * 8
             lib.or_export.restype = i32
-            lib.or_walk.argtypes = [P, dbl, dbl, i64, P, P, P, P, i32]
+            lib.or_walk.argtypes = [P, dbl, dbl, i32, i64, P, P, P, P, i32]
             lib.or_walk.restype = i32
             lib.or_walk_list.argtypes = [P, dbl, i64, P, i64]
             lib.or_walk_list.restype = i64
-            lib.or_walk_vote.argtypes = [P, dbl, dbl, i64, P, P, P, P, i32]
+            lib.or_walk_vote.argtypes = [P, dbl, dbl, i32, i64, P, P, P, P, i32]
+            lib.or_quadrupoles.argtypes = [P]
+            lib.or_quadrupoles.restype = i32
+            lib.or_export_quad.argtypes = [P, P]
+            lib.or_export_quad.restype = i32
             lib.or_walk_vote.restype = i32
             lib.or_direct.argtypes = [P, dbl, i64, P, P, i32]
             lib.or_direct.restype = i32
@@ -133,15 +137,30 @@ class Tree:
             targets = np.arange(self.ncells, dtype=np.int64)
         return np.ascontiguousarray(targets, dtype=np.int64)
 
-    def walk(self, theta: float, G: float = 1.0, targets=None, threads: int = 0):
+    def quadrupoles(self) -> np.ndarray:
+        """Traceless quadrupole of every node about its centre of mass,
+        columns xx, yy, zz, xy, xz, yz (box units; zero for cells)."""
+        lib = _load()
+        st = lib.or_quadrupoles(self._h)
+        if st != OR_OK:
+            raise OracleError(st, "or_quadrupoles")
+        q = np.empty((self.nnodes, 6))
+        lib.or_export_quad(self._h, _ptr(q))
+        return q
+
+    def walk(self, theta: float, G: float = 1.0, targets=None, threads: int = 0,
+             quad: bool = False):
         """Per-cell Barnes-Hut potential (Eqs. 3-4) at the given caller cell
-        indices (default: every cell).  Returns (phi, n_int, n_test)."""
+        indices (default: every cell), monopole or with the quadrupole term.
+        Returns (phi, n_int, n_test)."""
+        if quad:
+            self.quadrupoles()
         t = self._targets(targets)
         phi = np.empty(t.shape[0])
         ni = np.empty(t.shape[0], np.int64)
         nt = np.empty(t.shape[0], np.int64)
-        st = _load().or_walk(self._h, float(theta), float(G), t.shape[0], _ptr(t),
-                             _ptr(phi), _ptr(ni), _ptr(nt), int(threads))
+        st = _load().or_walk(self._h, float(theta), float(G), int(bool(quad)), t.shape[0],
+                             _ptr(t), _ptr(phi), _ptr(ni), _ptr(nt), int(threads))
         if st != OR_OK:
             raise OracleError(st, "or_walk")
         return phi, ni, nt
@@ -156,17 +175,20 @@ class Tree:
         lib.or_walk_list(self._h, float(theta), int(target), _ptr(buf), n)
         return buf[:n]
 
-    def walk_vote(self, theta: float, G: float = 1.0, bricks=None, threads: int = 0):
+    def walk_vote(self, theta: float, G: float = 1.0, bricks=None, threads: int = 0,
+                  quad: bool = False):
         """Paper-mode walk (all() vote over 32-cell bricks).  bricks are
         block*16 + brick; results come 32 per brick in local Morton order."""
+        if quad:
+            self.quadrupoles()
         if bricks is None:
             bricks = np.arange(16 * self.nblocks, dtype=np.int64)
         b = np.ascontiguousarray(bricks, dtype=np.int64)
         phi = np.empty(32 * b.shape[0])
         ni = np.empty(32 * b.shape[0], np.int64)
         nt = np.empty(32 * b.shape[0], np.int64)
-        st = _load().or_walk_vote(self._h, float(theta), float(G), b.shape[0], _ptr(b),
-                                  _ptr(phi), _ptr(ni), _ptr(nt), int(threads))
+        st = _load().or_walk_vote(self._h, float(theta), float(G), int(bool(quad)), b.shape[0],
+                                  _ptr(b), _ptr(phi), _ptr(ni), _ptr(nt), int(threads))
         if st != OR_OK:
             raise OracleError(st, "or_walk_vote")
         return phi, ni, nt

@@ -22,13 +22,14 @@ BH_PREC_F32, BH_PREC_F64 = 0, 1
 BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
 
 EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_potential", "bh_walk_counts",
-            "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_solve_noalloc",
-            "bh_last_error", "bh_destroy")
+            "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
+            "bh_solve_noalloc", "bh_last_error", "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("criterion", ctypes.c_int),
-                ("kahan", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("kahan", ctypes.c_int), ("quadrupole", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class BHError(RuntimeError):
@@ -61,9 +62,10 @@ def load(build_if_needed: bool = True):
         lib.bh_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(bh_options), I, P]
         lib.bh_build.argtypes = [P, I, P, P, P, D, P, I]
         lib.bh_potential.argtypes = [P, D, D, P]
-        lib.bh_walk_counts.argtypes = [P, D, P, P]
+        lib.bh_walk_counts.argtypes = [P, D, P, P, P]
         lib.bh_tree_size.argtypes = [P, P, P, P]
         lib.bh_export_nodes.argtypes = [P, P, P, P, P, P]
+        lib.bh_export_quadrupoles.argtypes = [P, P]
         lib.bh_solve_host.argtypes = [P, I, P, P, P, D, P, I, D, D, P]
         lib.bh_solve_noalloc.argtypes = [I, P, P, P, D, P, I, D, D, P, P]
         lib.bh_last_error.argtypes = [P]
@@ -71,7 +73,8 @@ def load(build_if_needed: bool = True):
         lib.bh_destroy.argtypes = [P]
         lib.bh_destroy.restype = None
         for name in ("bh_create", "bh_build", "bh_potential", "bh_walk_counts",
-                     "bh_tree_size", "bh_export_nodes", "bh_solve_host", "bh_solve_noalloc"):
+                     "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
+                     "bh_solve_noalloc"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -131,11 +134,13 @@ def bh_potential(ctx, theta: float, G: float, out) -> None:
     _check(ctx, st, "bh_potential")
 
 
-def bh_walk_counts(ctx, theta: float, n_int, n_test) -> None:
+def bh_walk_counts(ctx, theta: float, n_int, n_test, n_cell=None) -> None:
     import torch
     st = load().bh_walk_counts(ctx, float(theta),
                                ctypes.c_void_p(_dev_ptr(n_int, torch.int32)),
-                               ctypes.c_void_p(_dev_ptr(n_test, torch.int32)))
+                               ctypes.c_void_p(_dev_ptr(n_test, torch.int32)),
+                               ctypes.c_void_p(_dev_ptr(n_cell, torch.int32))
+                               if n_cell is not None else None)
     _check(ctx, st, "bh_walk_counts")
 
 
@@ -151,6 +156,13 @@ def bh_export_nodes(ctx, M=None, R=None, delta=None, skip=None, level=None) -> N
         return ctypes.c_void_p(_dev_ptr(t)) if t is not None else None
     st = load().bh_export_nodes(ctx, p(M), p(R), p(delta), p(skip), p(level))
     _check(ctx, st, "bh_export_nodes")
+
+
+def bh_export_quadrupoles(ctx, Q) -> None:
+    """Q: CUDA float64 tensor of 6 * n_nodes values (xx, yy, zz, xy, xz, yz)."""
+    import torch
+    st = load().bh_export_quadrupoles(ctx, ctypes.c_void_p(_dev_ptr(Q, torch.float64)))
+    _check(ctx, st, "bh_export_quadrupoles")
 
 
 def bh_solve_host(ctx, level, ijk, box_lo, box_len, density_host: np.ndarray, theta: float,
@@ -209,10 +221,11 @@ class Solver:
     """
 
     def __init__(self, precision=BH_PREC_F32, criterion=BH_CRIT_PER_CELL, kahan=True,
-                 device=0, stream=None):
+                 quadrupole=False, device=0, stream=None):
         import torch
         o = bh_default_options()
         o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
+        o.quadrupole = int(bool(quadrupole))
         self.options = o
         self.device = torch.device("cuda", device)
         if stream is None:
@@ -234,12 +247,15 @@ class Solver:
         bh_potential(self._ctx, theta, G, out)
         return out
 
-    def walk_counts(self, theta: float):
+    def walk_counts(self, theta: float, with_cells: bool = False):
+        """Per-cell interaction and opening-test counts (and, with_cells, the
+        interactions with single cells)."""
         import torch
         ni = torch.empty(self.ncells, dtype=torch.int32, device=self.device)
         nt = torch.empty(self.ncells, dtype=torch.int32, device=self.device)
-        bh_walk_counts(self._ctx, theta, ni, nt)
-        return ni, nt
+        nc = torch.empty(self.ncells, dtype=torch.int32, device=self.device) if with_cells else None
+        bh_walk_counts(self._ctx, theta, ni, nt, nc)
+        return (ni, nt, nc) if with_cells else (ni, nt)
 
     def tree_size(self):
         return bh_tree_size(self._ctx)
@@ -255,6 +271,13 @@ class Solver:
                    level=torch.empty(n, dtype=torch.int32, device=d))
         bh_export_nodes(self._ctx, **out)
         return out
+
+    def export_quadrupoles(self):
+        import torch
+        _, n, _ = self.tree_size()
+        q = torch.empty((n, 6), dtype=torch.float64, device=self.device)
+        bh_export_quadrupoles(self._ctx, q)
+        return q
 
     def solve_host(self, level, ijk, density_host, theta, G=1.0, out_host=None,
                    box_lo=(0.0, 0.0, 0.0), box_len=1.0):

@@ -63,6 +63,9 @@ void free_nodes(bhg::Tree &t) {
   release(t.d_aux);
   release(t.d_lvl);
   t.node_cap = 0;
+  release(t.d_q64);
+  release(t.d_qrec);
+  t.quad_cap = 0;
 }
 
 bh_status ensure_blocks(bh_ctx *ctx, int nb) {
@@ -86,8 +89,15 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
 
 bh_status ensure_nodes(bh_ctx *ctx, int64_t n_nodes) {
   bhg::Tree &t = ctx->tree;
-  if (t.node_cap >= n_nodes) return BH_OK;
+  const bool quad = ctx->opt.quadrupole != 0;
+  const bool quad64 = quad && ctx->opt.precision == BH_PREC_F64;
+  if (t.node_cap >= n_nodes && (!quad || t.quad_cap >= n_nodes)) return BH_OK;
   free_nodes(t);
+  if (quad) {
+    if (quad64) BH_CUDA(cudaMalloc(&t.d_q64, (size_t)n_nodes * 6 * sizeof(double)));
+    BH_CUDA(cudaMalloc(&t.d_qrec, (size_t)n_nodes * sizeof(bhg::WalkQuad)));
+    t.quad_cap = n_nodes;
+  }
   const size_t n = (size_t)n_nodes;
   BH_CUDA(cudaMalloc(&t.d_mom, n * sizeof(double4_32a)));
   BH_CUDA(cudaMalloc(&t.d_rec, n * sizeof(bhg::WalkRec)));
@@ -122,7 +132,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if (opt) o = *opt;
   if ((o.precision != BH_PREC_F32 && o.precision != BH_PREC_F64) ||
       (o.criterion != BH_CRIT_PER_CELL && o.criterion != BH_CRIT_WARP_VOTE) ||
-      (o.kahan != 0 && o.kahan != 1))
+      (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1))
     return BH_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -181,6 +191,9 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
   if ((st = ensure_nodes(ctx, n_nodes)) != BH_OK) return st;
   cudaStream_t s = ctx->stream;
   const int nb = nblocks;
+  // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
+  double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
+  bhg::WalkQuad *qrec = ctx->opt.quadrupole ? t.d_qrec : nullptr;
   BH_CUDA(cudaMemsetAsync(t.d_flags, 0, 4 * sizeof(unsigned), s));
   BH_CUDA(cudaMemcpyAsync(t.d_level, level, nb * sizeof(int), cudaMemcpyHostToDevice, s));
   BH_CUDA(cudaMemcpyAsync(t.d_ijk, ijk, 3 * (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -193,10 +206,10 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
                                 t.d_rec, t.d_aux, t.d_lvl, t.d_flags));
   BH_CUDA(bhg::launch_blocks(s, nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
                              density_is_fp64, box_len, n_nodes, t.d_mom, t.d_rec, t.d_aux,
-                             t.d_lvl, t.d_flags));
+                             t.d_lvl, q64, qrec, t.d_flags));
   for (int lev = max_level - 1; lev >= 0; --lev)
     BH_CUDA(bhg::launch_top_moments(s, nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
-                                    n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_flags));
+                                    n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags));
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
   const unsigned e = t.h_flags[0];
@@ -244,12 +257,13 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
   const double scale = -G / t.L;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_blk,
-                           t.d_orig, scale, out, nullptr, nullptr));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_qrec,
+                           t.d_q64, t.d_blk, t.d_orig, scale, out, nullptr, nullptr));
   return BH_OK;
 }
 
-bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test) {
+bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test,
+                         int32_t *n_cell) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
@@ -257,8 +271,9 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_blk,
-                           t.d_orig, 0.0, nullptr, n_int, n_test));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_qrec,
+                           t.d_q64, t.d_blk, t.d_orig, 0.0, nullptr, n_int, n_test,
+                           n_cell));
   return BH_OK;
 }
 
@@ -290,6 +305,30 @@ __global__ void k_export(int64_t n, const double4_32a *mom, const bhg::WalkRec *
 }
 }  // namespace
 
+namespace {
+// Quadrupoles are stored for internal nodes only; cells (node side 0) get
+// zeros.  FP64 values if they were built (FP64 walk), else the binary32 ones.
+__global__ void k_export_quad(int64_t n, const double *q64, const bhg::WalkQuad *qrec,
+                              const float2 *aux, double *Q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool cell = aux[i].x == 0.0f;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (!cell && q64) {
+    for (int a = 0; a < 6; ++a) v[a] = q64[6 * i + a];
+  } else if (!cell) {
+    const bhg::WalkQuad w = qrec[i];
+    v[0] = 2.0 * w.hxx;
+    v[1] = 2.0 * w.hyy;
+    v[2] = 2.0 * w.hzz;
+    v[3] = w.qxy;
+    v[4] = w.qxz;
+    v[5] = w.qyz;
+  }
+  for (int a = 0; a < 6; ++a) Q[6 * i + a] = v[a];
+}
+}  // namespace
+
 bh_status bh_export_nodes(const bh_ctx *cctx, double *M, double *R, float *delta, int32_t *skip,
                           int32_t *level) {
   bh_ctx *ctx = const_cast<bh_ctx *>(cctx);
@@ -301,6 +340,23 @@ bh_status bh_export_nodes(const bh_ctx *cctx, double *M, double *R, float *delta
   const int threads = 256;
   k_export<<<(unsigned)((t.n_nodes + threads - 1) / threads), threads, 0, ctx->stream>>>(
       t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl, M, R, delta, skip, level);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
+
+bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
+  bh_ctx *ctx = const_cast<bh_ctx *>(cctx);
+  if (!ctx) return BH_ERR_ARG;
+  if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
+  if (!ctx->opt.quadrupole)
+    return fail(ctx, BH_ERR_STATE, "the context was created without the quadrupole option");
+  if (!Q) return fail(ctx, BH_ERR_ARG, "bh_export_quadrupoles: Q is null");
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  const int threads = 256;
+  k_export_quad<<<(unsigned)((ctx->tree.n_nodes + threads - 1) / threads), threads, 0,
+                  ctx->stream>>>(ctx->tree.n_nodes, ctx->tree.d_q64, ctx->tree.d_qrec,
+                                 ctx->tree.d_aux, Q);
   BH_CUDA(cudaGetLastError());
   return BH_OK;
 }

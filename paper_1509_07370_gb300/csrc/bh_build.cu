@@ -282,6 +282,79 @@ __device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int lev
   if (lvl) lvl[id] = (uint8_t)level;
 }
 
+// Quadrupole about the parent's centre of mass (parallel-axis rule): the
+// child's own quadrupole plus m (3 s s^T - |s|^2 I), s = child COM - parent
+// COM.  Order: xx, yy, zz, xy, xz, yz.  Cells have none.
+__device__ __forceinline__ void add_shifted(double Q[6], const double *Qc, double m, double sx,
+                                            double sy, double sz) {
+  const double s2 = sx * sx + sy * sy + sz * sz;
+  Q[0] += m * (3.0 * sx * sx - s2);
+  Q[1] += m * (3.0 * sy * sy - s2);
+  Q[2] += m * (3.0 * sz * sz - s2);
+  Q[3] += m * (3.0 * sx * sy);
+  Q[4] += m * (3.0 * sx * sz);
+  Q[5] += m * (3.0 * sy * sz);
+  if (Qc)
+    for (int a = 0; a < 6; ++a) Q[a] += Qc[a];
+}
+
+// Binary32 version, used when the walk is binary32: the quadrupole term is a
+// small correction rounded to binary32 anyway, and GB300 runs FP64 far slower
+// than FP32.  The shift s is formed in FP64 (a difference of nearby centres of
+// mass) and then rounded.
+__device__ __forceinline__ void add_shifted_f(float Q[6], const float *Qc, double m, double sx,
+                                              double sy, double sz) {
+  const float fm = __double2float_rn(m);
+  const float x = __double2float_rn(sx), y = __double2float_rn(sy), z = __double2float_rn(sz);
+  const float s2 = x * x + y * y + z * z;
+  Q[0] += fm * (3.0f * x * x - s2);
+  Q[1] += fm * (3.0f * y * y - s2);
+  Q[2] += fm * (3.0f * z * z - s2);
+  Q[3] += fm * (3.0f * x * y);
+  Q[4] += fm * (3.0f * x * z);
+  Q[5] += fm * (3.0f * y * z);
+  if (Qc)
+    for (int a = 0; a < 6; ++a) Q[a] += Qc[a];
+}
+
+__device__ __forceinline__ void store_quad_f(int64_t id, const float Q[6], WalkQuad *qrec) {
+  WalkQuad w;
+  w.hxx = w.hxx2 = 0.5f * Q[0];
+  w.hyy = 0.5f * Q[1];
+  w.hzz = 0.5f * Q[2];
+  w.qxy = Q[3];
+  w.qxz = Q[4];
+  w.qyz = Q[5];
+  w.pad = 0.0f;
+  qrec[id] = w;
+}
+
+// The quadrupole of a node back from its binary32 walk record.
+__device__ __forceinline__ void load_quad_f(const WalkQuad &w, float Q[6]) {
+  Q[0] = 2.0f * w.hxx;
+  Q[1] = 2.0f * w.hyy;
+  Q[2] = 2.0f * w.hzz;
+  Q[3] = w.qxy;
+  Q[4] = w.qxz;
+  Q[5] = w.qyz;
+}
+
+// FP64 quadrupole and its binary32 walk record {Qxx/2 (twice), Qyy/2, Qzz/2,
+// Qxy, Qxz, Qyz, 0}: the halves fold the 1/2 of the quadrupole term.
+__device__ __forceinline__ void store_quad(int64_t id, const double Q[6], double *q64,
+                                           WalkQuad *qrec) {
+  for (int a = 0; a < 6; ++a) q64[6 * id + a] = Q[a];
+  WalkQuad w;
+  w.hxx = w.hxx2 = __double2float_rn(0.5 * Q[0]);
+  w.hyy = __double2float_rn(0.5 * Q[1]);
+  w.hzz = __double2float_rn(0.5 * Q[2]);
+  w.qxy = __double2float_rn(Q[3]);
+  w.qxz = __double2float_rn(Q[4]);
+  w.qyz = __double2float_rn(Q[5]);
+  w.pad = 0.0f;
+  qrec[id] = w;
+}
+
 constexpr int kBlockThreads = 128;
 
 template <typename T>
@@ -290,10 +363,15 @@ __global__ void __launch_bounds__(kBlockThreads)
              const int *__restrict__ count, const int *__restrict__ prestart,
              const T *__restrict__ density, double L, int64_t n_nodes,
              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec, float2 *__restrict__ aux,
-             uint8_t *__restrict__ lvl, unsigned *flags) {
+             uint8_t *__restrict__ lvl, double *__restrict__ q64, WalkQuad *__restrict__ qrec,
+             unsigned *flags) {
   __shared__ double cm[512], cxs[512], cys[512], czs[512];  // cells, local Morton order
   __shared__ double gm[64], gx[64], gy[64], gz[64];         // level lb+2 nodes
   __shared__ double pm[8], px[8], py[8], pz[8];             // level lb+1 nodes
+  __shared__ double gq[64][6], pq[8][6];                    // their quadrupoles (FP64)
+  __shared__ float gqf[64][6], pqf[8][6];                   // (binary32)
+  const bool quad64 = q64 != nullptr;                       // FP64 quadrupoles
+  const bool quad32 = !quad64 && qrec != nullptr;           // binary32 quadrupoles
   const int p = blockIdx.x;
   const int t = threadIdx.x;
   const int4 B = blk[p];
@@ -349,6 +427,23 @@ __global__ void __launch_bounds__(kBlockThreads)
     gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
     store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl);
+    if (quad64) {
+      double Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o) {
+        const int k = 8 * q + o;
+        add_shifted(Q, nullptr, cm[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
+      }
+      for (int a = 0; a < 6; ++a) gq[q][a] = Q[a];
+      store_quad(id, Q, q64, qrec);
+    } else if (quad32) {
+      float Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o) {
+        const int k = 8 * q + o;
+        add_shifted_f(Q, nullptr, cm[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
+      }
+      for (int a = 0; a < 6; ++a) gqf[q][a] = Q[a];
+      store_quad_f(id, Q, qrec);
+    }
   }
   __syncthreads();
   if (t < 8) {  // nodes at level lb+1
@@ -368,6 +463,23 @@ __global__ void __launch_bounds__(kBlockThreads)
     pz[c] = r.z;
     const int64_t id = root + 1 + 73 * c;
     store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl);
+    if (quad64) {
+      double Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o) {
+        const int k = 8 * c + o;
+        add_shifted(Q, gq[k], gm[k], gx[k] - r.x, gy[k] - r.y, gz[k] - r.z);
+      }
+      for (int a = 0; a < 6; ++a) pq[c][a] = Q[a];
+      store_quad(id, Q, q64, qrec);
+    } else if (quad32) {
+      float Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o) {
+        const int k = 8 * c + o;
+        add_shifted_f(Q, gqf[k], gm[k], gx[k] - r.x, gy[k] - r.y, gz[k] - r.z);
+      }
+      for (int a = 0; a < 6; ++a) pqf[c][a] = Q[a];
+      store_quad_f(id, Q, qrec);
+    }
   }
   __syncthreads();
   if (t == 0) {  // the block itself
@@ -380,6 +492,16 @@ __global__ void __launch_bounds__(kBlockThreads)
     for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
     store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl);
+    if (quad64) {
+      double Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o) add_shifted(Q, pq[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
+      store_quad(root, Q, q64, qrec);
+    } else if (quad32) {
+      float Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int o = 0; o < 8; ++o)
+        add_shifted_f(Q, pqf[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
+      store_quad_f(root, Q, qrec);
+    }
   }
 }
 
@@ -389,7 +511,8 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
                               const int4 *__restrict__ blk, const int *__restrict__ count,
                               const int *__restrict__ prestart, int64_t n_nodes,
                               double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
-                              float2 *__restrict__ aux, unsigned *flags) {
+                              float2 *__restrict__ aux, double *__restrict__ q64,
+                              WalkQuad *__restrict__ qrec, unsigned *flags) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int cnt = count[p];
@@ -417,6 +540,27 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
   const int64_t skip = rec[id].skip;
   store_internal(id, skip, level, r, mom, rec, aux, nullptr);
+  if (q64) {
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    c = id + 1;
+    for (int o = 0; o < 8; ++o) {
+      const double4_32a ch = mom[c];
+      add_shifted(Q, q64 + 6 * c, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
+      c = rec[c].skip;
+    }
+    store_quad(id, Q, q64, qrec);
+  } else if (qrec) {
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+    c = id + 1;
+    for (int o = 0; o < 8; ++o) {
+      const double4_32a ch = mom[c];
+      float Qc[6];
+      load_quad_f(qrec[c], Qc);
+      add_shifted_f(Q, Qc, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
+      c = rec[c].skip;
+    }
+    store_quad_f(id, Q, qrec);
+  }
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -461,24 +605,25 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
                           int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          WalkRec *rec, float2 *aux, uint8_t *lvl, unsigned *flags) {
+                          WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64, WalkQuad *qrec,
+                          unsigned *flags) {
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                    (const double *)density, L, n_nodes, mom,
-                                                   rec, aux, lvl, flags);
+                                                   rec, aux, lvl, q64, qrec, flags);
   else
     k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                   (const float *)density, L, n_nodes, mom, rec,
-                                                  aux, lvl, flags);
+                                                  aux, lvl, q64, qrec, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               unsigned *flags) {
+                               double *q64, WalkQuad *qrec, unsigned *flags) {
   k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
-                                                   n_nodes, mom, rec, aux, flags);
+                                                   n_nodes, mom, rec, aux, q64, qrec, flags);
   return cudaGetLastError();
 }
 

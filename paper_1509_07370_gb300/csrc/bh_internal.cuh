@@ -48,6 +48,18 @@ struct __align__(32) WalkRec {
 };
 static_assert(sizeof(WalkRec) == 32, "walk record must be 32 bytes");
 
+// Quadrupole walk record (only built with the quadrupole option): half the
+// diagonal of Q (Qxx/2 twice, for packed pairs), and the off-diagonal terms,
+// so that d^T Q d / 2 = dx (Qxx/2 dx + Qxy dy + Qxz dz) + dy (Qyy/2 dy + Qyz dz)
+//                       + Qzz/2 dz^2.
+struct __align__(32) WalkQuad {
+  float hxx, hxx2;
+  float hyy, hzz;
+  float qxy, qxz;
+  float qyz, pad;
+};
+static_assert(sizeof(WalkQuad) == 32, "quadrupole record must be 32 bytes");
+
 struct Tree {
   // block arrays (capacity nb_cap)
   int *d_level = nullptr, *d_ijk = nullptr;
@@ -65,6 +77,9 @@ struct Tree {
   float2 *d_aux = nullptr;
   uint8_t *d_lvl = nullptr;
   int64_t node_cap = 0;
+  double *d_q64 = nullptr;      // 6 per node, FP64 quadrupoles (quadrupole option)
+  WalkQuad *d_qrec = nullptr;   // binary32 quadrupole walk records
+  int64_t quad_cap = 0;
   // host staging for the density of bh_solve_host
   void *d_stage_in = nullptr, *d_stage_out = nullptr;
   int64_t stage_in_bytes = 0, stage_out_bytes = 0;
@@ -96,20 +111,21 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
                           int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          WalkRec *rec, float2 *aux, uint8_t *lvl, unsigned *flags);
+                          WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64, WalkQuad *qrec,
+                          unsigned *flags);
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               unsigned *flags);
+                               double *q64, WalkQuad *qrec, unsigned *flags);
 
 // ---- walk kernels (bh_walk.cu) ---------------------------------------------
 cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
                               float inv_theta);
 // out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const WalkRec *rec, const double4_32a *mom, const int4 *blk,
-                        const int *orig, double scale, void *out, int32_t *n_int,
-                        int32_t *n_test);
+                        const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
+                        const double *q64, const int4 *blk, const int *orig, double scale,
+                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf = nullptr);
 
 // ---- small device helpers ---------------------------------------------------
 // Spread the low 21 bits of v so bit b lands at bit 3b.

@@ -156,10 +156,10 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   NA_CUDA(launch_top_nodes(s, nb, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_rec, d_aux,
                            d_lvl, d_flags));
   NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64,
-                        box_len, n_nodes, d_mom, d_rec, d_aux, d_lvl, d_flags));
+                        box_len, n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
   for (int lev = max_level - 1; lev >= 0; --lev)
     NA_CUDA(launch_top_moments(s, nb, lev, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_mom,
-                               d_rec, d_aux, d_flags));
+                               d_rec, d_aux, nullptr, nullptr, d_flags));
   // the walk must only run on a valid tree: check the flags first
   unsigned h_flags[4] = {0, 0, 0, 0};
   NA_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));
@@ -170,7 +170,7 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   NA_CUDA(launch_prepare_s2(s, n_nodes, d_aux, d_rec, (float)(1.0 / theta)));
   bh_options opt;
   bh_default_options(&opt);
-  NA_CUDA(launch_walk(s, opt, nb, n_nodes, d_rec, d_mom, d_blk, d_orig, -G / box_len, out,
-                      nullptr, nullptr));
+  NA_CUDA(launch_walk(s, opt, nb, n_nodes, d_rec, d_mom, nullptr, nullptr, d_blk, d_orig,
+                      -G / box_len, out, nullptr, nullptr));
   return BH_OK;
 }

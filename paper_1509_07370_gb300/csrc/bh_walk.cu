@@ -99,6 +99,14 @@ __device__ __forceinline__ void load_rec(const WalkRec *p, u64 &q0, u64 &q1, u64
       : "l"(p));
 }
 
+// One 32-byte quadrupole record: w0 = {Qxx/2, Qxx/2}, w1 = {Qyy/2, Qzz/2},
+// w2 = {Qxy, Qxz}, w3 = {Qyz, 0}.
+__device__ __forceinline__ void load_quad(const WalkQuad *p, u64 &w0, u64 &w1, u64 &w2, u64 &w3) {
+  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+      : "l"(p));
+}
+
 // ---- per-cell binary32 walk, two x-neighbour targets per lane ---------------
 // Adds the pair `term` to the running (Kahan-compensated) pair sums.
 template <bool KAHAN>
@@ -117,14 +125,32 @@ __device__ __forceinline__ void accumulate2(u64 &sum, u64 &comp, u64 term) {
 // record's binary32 centre of mass, with the fixed rounding of the opening
 // test: d2 = fma(dx, dx, fma(dz, dz, dy*dy)); the (dy, dz) part is shared.
 __device__ __forceinline__ void dist2(u64 tx2, float ty, float tz, u64 q0, u64 q1, float &d2a,
-                                      float &d2b) {
+                                      float &d2b, u64 &dx2, float &dy, float &dz) {
   float py, pz;
   upk(q1, py, pz);
-  const u64 dx2 = sub2(tx2, q0);
-  const float dy = __fsub_rn(ty, py);
-  const float dz = __fsub_rn(tz, pz);
+  dx2 = sub2(tx2, q0);
+  dy = __fsub_rn(ty, py);
+  dz = __fsub_rn(tz, pz);
   const float h = __fmaf_rn(dz, dz, __fmul_rn(dy, dy));
   upk(fma2(dx2, dx2, pk(h, h)), d2a, d2b);
+}
+
+// Interaction pair of an accepted node with the quadrupole term:
+// rinv (M + (d^T Q d / 2) rinv^4), i.e. M/d + (1/2) d^T Q d / d^5.
+__device__ __forceinline__ u64 quad_term2(const WalkQuad *qr, u64 mm, u64 rr, u64 dx2, float dy,
+                                          float dz) {
+  u64 w0, w1, w2, w3;
+  load_quad(qr, w0, w1, w2, w3);
+  float hyy, hzz, qxy, qxz, qyz, unused;
+  upk(w1, hyy, hzz);
+  upk(w2, qxy, qxz);
+  upk(w3, qyz, unused);
+  const float u = __fmaf_rn(qxz, dz, __fmul_rn(qxy, dy));    // shared by the pair
+  const float v = __fmaf_rn(hyy, dy, __fmul_rn(qyz, dz));
+  const float c = __fmaf_rn(dy, v, __fmul_rn(__fmul_rn(hzz, dz), dz));
+  const u64 hq = fma2(dx2, fma2(w0, dx2, pk(u, u)), pk(c, c));
+  const u64 r2 = mul2(rr, rr);
+  return mul2(rr, fma2(hq, mul2(r2, r2), mm));
 }
 
 // Walk of one 64-cell octant (unit u = 8 * sorted block + octant).
@@ -136,13 +162,15 @@ __device__ __forceinline__ void dist2(u64 tx2, float ty, float tz, u64 q0, u64 q
 // node + 9.  Targets that do not open it have next >= node + 9 already: a
 // target whose walk does not contain a node has accepted one of its
 // ancestors and skipped past the ancestor's whole subtree.
-template <bool KAHAN, bool COUNTS>
+template <bool KAHAN, bool COUNTS, bool QUAD>
 __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nodes,
                                             const WalkRec *__restrict__ rec,
+                                            const WalkQuad *__restrict__ qrec,
                                             const int4 *__restrict__ blk,
                                             const int *__restrict__ orig, float scale,
                                             float *__restrict__ out, int32_t *__restrict__ n_int,
-                                            int32_t *__restrict__ n_test) {
+                                            int32_t *__restrict__ n_test,
+                                            int32_t *__restrict__ n_leaf) {
   const unsigned p = u >> 3;                          // sorted block
   const int ma = (int)((u & 7) << 6) | (lane << 1);   // local Morton index, even: x bit 0
   const int4 B = blk[p];
@@ -157,7 +185,7 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
   const u64 tx2 = pk(txa, txb);
 
   u64 sum = 0ull, comp = 0ull;  // (+0.0f, +0.0f) pairs
-  int nia = 0, nib = 0, nta = 0, ntb = 0;
+  int nia = 0, nib = 0, nta = 0, ntb = 0, nla = 0, nlb = 0;
   unsigned next_a = 0, next_b = 0;
   unsigned node = 0;
   while (node < n_nodes) {
@@ -166,8 +194,9 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
     float s2, skf;
     upk(q3, s2, skf);
     const unsigned skip = __float_as_uint(skf);
-    float d2a, d2b;
-    dist2(tx2, ty, tz, q0, q1, d2a, d2b);
+    float d2a, d2b, dy, dz;
+    u64 dx2;
+    dist2(tx2, ty, tz, q0, q1, d2a, d2b, dx2, dy, dz);
     const bool mine_a = next_a == node, mine_b = next_b == node;
     const bool take_a = mine_a && d2a > s2;
     const bool take_b = mine_b && d2b > s2;
@@ -177,11 +206,15 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
       nib += take_b;
       nta += mine_a && internal;
       ntb += mine_b && internal;
+      nla += take_a && !internal;
+      nlb += take_b && !internal;
     } else {
       float ra = rsqrt_approx(d2a), rb = rsqrt_approx(d2b);
       ra = take_a ? ra : 0.0f;
       rb = take_b ? rb : 0.0f;
-      accumulate2<KAHAN>(sum, comp, mul2(q2, pk(ra, rb)));
+      const u64 rr = pk(ra, rb);
+      accumulate2<KAHAN>(sum, comp,
+                         QUAD ? quad_term2(qrec + node, q2, rr, dx2, dy, dz) : mul2(q2, rr));
     }
     if (skip == node + 9u) {  // bottom node
       const bool open_a = mine_a && !take_a, open_b = mine_b && !take_b;
@@ -190,13 +223,16 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
         for (unsigned c = node + 1; c < node + 9u; ++c) {
           u64 c0, c1, c2, c3;
           load_rec(rec + c, c0, c1, c2, c3);
-          float e2a, e2b;
-          dist2(tx2, ty, tz, c0, c1, e2a, e2b);
+          float e2a, e2b, ey, ez;
+          u64 ex2;
+          dist2(tx2, ty, tz, c0, c1, e2a, e2b, ex2, ey, ez);
           const bool la = open_a && e2a > 0.0f;  // every cell but the target's own
           const bool lb = open_b && e2b > 0.0f;
           if (COUNTS) {
             nia += la;
             nib += lb;
+            nla += la;
+            nlb += lb;
           } else {
             float ra = rsqrt_approx(e2a), rb = rsqrt_approx(e2b);
             ra = la ? ra : 0.0f;
@@ -220,6 +256,10 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
     n_int[cell + 1] = nib;
     n_test[cell] = nta;
     n_test[cell + 1] = ntb;
+    if (n_leaf) {
+      n_leaf[cell] = nla;
+      n_leaf[cell + 1] = nlb;
+    }
   } else {
     if (KAHAN) sum = sub2(sum, comp);
     float sa, sb;
@@ -233,26 +273,29 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
 // persistent SM-affine schedule with work stealing raised the L1 hit rate
 // from 44 % to 57 % but ran 8 % slower on GB300, so the hardware schedule of a
 // plain grid is kept.)
-template <bool KAHAN, bool COUNTS>
+template <bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kWalkThreads)
     k_walk_pair(unsigned nunits, unsigned n_nodes, const WalkRec *__restrict__ rec,
-                const int4 *__restrict__ blk, const int *__restrict__ orig, float scale,
+                const WalkQuad *__restrict__ qrec, const int4 *__restrict__ blk,
+                const int *__restrict__ orig, float scale,
                 float *__restrict__ out, int32_t *__restrict__ n_int,
-                int32_t *__restrict__ n_test) {
+                int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
   const int lane = threadIdx.x & 31;
   const unsigned warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_octant<KAHAN, COUNTS>(warp, lane, n_nodes, rec, blk, orig, scale, out, n_int, n_test);
+  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, n_nodes, rec, qrec, blk, orig, scale, out, n_int,
+                                   n_test, n_leaf);
 }
 
 // ---- one target per lane: binary64 interactions and/or the warp vote --------
-template <bool F64, bool VOTE, bool KAHAN, bool COUNTS>
+template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kWalkThreads)
     k_walk_scalar(int nbricks, unsigned n_nodes, const WalkRec *__restrict__ rec,
-                  const double4_32a *__restrict__ mom, const int4 *__restrict__ blk,
+                  const double4_32a *__restrict__ mom, const WalkQuad *__restrict__ qrec,
+                  const double *__restrict__ q64, const int4 *__restrict__ blk,
                   const int *__restrict__ orig, float scale_f, double scale_d,
                   void *__restrict__ out, int32_t *__restrict__ n_int,
-                  int32_t *__restrict__ n_test) {
+                  int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
   const int warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= nbricks) return;  // whole warps only
@@ -268,7 +311,7 @@ __global__ void __launch_bounds__(kWalkThreads)
 
   float sum = 0.0f, comp = 0.0f;
   double sumd = 0.0;
-  int ni = 0, nt = 0;
+  int ni = 0, nt = 0, nl = 0;
   unsigned next = 0;
   unsigned node = 0;
   while (node < n_nodes) {
@@ -298,16 +341,33 @@ __global__ void __launch_bounds__(kWalkThreads)
     if (COUNTS) {
       nt += (mine && internal) ? 1 : 0;
       ni += take ? 1 : 0;
+      nl += (take && !internal) ? 1 : 0;
     } else if (F64) {
       if (take) {
         const double4_32a md = mom[node];
         const double ex = (double)tx - md.x, ey = (double)ty - md.y, ez = (double)tz - md.z;
-        sumd += md.w / sqrt(ex * ex + ey * ey + ez * ez);
+        const double dd = ex * ex + ey * ey + ez * ez;
+        const double rinv = 1.0 / sqrt(dd);
+        double t = md.w * rinv;
+        if (QUAD && internal) {
+          const double *Q = q64 + 6 * (size_t)node;
+          const double hq = 0.5 * (Q[0] * ex * ex + Q[1] * ey * ey + Q[2] * ez * ez) +
+                            Q[3] * ex * ey + Q[4] * ex * ez + Q[5] * ey * ez;
+          t += hq * rinv * rinv * rinv * rinv * rinv;
+        }
+        sumd += t;
       }
     } else {
       float r = rsqrt_approx(d2);
       r = take ? r : 0.0f;
-      const float term = __fmul_rn(mf, r);
+      float term = __fmul_rn(mf, r);
+      if (QUAD && internal) {  // cells carry no quadrupole (and have no record)
+        const WalkQuad w = qrec[node];
+        const float hq = dx * (w.hxx * dx + w.qxy * dy + w.qxz * dz) +
+                         dy * (w.hyy * dy + w.qyz * dz) + w.hzz * dz * dz;
+        const float r2 = r * r;
+        term = r * (mf + hq * r2 * r2);
+      }
       if (KAHAN) {
         const float y = __fsub_rn(term, comp);
         const float t = __fadd_rn(sum, y);
@@ -323,6 +383,7 @@ __global__ void __launch_bounds__(kWalkThreads)
   if (COUNTS) {
     n_int[cell] = ni;
     n_test[cell] = nt;
+    if (n_leaf) n_leaf[cell] = nl;
   } else if (F64) {
     reinterpret_cast<double *>(out)[cell] = sumd * scale_d;
   } else {
@@ -331,25 +392,54 @@ __global__ void __launch_bounds__(kWalkThreads)
   }
 }
 
-template <bool KAHAN, bool COUNTS>
-cudaError_t go_pair(cudaStream_t s, int nb, unsigned n, const WalkRec *rec, const int4 *blk,
-                    const int *orig, double scale, void *out, int32_t *ni, int32_t *nt) {
+template <bool KAHAN, bool COUNTS, bool QUAD>
+cudaError_t go_pair(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
+                    const WalkQuad *qrec, const int4 *blk, const int *orig, double scale,
+                    void *out, int32_t *ni, int32_t *nt, int32_t *nl = nullptr) {
   const unsigned nunits = (unsigned)nb * 8u;
   const int grid = (int)((nunits + kWarpsPerCta - 1) / kWarpsPerCta);
-  k_walk_pair<KAHAN, COUNTS><<<grid, kWalkThreads, 0, s>>>(nunits, n, rec, blk, orig,
-                                                          (float)scale, (float *)out, ni, nt);
+  k_walk_pair<KAHAN, COUNTS, QUAD><<<grid, kWalkThreads, 0, s>>>(
+      nunits, n, rec, qrec, blk, orig, (float)scale, (float *)out, ni, nt, nl);
   return cudaGetLastError();
 }
 
-template <bool F64, bool VOTE, bool KAHAN, bool COUNTS>
+template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
 cudaError_t go_scalar(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
-                      const double4_32a *mom, const int4 *blk, const int *orig, double scale,
-                      void *out, int32_t *ni, int32_t *nt) {
+                      const double4_32a *mom, const WalkQuad *qrec, const double *q64,
+                      const int4 *blk, const int *orig, double scale, void *out, int32_t *ni,
+                      int32_t *nt, int32_t *nl = nullptr) {
   const int nbricks = nb * 16;
   const int grid = (nbricks + kWarpsPerCta - 1) / kWarpsPerCta;
-  k_walk_scalar<F64, VOTE, KAHAN, COUNTS><<<grid, kWalkThreads, 0, s>>>(
-      nbricks, n, rec, mom, blk, orig, (float)scale, scale, out, ni, nt);
+  k_walk_scalar<F64, VOTE, KAHAN, COUNTS, QUAD><<<grid, kWalkThreads, 0, s>>>(
+      nbricks, n, rec, mom, qrec, q64, blk, orig, (float)scale, scale, out, ni, nt, nl);
   return cudaGetLastError();
+}
+
+// Picks the kernel instance for the options.  The counting walk takes the
+// same decisions as every walk of the same criterion (the opening test does
+// not depend on precision, summation or the quadrupole term).
+template <bool QUAD>
+cudaError_t launch_walk_q(cudaStream_t s, const bh_options &opt, int nb, unsigned n,
+                          const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
+                          const double *q64, const int4 *blk, const int *orig, double scale,
+                          void *out) {
+  const bool vote = opt.criterion == BH_CRIT_WARP_VOTE;
+  if (opt.precision == BH_PREC_F64)
+    return vote ? go_scalar<true, true, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64, blk,
+                                                            orig, scale, out, nullptr, nullptr)
+                : go_scalar<true, false, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64, blk,
+                                                             orig, scale, out, nullptr, nullptr);
+  if (vote)
+    return opt.kahan ? go_scalar<false, true, true, false, QUAD>(s, nb, n, rec, mom, qrec, q64,
+                                                                 blk, orig, scale, out, nullptr,
+                                                                 nullptr)
+                     : go_scalar<false, true, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64,
+                                                                  blk, orig, scale, out, nullptr,
+                                                                  nullptr);
+  return opt.kahan ? go_pair<true, false, QUAD>(s, nb, n, rec, qrec, blk, orig, scale, out,
+                                                nullptr, nullptr)
+                   : go_pair<false, false, QUAD>(s, nb, n, rec, qrec, blk, orig, scale, out,
+                                                 nullptr, nullptr);
 }
 
 }  // namespace
@@ -363,31 +453,20 @@ cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux
 }
 
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const WalkRec *rec, const double4_32a *mom, const int4 *blk,
-                        const int *orig, double scale, void *out, int32_t *n_int,
-                        int32_t *n_test) {
+                        const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
+                        const double *q64, const int4 *blk, const int *orig, double scale,
+                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf) {
   const unsigned n = (unsigned)n_nodes;
-  const bool vote = opt.criterion == BH_CRIT_WARP_VOTE;
-  if (n_int) {  // counting walk: same decisions as the walk of these options
-    return vote ? go_scalar<false, true, false, true>(s, nb, n, rec, mom, blk, orig, scale, out,
-                                                      n_int, n_test)
-                : go_pair<false, true>(s, nb, n, rec, blk, orig, scale, out, n_int, n_test);
-  }
-  if (opt.precision == BH_PREC_F64) {
-    return vote ? go_scalar<true, true, false, false>(s, nb, n, rec, mom, blk, orig, scale, out,
-                                                      nullptr, nullptr)
-                : go_scalar<true, false, false, false>(s, nb, n, rec, mom, blk, orig, scale,
-                                                       out, nullptr, nullptr);
-  }
-  if (vote) {
-    return opt.kahan ? go_scalar<false, true, true, false>(s, nb, n, rec, mom, blk, orig, scale,
-                                                           out, nullptr, nullptr)
-                     : go_scalar<false, true, false, false>(s, nb, n, rec, mom, blk, orig,
-                                                            scale, out, nullptr, nullptr);
-  }
-  return opt.kahan ? go_pair<true, false>(s, nb, n, rec, blk, orig, scale, out, nullptr, nullptr)
-                   : go_pair<false, false>(s, nb, n, rec, blk, orig, scale, out, nullptr,
-                                           nullptr);
+  if (n_int)  // counting walk
+    return opt.criterion == BH_CRIT_WARP_VOTE
+               ? go_scalar<false, true, false, true, false>(s, nb, n, rec, mom, qrec, q64, blk,
+                                                           orig, scale, out, n_int, n_test,
+                                                           n_leaf)
+               : go_pair<false, true, false>(s, nb, n, rec, qrec, blk, orig, scale, out, n_int,
+                                             n_test, n_leaf);
+  if (opt.quadrupole)
+    return launch_walk_q<true>(s, opt, nb, n, rec, mom, qrec, q64, blk, orig, scale, out);
+  return launch_walk_q<false>(s, opt, nb, n, rec, mom, qrec, q64, blk, orig, scale, out);
 }
 
 }  // namespace bhg

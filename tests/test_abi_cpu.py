@@ -41,7 +41,7 @@ def test_null_arguments_fail_without_touching_the_gpu():
     assert lib.bh_create(None, None, 0, None) == B.BH_ERR_ARG
     assert lib.bh_build(None, 1, None, None, None, 1.0, None, 0) == B.BH_ERR_ARG
     assert lib.bh_potential(None, 0.5, 1.0, None) == B.BH_ERR_ARG
-    assert lib.bh_walk_counts(None, 0.5, None, None) == B.BH_ERR_ARG
+    assert lib.bh_walk_counts(None, 0.5, None, None, None) == B.BH_ERR_ARG
     assert lib.bh_tree_size(None, None, None, None) == B.BH_ERR_ARG
     assert lib.bh_export_nodes(None, None, None, None, None, None) == B.BH_ERR_ARG
     assert lib.bh_last_error(None) == b"null context"

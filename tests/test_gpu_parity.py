@@ -119,6 +119,17 @@ def test_opening_decisions_bit_exact(name, theta):
     assert np.array_equal(ni, oi) and np.array_equal(nt, ot)
 
 
+def test_cell_interaction_counts_match_accepted_sets():
+    mesh, rho = _mesh("diag_refined")
+    s = _build(_solver(), mesh, rho)
+    ni, nt, nc = (x.cpu().numpy() for x in s.walk_counts(0.6, with_cells=True))
+    t = _oracle(mesh, rho)
+    leaf = t.export()["is_leaf"]
+    for tgt in np.random.default_rng(4).choice(mesh.ncells, 40, replace=False):
+        acc = t.walk_list(0.6, tgt)
+        assert nc[tgt] == int(leaf[acc].sum()) and ni[tgt] == len(acc)
+
+
 @pytest.mark.parametrize("name", ["refined_twice", "c1"])
 def test_paper_mode_decisions_bit_exact(name):
     mesh, rho = _mesh(name)
@@ -232,6 +243,64 @@ def test_cloud_core_full_size_sampled():
     ref, _, _ = t.walk(0.5, targets=tg)
     assert _rel(phi[tg], ref).max() <= F32_TOL
     assert np.all(np.isfinite(phi)) and np.all(phi < 0)
+
+
+# ----------------------------------------------------- quadrupole term ---
+@pytest.mark.parametrize("name", ["refined_twice", "c1", "maclaurin_small"])
+@pytest.mark.parametrize("prec,tol", [(B.BH_PREC_F64, 1e-12), (B.BH_PREC_F32, 1e-5)])
+def test_quadrupole_moments_match_oracle(name, prec, tol):
+    """FP64 quadrupoles (FP64 walk) to 1e-12 and binary32 ones (binary32 walk)
+    to 1e-5 of M l^2, the natural scale of a node's quadrupole."""
+    mesh, rho = _mesh(name)
+    s = _build(B.Solver(precision=prec, quadrupole=True), mesh, rho)
+    q = s.export_quadrupoles().cpu().numpy()
+    t = _oracle(mesh, rho)
+    qo = t.quadrupoles()
+    e = t.export()
+    scale = e["M"] * np.exp2(-2.0 * e["level"]) + 1e-300     # M l^2 of each node
+    assert np.all(np.abs(q - qo) <= tol * scale[:, None])
+
+
+@pytest.mark.parametrize("name", ["refined_twice", "c1", "diag_refined_shuffled"])
+@pytest.mark.parametrize("theta", [0.5, 0.8])
+def test_quadrupole_potential_f32_matches_oracle(name, theta):
+    mesh, rho = _mesh(name)
+    s = _build(B.Solver(quadrupole=True), mesh, rho)
+    phi = s.potential(theta).cpu().numpy()
+    ref, _, _ = _oracle(mesh, rho).walk(theta, quad=True)
+    assert _rel(phi, ref).max() <= F32_TOL
+
+
+def test_quadrupole_potential_f64_and_paper_mode():
+    mesh, rho = _mesh("c1")
+    t = _oracle(mesh, rho)
+    s = _build(B.Solver(precision=B.BH_PREC_F64, quadrupole=True), mesh, rho)
+    ref, _, _ = t.walk(0.7, quad=True)
+    assert _rel(s.potential(0.7).cpu().numpy(), ref).max() <= F64_TOL
+    for prec, tol in ((B.BH_PREC_F32, F32_TOL), (B.BH_PREC_F64, F64_TOL)):
+        s = _build(B.Solver(precision=prec, criterion=B.BH_CRIT_WARP_VOTE, quadrupole=True),
+                   mesh, rho)
+        refv, _, _ = t.walk_vote(0.7, quad=True)
+        assert _rel(s.potential(0.7).cpu().numpy()[_vote_to_caller(mesh)], refv).max() <= tol
+
+
+@pytest.mark.parametrize("theta", [0.7, 0.8])
+def test_quadrupole_maclaurin_full_size_sampled(theta):
+    mesh, rho = _mesh("maclaurin")
+    s = _build(B.Solver(quadrupole=True), mesh, rho)
+    phi = s.potential(theta).cpu().numpy()
+    tg = _sample(mesh.ncells, 3000, seed=int(theta * 10))
+    ref, _, _ = _oracle(mesh, rho).walk(theta, targets=tg, quad=True)
+    assert _rel(phi[tg], ref).max() <= F32_TOL
+    assert np.all(np.isfinite(phi)) and np.all(phi < 0)
+
+
+def test_quadrupole_export_needs_the_option():
+    mesh, rho = _mesh("one_block")
+    s = _build(_solver(), mesh, rho)
+    with pytest.raises(B.BHError) as e:
+        s.export_quadrupoles()
+    assert e.value.status == B.BH_ERR_STATE
 
 
 # --------------------------------------------------------------- errors ---

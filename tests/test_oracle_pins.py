@@ -397,3 +397,55 @@ def test_error_curve_matches_paper_figure(golden_dir):
         errs[th] = np.abs(t.walk(th, targets=tg)[0] / ref[tg] - 1.0).max()
         assert paper[th] / 10.0 < errs[th] < paper[th] * 10.0, (th, errs[th])
     assert errs[1.0] > errs[0.75] > errs[0.5] > errs[0.25]
+
+
+# ------------------------------------------------- quadrupole extension ---
+def test_quadrupole_traceless_and_zero_for_a_point_mass(tiny):
+    m, rho = tiny["refined_corner"]
+    t = _tree(m, rho)
+    e = t.export()
+    Q = t.quadrupoles()
+    scale = e["M"] * np.exp2(-2.0 * e["level"]) + 1e-300
+    assert np.all(np.abs(Q[:, 0] + Q[:, 1] + Q[:, 2]) <= 1e-13 * scale)
+    assert np.all(Q[e["is_leaf"] == 1] == 0.0)
+    # all mass in one cell: every node is that point mass about its own
+    # centre of mass, so Q = 0 and the quadrupole walk equals the monopole walk
+    one = np.zeros_like(rho)
+    one[3, 2, 5, 1] = 4.0
+    t1 = _tree(m, one)
+    assert np.abs(t1.quadrupoles()).max() <= 1e-15
+    tg = np.arange(0, m.ncells, 13)
+    assert np.allclose(t1.walk(0.7, targets=tg, quad=True)[0], t1.walk(0.7, targets=tg)[0],
+                       rtol=1e-15, atol=0)
+
+
+def test_quadrupole_of_two_masses_far_field():
+    """Two equal masses 2a apart seen from distance r along their axis: the
+    monopole errs by ~(a/r)^2, the quadrupole term removes that order."""
+    m = mg.uniform_mesh(2)                     # 32^3 cells of side 1/32
+    rho = np.zeros((m.nblocks, 8, 8, 8))
+    u, _ = _cell_geometry(m)
+    key = {tuple(np.round(p * 64).astype(int)): i for i, p in enumerate(u)}
+    a = key[(1, 1, 1)]                         # cell centres (1,1,1)/64 and (5,1,1)/64
+    b = key[(5, 1, 1)]
+    rho.reshape(-1)[a] = rho.reshape(-1)[b] = 1.0
+    t = _tree(m, rho)
+    far = [key[(k, 1, 1)] for k in (41, 51, 61)]   # along the axis
+    d = t.direct(targets=far)
+    mono = t.walk(1.0, targets=far)[0]
+    quad = t.walk(1.0, targets=far, quad=True)[0]
+    em, eq = np.abs(mono / d - 1), np.abs(quad / d - 1)
+    assert np.all(em > 1e-4) and np.all(eq < 0.05 * em)
+
+
+def test_quadrupole_reduces_walk_error():
+    w = mg.uniform_sphere(block_level=2)
+    t = O.Tree.from_workload(w)
+    tg = np.random.default_rng(2).choice(w.ncells, 600, replace=False)
+    d = t.direct(targets=tg)
+    for th, factor in ((0.3, 8.0), (0.5, 8.0), (0.8, 3.0)):
+        em = np.abs(t.walk(th, targets=tg)[0] / d - 1).max()
+        eq = np.abs(t.walk(th, targets=tg, quad=True)[0] / d - 1).max()
+        assert eq < em / factor, (th, em, eq)
+    # the opening decisions do not depend on the quadrupole term
+    assert np.array_equal(t.walk(0.6, targets=tg)[1], t.walk(0.6, targets=tg, quad=True)[1])
