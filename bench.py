@@ -131,24 +131,27 @@ class ClockSampler:
 
 
 # ----------------------------------------------------- captured traffic --
-def captured_traffic(workload_name, theta):
+def captured_traffic(workload_name, theta, mode):
     """DRAM bytes per walk launch from the committed ncu summary, if that
     capture is of this workload and of the walk source as it is now."""
     import hashlib
     import re
     try:
-        txt = open(os.path.join(ROOT, "profiles", "walk_pair_maclaurin_2M.md")).read()
+        txt = open(os.path.join(ROOT, "profiles",
+                                "walk_pair_quadrupole_theta0.7_maclaurin_2M.md")).read()
         src = open(os.path.join(ROOT, "paper_1509_07370_gb300", "csrc", "bh_walk.cu"), "rb").read()
     except OSError:
         return None
     sha = re.search(r"source_sha256: ([0-9a-f]{64})", txt)
-    wl = re.search(r"workload: (\S+) theta=([0-9.]+)", txt)
+    wl = re.search(r"workload: (\S+) theta=([0-9.]+) mode=(\w+)", txt)
     tb = re.search(r"dram_bytes_per_launch: (\d+)", txt)
     if not (sha and wl and tb):
         return None
     if sha.group(1) != hashlib.sha256(src).hexdigest():
         return None
     if wl.group(1) != workload_name or float(wl.group(2)) != float(theta):
+        return None
+    if wl.group(3) != mode:
         return None
     return int(tb.group(1))
 
@@ -167,6 +170,7 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None):
     rng = np.random.default_rng(1234)
     n = w.ncells
     probe = rng.choice(n, min(n, 2000), replace=False)
+    tree.walk(theta, targets=probe[:64], quad=quad)      # start the OpenMP threads
     t0 = time.perf_counter()
     tree.walk(theta, targets=probe, quad=quad)
     per = (time.perf_counter() - t0) / len(probe)
@@ -335,7 +339,8 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
-    traffic = captured_traffic(w.name, args.theta) if (quad, args.vote) == (False, False) else None
+    traffic = (captured_traffic(w.name, args.theta, "quadrupole" if quad else "monopole")
+               if not args.vote else None)
     _, nn, maxlev = solver.tree_size()
     launches_per_step = 6 + (maxlev - 3) + 2
 
