@@ -123,6 +123,49 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
  * Errors: BH_ERR_STATE (no tree), BH_ERR_ARG, BH_ERR_CUDA. */
 bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out);
 
+/* Several independent meshes ("fields") at once: one tree per field, all
+ * built by the same kernel launches and walked by one launch of bh_potential
+ * (each cell only sees its own field).  Not in the paper: batching for many
+ * small solves, whose single launches would each fill only part of the GPU.
+ *   nfields          number of fields (>= 1)
+ *   nblocks          HOST int32[nfields], blocks per field
+ *   level, ijk       HOST arrays of all fields' blocks, field after field
+ *   box_lo, box_len  HOST double[nfields][3] and double[nfields]: each field's box
+ *   density          DEVICE array, field after field, 512 values per block
+ * Cell arrays (density, potential) follow the concatenated block order.
+ * bh_potential, bh_walk_counts, bh_export_* then cover all fields.  Same
+ * errors as bh_build. */
+bh_status bh_build_batch(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
+                         const int32_t *ijk, const double *box_lo, const double *box_len,
+                         const void *density, int density_is_fp64);
+
+/* New densities on the current geometry: recomputes the moments (and
+ * quadrupoles) only, without the geometry work and without synchronising
+ * the stream.  Densities are checked on the device; bh_sync_status reports a
+ * negative or non-finite value (BH_ERR_ARG).  BH_ERR_STATE if no tree. */
+bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp64);
+
+/* Synchronises the context's stream and reports errors the device raised
+ * since the last build or density update (BH_OK if none). */
+bh_status bh_sync_status(bh_ctx *ctx);
+
+/* Times the binary32 per-cell walk of the current tree at this theta for
+ * CTAs of 2, 4, 8 and 16 warps (one warp per 64-cell octant) and keeps the
+ * fastest for later walks; *warps_per_cta (may be NULL) receives it (0 for
+ * walk modes with a fixed launch shape).  Allocates a scratch output once. */
+bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta);
+
+/* bh_update_density + bh_potential as ONE CUDA graph launch: the first call
+ * (or a call with a different density/out pointer, density type, theta or G)
+ * tunes the walk if it was not tuned yet, captures the sequence on the
+ * context's stream and instantiates it; later calls replay it.  The context
+ * must run on a created (non-default) stream.  Nothing is synchronised:
+ * out is ready when the stream reaches the end of the graph; density errors
+ * are reported by bh_sync_status.  Errors: BH_ERR_STATE, BH_ERR_ARG,
+ * BH_ERR_CUDA. */
+bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, double theta,
+                         double G, void *out);
+
 /* Same walk as bh_potential, but instead of the potential it writes, per
  * cell in the density layout, the number of interactions n_int (accepted
  * nodes plus other cells reached), of opening tests n_test (internal nodes

@@ -21,9 +21,11 @@ BH_OK, BH_ERR_ARG, BH_ERR_GEOMETRY, BH_ERR_OOM, BH_ERR_CUDA, BH_ERR_DEVICE_TIMEO
 BH_PREC_F32, BH_PREC_F64 = 0, 1
 BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
 
-EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_potential", "bh_walk_counts",
-            "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
-            "bh_solve_noalloc", "bh_last_error", "bh_destroy")
+EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
+            "bh_update_density", "bh_sync_status", "bh_autotune", "bh_solve_graph",
+            "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
+            "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_last_error",
+            "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
@@ -62,6 +64,11 @@ def load(build_if_needed: bool = True):
         lib.bh_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(bh_options), I, P]
         lib.bh_build.argtypes = [P, I, P, P, P, D, P, I]
         lib.bh_potential.argtypes = [P, D, D, P]
+        lib.bh_build_batch.argtypes = [P, I, P, P, P, P, P, P, I]
+        lib.bh_update_density.argtypes = [P, P, I]
+        lib.bh_sync_status.argtypes = [P]
+        lib.bh_autotune.argtypes = [P, D, P]
+        lib.bh_solve_graph.argtypes = [P, P, I, D, D, P]
         lib.bh_walk_counts.argtypes = [P, D, P, P, P]
         lib.bh_tree_size.argtypes = [P, P, P, P]
         lib.bh_export_nodes.argtypes = [P, P, P, P, P, P]
@@ -72,7 +79,9 @@ def load(build_if_needed: bool = True):
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
         lib.bh_destroy.restype = None
-        for name in ("bh_create", "bh_build", "bh_potential", "bh_walk_counts",
+        for name in ("bh_create", "bh_build", "bh_build_batch", "bh_update_density",
+                     "bh_sync_status", "bh_autotune", "bh_solve_graph", "bh_potential",
+                     "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc"):
             getattr(lib, name).restype = I
@@ -127,6 +136,48 @@ def bh_build(ctx, level, ijk, box_lo, box_len, density) -> None:
                          float(box_len), ctypes.c_void_p(_dev_ptr(density)),
                          int(density.dtype == torch.float64))
     _check(ctx, st, "bh_build")
+
+
+def bh_build_batch(ctx, nblocks, level, ijk, box_lo, box_len, density) -> None:
+    """nblocks: blocks per field; level/ijk: all fields' blocks concatenated;
+    box_lo [nfields, 3], box_len [nfields] host arrays; density: CUDA tensor."""
+    import torch
+    nb = np.ascontiguousarray(nblocks, dtype=np.int32)
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64).reshape(-1, 3)
+    ln = np.ascontiguousarray(box_len, dtype=np.float64)
+    if density.numel() != 512 * level.shape[0] or nb.sum() != level.shape[0]:
+        raise ValueError("density must hold 512 values per block; nblocks must sum to the blocks")
+    st = load().bh_build_batch(ctx, int(nb.shape[0]), _np_ptr(nb), _np_ptr(level), _np_ptr(ijk),
+                               _np_ptr(lo), _np_ptr(ln), ctypes.c_void_p(_dev_ptr(density)),
+                               int(density.dtype == torch.float64))
+    _check(ctx, st, "bh_build_batch")
+
+
+def bh_update_density(ctx, density) -> None:
+    import torch
+    st = load().bh_update_density(ctx, ctypes.c_void_p(_dev_ptr(density)),
+                                  int(density.dtype == torch.float64))
+    _check(ctx, st, "bh_update_density")
+
+
+def bh_sync_status(ctx) -> None:
+    _check(ctx, load().bh_sync_status(ctx), "bh_sync_status")
+
+
+def bh_autotune(ctx, theta: float) -> int:
+    w = ctypes.c_int()
+    _check(ctx, load().bh_autotune(ctx, float(theta), ctypes.byref(w)), "bh_autotune")
+    return w.value
+
+
+def bh_solve_graph(ctx, density, theta: float, G: float, out) -> None:
+    import torch
+    st = load().bh_solve_graph(ctx, ctypes.c_void_p(_dev_ptr(density)),
+                               int(density.dtype == torch.float64), float(theta), float(G),
+                               ctypes.c_void_p(_dev_ptr(out)))
+    _check(ctx, st, "bh_solve_graph")
 
 
 def bh_potential(ctx, theta: float, G: float, out) -> None:
@@ -234,10 +285,48 @@ class Solver:
         self._ctx = bh_create(o, device, stream.cuda_stream)
         self.ncells = 0
 
+    def _handoff(self, *tensors):
+        """Outputs are written on the library's stream: tie them to it and make
+        the caller's current stream wait for it."""
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        for t in tensors:
+            if t is not None:
+                t.record_stream(self.stream)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
     def build(self, level, ijk, density, box_lo=(0.0, 0.0, 0.0), box_len=1.0):
         bh_build(self._ctx, level, ijk, box_lo, box_len, density)
         self.ncells = 512 * len(level)
         return self
+
+    def build_batch(self, nblocks, level, ijk, density, box_lo=None, box_len=None):
+        """Several fields at once (see bh_build_batch)."""
+        nf = len(nblocks)
+        box_lo = np.zeros((nf, 3)) if box_lo is None else box_lo
+        box_len = np.ones(nf) if box_len is None else box_len
+        bh_build_batch(self._ctx, nblocks, level, ijk, box_lo, box_len, density)
+        self.ncells = 512 * int(np.sum(nblocks))
+        return self
+
+    def update_density(self, density):
+        bh_update_density(self._ctx, density)
+
+    def sync_status(self):
+        bh_sync_status(self._ctx)
+
+    def autotune(self, theta: float) -> int:
+        return bh_autotune(self._ctx, theta)
+
+    def solve_graph(self, density, theta: float, G: float = 1.0, out=None):
+        import torch
+        if out is None:
+            dt = torch.float64 if self.options.precision == BH_PREC_F64 else torch.float32
+            out = torch.empty(self.ncells, dtype=dt, device=self.device)
+        bh_solve_graph(self._ctx, density, theta, G, out)
+        self._handoff(out)
+        return out
 
     def potential(self, theta: float, G: float = 1.0, out=None):
         import torch
@@ -245,6 +334,7 @@ class Solver:
             dt = torch.float64 if self.options.precision == BH_PREC_F64 else torch.float32
             out = torch.empty(self.ncells, dtype=dt, device=self.device)
         bh_potential(self._ctx, theta, G, out)
+        self._handoff(out)
         return out
 
     def walk_counts(self, theta: float, with_cells: bool = False):
@@ -255,6 +345,7 @@ class Solver:
         nt = torch.empty(self.ncells, dtype=torch.int32, device=self.device)
         nc = torch.empty(self.ncells, dtype=torch.int32, device=self.device) if with_cells else None
         bh_walk_counts(self._ctx, theta, ni, nt, nc)
+        self._handoff(ni, nt, nc)
         return (ni, nt, nc) if with_cells else (ni, nt)
 
     def tree_size(self):
@@ -270,6 +361,7 @@ class Solver:
                    skip=torch.empty(n, dtype=torch.int32, device=d),
                    level=torch.empty(n, dtype=torch.int32, device=d))
         bh_export_nodes(self._ctx, **out)
+        self._handoff(*out.values())
         return out
 
     def export_quadrupoles(self):
@@ -277,6 +369,7 @@ class Solver:
         _, n, _ = self.tree_size()
         q = torch.empty((n, 6), dtype=torch.float64, device=self.device)
         bh_export_quadrupoles(self._ctx, q)
+        self._handoff(q)
         return q
 
     def solve_host(self, level, ijk, density_host, theta, G=1.0, out_host=None,

@@ -1,6 +1,7 @@
-// C-ABI of libbhgrav: argument checking, buffer ownership and the order of
-// the build and walk launches.  The arithmetic lives in bh_build.cu and
-// bh_walk.cu; this file holds no kernels.
+// C-ABI of libbhgrav: argument checking, buffer ownership, the order of the
+// build and walk launches, and the batched (CUDA graph) solve.  The method's
+// arithmetic lives in bh_build.cu and bh_walk.cu; this file only holds the
+// small export kernels.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -54,6 +55,8 @@ void free_blocks(bhg::Tree &t) {
   release(t.d_prestart);
   release(t.d_blk);
   release(t.d_orig);
+  release(t.d_fid);
+  release(t.d_fld);
   t.nb_cap = 0;
 }
 
@@ -83,6 +86,8 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   BH_CUDA(cudaMalloc(&t.d_prestart, n * sizeof(int)));
   BH_CUDA(cudaMalloc(&t.d_blk, n * sizeof(int4)));
   BH_CUDA(cudaMalloc(&t.d_orig, n * sizeof(int)));
+  BH_CUDA(cudaMalloc(&t.d_fid, n * sizeof(int)));
+  BH_CUDA(cudaMalloc(&t.d_fld, n * sizeof(int4)));
   t.nb_cap = nb;
   return BH_OK;
 }
@@ -109,6 +114,158 @@ bh_status ensure_nodes(bh_ctx *ctx, int64_t n_nodes) {
 
 bh_status use_device(bh_ctx *ctx) {
   BH_CUDA(cudaSetDevice(ctx->device));
+  return BH_OK;
+}
+
+void free_fields(bhg::Tree &t) {
+  release(t.d_fstart);
+  release(t.d_invL);
+  release(t.d_L);
+  t.nf_cap = 0;
+}
+
+void drop_graph(bhg::Tree &t) {
+  if (t.graph_exec) cudaGraphExecDestroy(t.graph_exec);
+  if (t.graph) cudaGraphDestroy(t.graph);
+  t.graph_exec = nullptr;
+  t.graph = nullptr;
+  t.graph_density = nullptr;
+  t.graph_out = nullptr;
+}
+
+bh_status ensure_fields(bh_ctx *ctx, int nfields) {
+  bhg::Tree &t = ctx->tree;
+  if (t.nf_cap >= nfields) return BH_OK;
+  release(t.d_fstart);
+  release(t.d_invL);
+  release(t.d_L);
+  t.nf_cap = 0;
+  BH_CUDA(cudaMalloc(&t.d_fstart, (size_t)(nfields + 1) * sizeof(int)));
+  BH_CUDA(cudaMalloc(&t.d_invL, (size_t)nfields * sizeof(double)));
+  BH_CUDA(cudaMalloc(&t.d_L, (size_t)nfields * sizeof(double)));
+  t.nf_cap = nfields;
+  return BH_OK;
+}
+
+bhg::FieldArgs field_args(bhg::Tree &t) {
+  bhg::FieldArgs fa;
+  fa.nfields = t.nfields;
+  fa.fstart = t.d_fstart;
+  fa.fid = t.d_fid;
+  fa.fld = t.d_fld;
+  fa.invL = t.d_invL;
+  fa.L = t.d_L;
+  return fa;
+}
+
+// Moments of the current geometry from a density (k_blocks + one launch per
+// level above the blocks); stream-ordered, no host synchronisation.
+bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64) {
+  bhg::Tree &t = ctx->tree;
+  cudaStream_t s = ctx->stream;
+  // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
+  double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
+  bhg::WalkQuad *qrec = ctx->opt.quadrupole ? t.d_qrec : nullptr;
+  const bhg::FieldArgs fa = field_args(t);
+  BH_CUDA(bhg::launch_blocks(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
+                             density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl,
+                             q64, qrec, t.d_flags));
+  for (int lev = t.max_block_level - 1; lev >= 0; --lev)
+    BH_CUDA(bhg::launch_top_moments(s, t.nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
+                                    t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags));
+  return BH_OK;
+}
+
+// Tree and moments of nfields meshes (one field = bh_build).  Synchronises
+// once to report geometry and density errors.
+bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
+                       const int32_t *ijk, const double *box_lo, const double *box_len,
+                       const void *density, int density_is_fp64, const char *who) {
+  bhg::Tree &t = ctx->tree;
+  t.built = false;
+  drop_graph(t);
+  if (nfields <= 0 || !nblocks || !level || !ijk || !box_lo || !box_len || !density)
+    return fail(ctx, BH_ERR_ARG, "%s: nblocks must be >= 1 and pointers non-null", who);
+  if (density_is_fp64 != 0 && density_is_fp64 != 1)
+    return fail(ctx, BH_ERR_ARG, "%s: density_is_fp64 must be 0 or 1", who);
+  std::vector<int> fstart(nfields + 1, 0);
+  std::vector<double> invL(nfields), L(nfields);
+  int64_t nb64 = 0, n_nodes = 0, tops = 0;
+  for (int f = 0; f < nfields; ++f) {
+    const int nbf = nblocks[f];
+    if (nbf <= 0) return fail(ctx, BH_ERR_ARG, "%s: field %d has no blocks", who, f);
+    if (!(box_len[f] > 0.0) || !std::isfinite(box_len[f]) || !std::isfinite(box_lo[3 * f]) ||
+        !std::isfinite(box_lo[3 * f + 1]) || !std::isfinite(box_lo[3 * f + 2]))
+      return fail(ctx, BH_ERR_ARG, "%s: box_len must be finite and > 0, box_lo finite", who);
+    // a tiling has nb = 1 + 7k blocks
+    if ((nbf - 1) % 7 != 0)
+      return fail(ctx, BH_ERR_GEOMETRY, "%s: %d blocks cannot tile a cube (need 1 + 7k)", who,
+                  nbf);
+    fstart[f] = (int)nb64;
+    nb64 += nbf;
+    tops += (nbf - 1) / 7;
+    n_nodes += (int64_t)bhg::kNodesPerBlock * nbf + (nbf - 1) / 7;
+    L[f] = box_len[f];
+    invL[f] = 1.0 / box_len[f];
+  }
+  // node indices must fit 31 bits
+  if (n_nodes >= (int64_t)0x7fffffff || nb64 >= (int64_t)0x7fffffff)
+    return fail(ctx, BH_ERR_ARG, "%s: %lld blocks exceed the 2^31 node limit", who,
+                (long long)nb64);
+  const int nb = (int)nb64;
+  fstart[nfields] = nb;
+  int max_level = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (level[b] < 0 || level[b] > bhg::kMaxBlockLevel)
+      return fail(ctx, BH_ERR_GEOMETRY, "%s: block %d has level %d outside [0, 18]", who, b,
+                  level[b]);
+    max_level = level[b] > max_level ? level[b] : max_level;
+  }
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  if ((st = ensure_blocks(ctx, nb)) != BH_OK) return st;
+  if ((st = ensure_fields(ctx, nfields)) != BH_OK) return st;
+  if ((st = ensure_nodes(ctx, n_nodes)) != BH_OK) return st;
+  t.nfields = nfields;
+  t.nb = nb;
+  t.n_nodes = n_nodes;
+  t.max_block_level = max_level;
+  t.h_L = L;
+  cudaStream_t s = ctx->stream;
+  const bhg::FieldArgs fa = field_args(t);
+  BH_CUDA(cudaMemsetAsync(t.d_flags, 0, 4 * sizeof(unsigned), s));
+  BH_CUDA(cudaMemcpyAsync(t.d_level, level, nb * sizeof(int), cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaMemcpyAsync(t.d_ijk, ijk, 3 * (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaMemcpyAsync(t.d_fstart, fstart.data(), (nfields + 1) * sizeof(int),
+                          cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaMemcpyAsync(t.d_invL, invL.data(), nfields * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaMemcpyAsync(t.d_L, L.data(), nfields * sizeof(double), cudaMemcpyHostToDevice, s));
+  BH_CUDA(bhg::launch_block_keys(s, nb, t.d_level, t.d_ijk, t.d_key[0], t.d_idx[0], t.d_flags,
+                                 fa));
+  BH_CUDA(bhg::launch_sort_blocks(s, t.d_key, t.d_idx, t.d_flags, fa));
+  BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
+                                     t.d_count, t.d_blk, t.d_orig, t.d_flags, fa));
+  BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
+  BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
+                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig));
+  if ((st = enqueue_moments(ctx, density, density_is_fp64)) != BH_OK) return st;
+  BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  BH_CUDA(cudaStreamSynchronize(s));
+  const unsigned e = t.h_flags[0];
+  if (e & (bhg::kErrLevel | bhg::kErrCoord))
+    return fail(ctx, BH_ERR_GEOMETRY, "%s: a block coordinate lies outside its level", who);
+  if (e & bhg::kErrTiling)
+    return fail(ctx, BH_ERR_GEOMETRY, "%s: the blocks do not tile the box (gap or overlap)", who);
+  if ((int64_t)t.h_flags[2] != tops || (e & bhg::kErrIndex))
+    return fail(ctx, BH_ERR_GEOMETRY, "%s: inconsistent block tree (%u internal nodes)", who,
+                t.h_flags[2]);
+  if (e & bhg::kErrDensity)
+    return fail(ctx, BH_ERR_ARG, "%s: density has a negative or non-finite value", who);
+  for (int a = 0; a < 3; ++a) t.lo[a] = box_lo[a];
+  t.L = box_len[0];
+  t.s2_inv_theta = -1.0f;
+  t.built = true;
   return BH_OK;
 }
 
@@ -162,73 +319,52 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
                    int density_is_fp64) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
-  bhg::Tree &t = ctx->tree;
-  t.built = false;
-  if (nblocks <= 0 || !level || !ijk || !box_lo || !density)
+  if (nblocks <= 0) {
+    ctx->tree.built = false;
     return fail(ctx, BH_ERR_ARG, "bh_build: nblocks must be >= 1 and pointers non-null");
-  if (!(box_len > 0.0) || !std::isfinite(box_len) || !std::isfinite(box_lo[0]) ||
-      !std::isfinite(box_lo[1]) || !std::isfinite(box_lo[2]))
-    return fail(ctx, BH_ERR_ARG, "bh_build: box_len must be finite and > 0, box_lo finite");
-  if (density_is_fp64 != 0 && density_is_fp64 != 1)
-    return fail(ctx, BH_ERR_ARG, "bh_build: density_is_fp64 must be 0 or 1");
-  // a tiling has nb = 1 + 7k blocks; node count must fit a 32-bit index
-  if ((nblocks - 1) % 7 != 0)
-    return fail(ctx, BH_ERR_GEOMETRY, "bh_build: %d blocks cannot tile a cube (need 1 + 7k)",
-                nblocks);
-  const int64_t n_nodes = (int64_t)bhg::kNodesPerBlock * nblocks + (nblocks - 1) / 7;
-  if (n_nodes >= (int64_t)0x7fffffff)
-    return fail(ctx, BH_ERR_ARG, "bh_build: %d blocks exceed the 2^31 node limit", nblocks);
-  int max_level = 0;
-  for (int b = 0; b < nblocks; ++b) {
-    if (level[b] < 0 || level[b] > bhg::kMaxBlockLevel)
-      return fail(ctx, BH_ERR_GEOMETRY, "bh_build: block %d has level %d outside [0, 18]", b,
-                  level[b]);
-    max_level = level[b] > max_level ? level[b] : max_level;
   }
+  const int32_t nb = nblocks;
+  return build_fields(ctx, 1, &nb, level, ijk, box_lo, &box_len, density, density_is_fp64,
+                      "bh_build");
+}
+
+bh_status bh_build_batch(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
+                         const int32_t *ijk, const double *box_lo, const double *box_len,
+                         const void *density, int density_is_fp64) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  return build_fields(ctx, nfields, nblocks, level, ijk, box_lo, box_len, density,
+                      density_is_fp64, "bh_build_batch");
+}
+
+bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp64) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
+  if (!density || (density_is_fp64 != 0 && density_is_fp64 != 1))
+    return fail(ctx, BH_ERR_ARG, "bh_update_density: bad density");
   bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
-  if ((st = ensure_blocks(ctx, nblocks)) != BH_OK) return st;
-  if ((st = ensure_nodes(ctx, n_nodes)) != BH_OK) return st;
-  cudaStream_t s = ctx->stream;
-  const int nb = nblocks;
-  // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
-  double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
-  bhg::WalkQuad *qrec = ctx->opt.quadrupole ? t.d_qrec : nullptr;
-  BH_CUDA(cudaMemsetAsync(t.d_flags, 0, 4 * sizeof(unsigned), s));
-  BH_CUDA(cudaMemcpyAsync(t.d_level, level, nb * sizeof(int), cudaMemcpyHostToDevice, s));
-  BH_CUDA(cudaMemcpyAsync(t.d_ijk, ijk, 3 * (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, s));
-  BH_CUDA(bhg::launch_block_keys(s, nb, t.d_level, t.d_ijk, t.d_key[0], t.d_idx[0], t.d_flags));
-  BH_CUDA(bhg::launch_sort_blocks(s, nb, t.d_key, t.d_idx, t.d_flags, nullptr));
-  BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
-                                     t.d_count, t.d_blk, t.d_orig, t.d_flags));
-  BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
-  BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
-                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags));
-  BH_CUDA(bhg::launch_blocks(s, nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
-                             density_is_fp64, box_len, n_nodes, t.d_mom, t.d_rec, t.d_aux,
-                             t.d_lvl, q64, qrec, t.d_flags));
-  for (int lev = max_level - 1; lev >= 0; --lev)
-    BH_CUDA(bhg::launch_top_moments(s, nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
-                                    n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags));
-  BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  BH_CUDA(cudaStreamSynchronize(s));
-  const unsigned e = t.h_flags[0];
-  if (e & (bhg::kErrLevel | bhg::kErrCoord))
-    return fail(ctx, BH_ERR_GEOMETRY, "bh_build: a block coordinate lies outside its level");
-  if (e & bhg::kErrTiling)
-    return fail(ctx, BH_ERR_GEOMETRY, "bh_build: the blocks do not tile the box (gap or overlap)");
-  if ((int64_t)t.h_flags[2] != (nb - 1) / 7 || (e & bhg::kErrIndex))
-    return fail(ctx, BH_ERR_GEOMETRY, "bh_build: inconsistent block tree (%u internal nodes)",
-                t.h_flags[2]);
-  if (e & bhg::kErrDensity)
-    return fail(ctx, BH_ERR_ARG, "bh_build: density has a negative or non-finite value");
-  t.nb = nb;
-  t.max_block_level = max_level;
-  t.n_nodes = n_nodes;
-  for (int a = 0; a < 3; ++a) t.lo[a] = box_lo[a];
-  t.L = box_len;
-  t.s2_inv_theta = -1.0f;
-  t.built = true;
+  BH_CUDA(cudaMemsetAsync(ctx->tree.d_flags, 0, sizeof(unsigned), ctx->stream));
+  // the records are rewritten (s2 included, and delta changes with the
+  // density): the next walk must prepare s2 again
+  ctx->tree.s2_inv_theta = -1.0f;
+  return enqueue_moments(ctx, density, density_is_fp64);
+}
+
+bh_status bh_sync_status(bh_ctx *ctx) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  bhg::Tree &t = ctx->tree;
+  BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  BH_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (t.h_flags[0] & bhg::kErrDensity)
+    return fail(ctx, BH_ERR_ARG, "density has a negative or non-finite value");
+  if (t.h_flags[0] & ~bhg::kErrDensity)
+    return fail(ctx, BH_ERR_GEOMETRY, "device error flags 0x%x", t.h_flags[0]);
   return BH_OK;
 }
 
@@ -256,9 +392,9 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  const double scale = -G / t.L;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_qrec,
-                           t.d_q64, t.d_blk, t.d_orig, scale, out, nullptr, nullptr));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
+                           t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr, nullptr,
+                           t.wpc));
   return BH_OK;
 }
 
@@ -271,9 +407,9 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.n_nodes, t.d_rec, t.d_mom, t.d_qrec,
-                           t.d_q64, t.d_blk, t.d_orig, 0.0, nullptr, n_int, n_test,
-                           n_cell));
+  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
+                           t.d_blk, t.d_orig, field_args(t), 0.0, nullptr, n_int, n_test, n_cell,
+                           t.wpc));
   return BH_OK;
 }
 
@@ -361,6 +497,109 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
   return BH_OK;
 }
 
+bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  bh_status st = prepare(ctx, theta);
+  if (st != BH_OK) return st;
+  bhg::Tree &t = ctx->tree;
+  const bool tunable = ctx->opt.precision == BH_PREC_F32 &&
+                       ctx->opt.criterion == BH_CRIT_PER_CELL;
+  if (tunable) {
+    const int64_t out_bytes = (int64_t)t.nb * bhg::kCellsPerBlock * sizeof(float);
+    if (t.stage_out_bytes < out_bytes) {
+      release(t.d_stage_out);
+      t.stage_out_bytes = 0;
+      BH_CUDA(cudaMalloc(&t.d_stage_out, out_bytes));
+      t.stage_out_bytes = out_bytes;
+    }
+    cudaEvent_t e0, e1;
+    BH_CUDA(cudaEventCreate(&e0));
+    BH_CUDA(cudaEventCreate(&e1));
+    const int cand[4] = {2, 4, 8, 16};
+    float best = 1e30f;
+    int best_w = 8;
+    for (int w : cand) {
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        BH_CUDA(cudaEventRecord(e0, ctx->stream));
+        BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec,
+                                 t.d_q64, t.d_blk, t.d_orig, field_args(t), 1.0, t.d_stage_out,
+                                 nullptr, nullptr, nullptr, w));
+        BH_CUDA(cudaEventRecord(e1, ctx->stream));
+        BH_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        tmin = ms < tmin ? ms : tmin;
+      }
+      if (tmin < best) {
+        best = tmin;
+        best_w = w;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t.wpc = best_w;
+    drop_graph(t);
+  }
+  if (warps_per_cta) *warps_per_cta = tunable ? t.wpc : 0;
+  return BH_OK;
+}
+
+bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, double theta,
+                         double G, void *out) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  bhg::Tree &t = ctx->tree;
+  if (!t.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build or bh_build_batch first");
+  if (!density || !out || (density_is_fp64 != 0 && density_is_fp64 != 1))
+    return fail(ctx, BH_ERR_ARG, "bh_solve_graph: null buffer or bad density type");
+  if (!(theta > 0.0) || !(theta <= 1.0) || !std::isfinite(G))
+    return fail(ctx, BH_ERR_ARG, "bh_solve_graph: theta must lie in (0, 1] and G be finite");
+  if (!ctx->stream)
+    return fail(ctx, BH_ERR_ARG, "bh_solve_graph: needs a context on a created (non-default) "
+                                 "CUDA stream");
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  const bool same = t.graph_exec && t.graph_density == density && t.graph_out == out &&
+                    t.graph_fp64 == density_is_fp64 && t.graph_theta == theta && t.graph_G == G;
+  if (!same) {
+    drop_graph(t);
+    if (t.wpc == 0 && (st = bh_autotune(ctx, theta, nullptr)) != BH_OK) return st;
+    cudaStream_t s = ctx->stream;
+    BH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    bh_status cap = BH_OK;
+    cudaError_t e = cudaMemsetAsync(t.d_flags, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+      cap = enqueue_moments(ctx, density, density_is_fp64);
+      if (cap == BH_OK)
+        e = bhg::launch_prepare_s2(s, t.n_nodes, t.d_aux, t.d_rec, (float)(1.0 / theta));
+      if (cap == BH_OK && e == cudaSuccess)
+        e = bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
+                             t.d_orig, field_args(t), G, out, nullptr, nullptr, nullptr, t.wpc);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &g);
+    if (cap != BH_OK || e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return cap != BH_OK ? cap
+                          : fail(ctx, BH_ERR_CUDA, "bh_solve_graph: capture failed: %s",
+                                 cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    t.graph = g;
+    BH_CUDA(cudaGraphInstantiate(&t.graph_exec, t.graph, 0));
+    t.graph_density = density;
+    t.graph_out = out;
+    t.graph_fp64 = density_is_fp64;
+    t.graph_theta = theta;
+    t.graph_G = G;
+  }
+  BH_CUDA(cudaGraphLaunch(t.graph_exec, ctx->stream));
+  t.s2_inv_theta = (float)(1.0 / theta);
+  return BH_OK;
+}
+
 bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
                         const double *box_lo, double box_len, const void *density_host,
                         int density_is_fp64, double theta, double G, void *out_host) {
@@ -404,8 +643,10 @@ void bh_destroy(bh_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx->tree);
   free_blocks(ctx->tree);
   free_nodes(ctx->tree);
+  free_fields(ctx->tree);
   release(ctx->tree.d_stage_in);
   release(ctx->tree.d_stage_out);
   release(ctx->tree.d_flags);

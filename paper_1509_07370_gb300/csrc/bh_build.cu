@@ -23,6 +23,14 @@
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
+//
+// Several independent fields (meshes, each in its own box) can be built at
+// once: their block lists are concatenated (fstart[f] = first block of field
+// f), blocks are sorted within their field, every field gets its own tree,
+// and the trees' pre-order node ranges follow each other in one node array.
+// The formulas above hold unchanged over the concatenation: the pre-order
+// index of the first node of block p is still 585 p + (top nodes before p),
+// and a field's range ends where the next field's first node starts.
 #include "bh_internal.cuh"
 
 namespace bhg {
@@ -52,19 +60,33 @@ __device__ __forceinline__ bool valid_block(int lb, int i, int j, int k, unsigne
   return true;
 }
 
+// Field of caller block b: the last f with fstart[f] <= b.
+__device__ __forceinline__ int field_of(int b, int nfields, const int *fstart) {
+  int a = 0, e = nfields;  // invariant: fstart[a] <= b < fstart[e]
+  while (e - a > 1) {
+    const int m = (a + e) >> 1;
+    if (fstart[m] <= b) a = m; else e = m;
+  }
+  return a;
+}
+
 __global__ void k_block_keys(int nb, const int *__restrict__ level, const int *__restrict__ ijk,
                              unsigned long long *__restrict__ key, int *__restrict__ idx,
-                             unsigned *flags) {
+                             unsigned *flags, int nfields, const int *__restrict__ fstart,
+                             int *__restrict__ fid) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
+  const int f = field_of(b, nfields, fstart);
+  fid[b] = f;
   const int lb = level[b];
   const int i = ijk[3 * b], j = ijk[3 * b + 1], k = ijk[3 * b + 2];
   unsigned long long kb = ~0ull;
   if (valid_block(lb, i, j, k, flags)) kb = block_key(lb, i, j, k);
   key[b] = kb;
   idx[b] = b;
-  // is the caller's order already the key order?  (compare with block b+1)
-  if (b + 1 < nb) {
+  // is the caller's order already the key order?  (compare with block b+1
+  // of the same field)
+  if (b + 1 < fstart[f + 1]) {
     const int l2 = level[b + 1];
     unsigned long long k2 = ~0ull;
     if (l2 >= 0 && l2 <= kMaxBlockLevel) k2 = block_key(l2, ijk[3 * b + 3], ijk[3 * b + 4], ijk[3 * b + 5]);
@@ -72,15 +94,21 @@ __global__ void k_block_keys(int nb, const int *__restrict__ level, const int *_
   }
 }
 
-// Stable LSD radix sort of (key, idx) in one CTA, 4 bits per pass, 16
-// passes, result back in buffer 0.  Block lists are small (a 16M-cell mesh
-// has ~32k blocks), and the sort only runs when the caller's block order is
-// not already the Morton order.
+// Stable LSD radix sort of (key, idx), one CTA per field (its segment of the
+// block list), 4 bits per pass, 16 passes, result back in buffer 0.  Block
+// lists are small (a 16M-cell mesh has ~32k blocks), and the sort only runs
+// when the caller's block order is not already the Morton order.
 constexpr int kSortThreads = 512;
 __global__ void __launch_bounds__(kSortThreads)
-    k_sort_blocks(int n, unsigned long long *k0, int *v0, unsigned long long *k1, int *v1,
-                  const unsigned *flags) {
+    k_sort_blocks(const int *__restrict__ fstart, unsigned long long *k0, int *v0,
+                  unsigned long long *k1, int *v1, const unsigned *flags) {
   if (flags[1] == 0u) return;  // already sorted
+  const int off = fstart[blockIdx.x];
+  const int n = fstart[blockIdx.x + 1] - off;
+  k0 += off;
+  v0 += off;
+  k1 += off;
+  v1 += off;
   __shared__ int hist[16 * kSortThreads];
   __shared__ int part[kSortThreads];
   const int t = threadIdx.x;
@@ -138,16 +166,18 @@ __global__ void k_tile_and_count(int nb, const unsigned long long *__restrict__ 
                                  const int *__restrict__ idx, const int *__restrict__ level,
                                  const int *__restrict__ ijk, int *__restrict__ count,
                                  int4 *__restrict__ blk, int *__restrict__ orig,
-                                 unsigned *flags) {
+                                 unsigned *flags, const int *__restrict__ fstart,
+                                 const int *__restrict__ fid) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int b = idx[p];
   const int lb = level[b];
   const unsigned long long kp = key[p];
+  const int f = fid[b];
   int cnt = 0;
   if (kp != ~0ull && lb >= 0 && lb <= kMaxBlockLevel) {
     bool ok = true;
-    if (p == 0) {
+    if (p == fstart[f]) {
       ok = ok && kp == 0ull;
     } else {
       const int lprev = level[idx[p - 1]];
@@ -155,7 +185,7 @@ __global__ void k_tile_and_count(int nb, const unsigned long long *__restrict__ 
       ok = ok && kprev != ~0ull && lprev >= 0 && lprev <= kMaxBlockLevel &&
            kprev + key_span(lprev) == kp;
     }
-    if (p == nb - 1) ok = ok && kp + key_span(lb) == (1ull << 63);
+    if (p == fstart[f + 1] - 1) ok = ok && kp + key_span(lb) == (1ull << 63);
     if (!ok) atomicOr(flags, kErrTiling);
     cnt = max(0, lb - top_start_level(kp));
   }
@@ -199,13 +229,22 @@ __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023,
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// Also records, per block, its field's node range: fld[p] = {first node of
+// the field (its root), one past its last node, first block of the next
+// field, field index}.
 __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
                             const int4 *__restrict__ blk, const int *__restrict__ count,
                             const int *__restrict__ prestart, int64_t n_nodes,
                             WalkRec *__restrict__ rec, float2 *__restrict__ aux,
-                            uint8_t *__restrict__ lvl, unsigned *flags) {
+                            uint8_t *__restrict__ lvl, unsigned *flags, int nfields,
+                            const int *__restrict__ fstart, const int *__restrict__ fid,
+                            const int *__restrict__ orig, int4 *__restrict__ fld) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
+  const int f = fid[orig[p]];
+  const int fend = fstart[f + 1];
+  const int64_t node_end = fend < nb ? (int64_t)prestart[fend] : n_nodes;
+  fld[p] = make_int4(prestart[fstart[f]], (int)node_end, fend, f);
   const int cnt = count[p];
   if (cnt == 0) return;
   const int lb = blk[p].x;
@@ -215,12 +254,12 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
     const int64_t id = (int64_t)prestart[p] + (k - j0);
     // first block whose key lies beyond this cube: its first node follows the subtree
     const unsigned long long lim = kp + (1ull << (3 * (kKeyLevels - k)));
-    int a = p + 1, e = nb;
+    int a = p + 1, e = fend;
     while (a < e) {
       const int m = (a + e) >> 1;
       if (key[m] < lim) a = m + 1; else e = m;
     }
-    const int64_t skip = a < nb ? (int64_t)prestart[a] : n_nodes;
+    const int64_t skip = a < fend ? (int64_t)prestart[a] : node_end;
     if (id < 0 || id >= n_nodes || skip > n_nodes) {
       atomicOr(flags, kErrIndex);
       continue;
@@ -361,7 +400,8 @@ template <typename T>
 __global__ void __launch_bounds__(kBlockThreads)
     k_blocks(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
              const int *__restrict__ count, const int *__restrict__ prestart,
-             const T *__restrict__ density, double L, int64_t n_nodes,
+             const T *__restrict__ density, const double *__restrict__ Lf,
+             const int *__restrict__ fid, int64_t n_nodes,
              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec, float2 *__restrict__ aux,
              uint8_t *__restrict__ lvl, double *__restrict__ q64, WalkQuad *__restrict__ qrec,
              unsigned *flags) {
@@ -383,6 +423,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     return;
   }
   const int lc = lb + 3;
+  const double L = Lf[fid[orig[p]]];          // box side of this block's field
   const double hs = pow2d(-lc);               // cell side, box units
   const double h = __dmul_rn(L, hs);          // cell side, physical
   const double vol = __dmul_rn(__dmul_rn(h, h), h);
@@ -568,22 +609,25 @@ inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / t
 }  // namespace
 
 cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
-                              unsigned long long *key, int *idx, unsigned *flags) {
-  k_block_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, ijk, key, idx, flags);
+                              unsigned long long *key, int *idx, unsigned *flags,
+                              const FieldArgs &fa) {
+  k_block_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
+                                                  fa.fstart, fa.fid);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort_blocks(cudaStream_t s, int nb, unsigned long long *key[2], int *idx[2],
-                               unsigned *flags, int *) {
-  k_sort_blocks<<<1, kSortThreads, 0, s>>>(nb, key[0], idx[0], key[1], idx[1], flags);
+cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *idx[2],
+                               unsigned *flags, const FieldArgs &fa) {
+  k_sort_blocks<<<fa.nfields, kSortThreads, 0, s>>>(fa.fstart, key[0], idx[0], key[1], idx[1],
+                                                     flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk, int *count,
-                                  int4 *blk, int *orig, unsigned *flags) {
+                                  int4 *blk, int *orig, unsigned *flags, const FieldArgs &fa) {
   k_tile_and_count<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, idx, level, ijk, count, blk, orig,
-                                                      flags);
+                                                      flags, fa.fstart, fa.fid);
   return cudaGetLastError();
 }
 
@@ -596,25 +640,26 @@ cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
-                             unsigned *flags) {
+                             unsigned *flags, const FieldArgs &fa, const int *orig) {
   k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec,
-                                                 aux, lvl, flags);
+                                                 aux, lvl, flags, fa.nfields, fa.fstart, fa.fid,
+                                                 orig, fa.fld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
-                          int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64, WalkQuad *qrec,
-                          unsigned *flags) {
+                          int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
+                          double4_32a *mom, WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
+                          WalkQuad *qrec, unsigned *flags) {
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                   (const double *)density, L, n_nodes, mom,
-                                                   rec, aux, lvl, q64, qrec, flags);
+                                                   (const double *)density, fa.L, fa.fid,
+                                                   n_nodes, mom, rec, aux, lvl, q64, qrec, flags);
   else
     k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                  (const float *)density, L, n_nodes, mom, rec,
-                                                  aux, lvl, q64, qrec, flags);
+                                                  (const float *)density, fa.L, fa.fid, n_nodes,
+                                                  mom, rec, aux, lvl, q64, qrec, flags);
   return cudaGetLastError();
 }
 

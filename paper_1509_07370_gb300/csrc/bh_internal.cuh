@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "bhgrav.h"  // -I include
 
 namespace bhg {
@@ -70,6 +72,23 @@ struct Tree {
   int *d_orig = nullptr;
   unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total
   unsigned *h_flags = nullptr;  // pinned mirror of d_flags
+  // fields
+  int nfields = 0;
+  int *d_fstart = nullptr;      // nfields + 1
+  int *d_fid = nullptr;         // per caller block
+  int4 *d_fld = nullptr;        // per sorted block
+  double *d_invL = nullptr;     // per field
+  double *d_L = nullptr;        // per field
+  int nf_cap = 0;
+  std::vector<double> h_L;      // per field, host copy
+  // batched solve: CUDA graph of (moments for new densities + walk)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void *graph_density = nullptr;
+  void *graph_out = nullptr;
+  int graph_fp64 = -1;
+  double graph_theta = 0.0, graph_G = 0.0;
+  int wpc = 0;                  // tuned warps per CTA of the walk (0 = default)
   int64_t nb_cap = 0;
   // node arrays (capacity node_cap)
   double4_32a *d_mom = nullptr;
@@ -93,26 +112,42 @@ struct Tree {
   float s2_inv_theta = -1.0f;  // inverse theta the s2 field was prepared for
 };
 
+// Several fields (independent meshes) built and walked together: their
+// blocks are concatenated; fstart[f] .. fstart[f+1]-1 are field f's blocks
+// (nfields + 1 entries), fid[b] the field of caller block b, fld[p] = {first
+// node, end node, first block of the next field, field} per sorted block, and
+// invL[f] = 1 / box side of field f.  One field is the ordinary case.
+struct FieldArgs {
+  int nfields;
+  const int *fstart;
+  int *fid;
+  int4 *fld;
+  const double *invL;
+  const double *L;   // box side per field
+};
+
 // ---- build kernels (bh_build.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
 cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
-                              unsigned long long *key, int *idx, unsigned *flags);
-cudaError_t launch_sort_blocks(cudaStream_t s, int nb, unsigned long long *key[2], int *idx[2],
-                               unsigned *flags, int *which_out_host_unused);
+                              unsigned long long *key, int *idx, unsigned *flags,
+                              const FieldArgs &fa);
+cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *idx[2],
+                               unsigned *flags, const FieldArgs &fa);
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk,
-                                  int *count, int4 *blk, int *orig, unsigned *flags);
+                                  int *count, int4 *blk, int *orig, unsigned *flags,
+                                  const FieldArgs &fa);
 cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
                                  unsigned *flags);
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
-                             unsigned *flags);
+                             unsigned *flags, const FieldArgs &fa, const int *orig);
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
-                          int density_is_fp64, double L, int64_t n_nodes, double4_32a *mom,
-                          WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64, WalkQuad *qrec,
-                          unsigned *flags);
+                          int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
+                          double4_32a *mom, WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
+                          WalkQuad *qrec, unsigned *flags);
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
@@ -122,10 +157,13 @@ cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned
 cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
                               float inv_theta);
 // out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
-cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
-                        const double *q64, const int4 *blk, const int *orig, double scale,
-                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf = nullptr);
+// Potential scale of field f: -G * invL[f].  wpc = warps per CTA of the
+// per-cell binary32 walk (0 = default), a tunable launch shape.
+cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
+                        const double4_32a *mom, const WalkQuad *qrec, const double *q64,
+                        const int4 *blk, const int *orig, const FieldArgs &fa, double G,
+                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf = nullptr,
+                        int wpc = 0);
 
 // ---- small device helpers ---------------------------------------------------
 // Spread the low 21 bits of v so bit b lands at bit 3b.

@@ -48,7 +48,11 @@ constexpr size_t kOffPrestart = up256(kOffCount + sizeof(int) * kNoAllocMaxBlock
 constexpr size_t kOffBlk = up256(kOffPrestart + sizeof(int) * kNoAllocMaxBlocks);
 constexpr size_t kOffOrig = up256(kOffBlk + sizeof(int4) * kNoAllocMaxBlocks);
 constexpr size_t kOffFlags = up256(kOffOrig + sizeof(int) * kNoAllocMaxBlocks);
-constexpr size_t kOffMom = up256(kOffFlags + 4 * sizeof(unsigned));
+constexpr size_t kOffFstart = up256(kOffFlags + 4 * sizeof(unsigned));   // one field
+constexpr size_t kOffFid = up256(kOffFstart + 2 * sizeof(int));
+constexpr size_t kOffFld = up256(kOffFid + sizeof(int) * kNoAllocMaxBlocks);
+constexpr size_t kOffBox = up256(kOffFld + sizeof(int4) * kNoAllocMaxBlocks);  // L, 1/L
+constexpr size_t kOffMom = up256(kOffBox + 2 * sizeof(double));
 constexpr size_t kOffRec = up256(kOffMom + sizeof(double4_32a) * kNoAllocMaxNodes);
 constexpr size_t kOffAux = up256(kOffRec + sizeof(WalkRec) * kNoAllocMaxNodes);
 constexpr size_t kOffLvl = up256(kOffAux + sizeof(float2) * kNoAllocMaxNodes);
@@ -63,11 +67,18 @@ struct Geometry {  // passed by value as a kernel parameter (1 KB)
   int ijk[3 * kNoAllocMaxBlocks];
 };
 
-// Copies the block geometry from the kernel parameter into the scratch and
-// clears the error flags of this call.
-__global__ void k_stage_geometry(Geometry g, int nb, int *level, int *ijk, unsigned *flags) {
+// Copies the block geometry from the kernel parameter into the scratch,
+// describes the single field, and clears the error flags of this call.
+__global__ void k_stage_geometry(Geometry g, int nb, int *level, int *ijk, unsigned *flags,
+                                 int *fstart, double *box, double L) {
   const int t = threadIdx.x;
   if (t < 4) flags[t] = 0u;
+  if (t == 0) {
+    fstart[0] = 0;
+    fstart[1] = nb;
+    box[0] = L;
+    box[1] = 1.0 / L;
+  }
   for (int i = t; i < nb; i += blockDim.x) level[i] = g.level[i];
   for (int i = t; i < 3 * nb; i += blockDim.x) ijk[i] = g.ijk[i];
 }
@@ -145,18 +156,27 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   WalkRec *d_rec = (WalkRec *)(base + kOffRec);
   float2 *d_aux = (float2 *)(base + kOffAux);
   uint8_t *d_lvl = (uint8_t *)(base + kOffLvl);
+  int *d_fstart = (int *)(base + kOffFstart);
+  double *d_box = (double *)(base + kOffBox);
+  FieldArgs fa;
+  fa.nfields = 1;
+  fa.fstart = d_fstart;
+  fa.fid = (int *)(base + kOffFid);
+  fa.fld = (int4 *)(base + kOffFld);
+  fa.L = d_box;
+  fa.invL = d_box + 1;
 
-  k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags);
+  k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags, d_fstart, d_box, box_len);
   NA_CUDA(cudaGetLastError());
-  NA_CUDA(launch_block_keys(s, nb, d_level, d_ijk, d_key[0], d_idx[0], d_flags));
-  NA_CUDA(launch_sort_blocks(s, nb, d_key, d_idx, d_flags, nullptr));
+  NA_CUDA(launch_block_keys(s, nb, d_level, d_ijk, d_key[0], d_idx[0], d_flags, fa));
+  NA_CUDA(launch_sort_blocks(s, d_key, d_idx, d_flags, fa));
   NA_CUDA(launch_tile_and_count(s, nb, d_key[0], d_idx[0], d_level, d_ijk, d_count, d_blk,
-                                d_orig, d_flags));
+                                d_orig, d_flags, fa));
   NA_CUDA(launch_prestart_scan(s, nb, d_count, d_prestart, d_flags));
   NA_CUDA(launch_top_nodes(s, nb, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_rec, d_aux,
-                           d_lvl, d_flags));
-  NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64,
-                        box_len, n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
+                           d_lvl, d_flags, fa, d_orig));
+  NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64, fa,
+                        n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
   for (int lev = max_level - 1; lev >= 0; --lev)
     NA_CUDA(launch_top_moments(s, nb, lev, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_mom,
                                d_rec, d_aux, nullptr, nullptr, d_flags));
@@ -170,7 +190,7 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   NA_CUDA(launch_prepare_s2(s, n_nodes, d_aux, d_rec, (float)(1.0 / theta)));
   bh_options opt;
   bh_default_options(&opt);
-  NA_CUDA(launch_walk(s, opt, nb, n_nodes, d_rec, d_mom, nullptr, nullptr, d_blk, d_orig,
-                      -G / box_len, out, nullptr, nullptr));
+  NA_CUDA(launch_walk(s, opt, nb, d_rec, d_mom, nullptr, nullptr, d_blk, d_orig, fa, G, out,
+                      nullptr, nullptr, nullptr, 0));
   return BH_OK;
 }

@@ -38,8 +38,9 @@
 namespace bhg {
 namespace {
 
-constexpr int kWalkThreads = 256;
+constexpr int kWalkThreads = 256;               // default CTA: 8 warps = one block
 constexpr int kWarpsPerCta = kWalkThreads / 32;
+constexpr int kMaxWalkThreads = 512;            // largest tunable CTA
 constexpr unsigned kFull = 0xffffffffu;
 typedef unsigned long long u64;
 
@@ -163,15 +164,18 @@ __device__ __forceinline__ u64 quad_term2(const WalkQuad *qr, u64 mm, u64 rr, u6
 // target whose walk does not contain a node has accepted one of its
 // ancestors and skipped past the ancestor's whole subtree.
 template <bool KAHAN, bool COUNTS, bool QUAD>
-__device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nodes,
-                                            const WalkRec *__restrict__ rec,
+__device__ __forceinline__ void walk_octant(unsigned u, int lane, const WalkRec *__restrict__ rec,
                                             const WalkQuad *__restrict__ qrec,
                                             const int4 *__restrict__ blk,
-                                            const int *__restrict__ orig, float scale,
+                                            const int *__restrict__ orig,
+                                            const int4 *__restrict__ fld,
+                                            const double *__restrict__ invL, double G,
                                             float *__restrict__ out, int32_t *__restrict__ n_int,
                                             int32_t *__restrict__ n_test,
                                             int32_t *__restrict__ n_leaf) {
   const unsigned p = u >> 3;                          // sorted block
+  const int4 F = fld[p];                              // this field's node range
+  const unsigned n_nodes = (unsigned)F.y;
   const int ma = (int)((u & 7) << 6) | (lane << 1);   // local Morton index, even: x bit 0
   const int4 B = blk[p];
   const int cx = (int)compact3(ma), cy = (int)compact3(ma >> 1), cz = (int)compact3(ma >> 2);
@@ -186,8 +190,8 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
 
   u64 sum = 0ull, comp = 0ull;  // (+0.0f, +0.0f) pairs
   int nia = 0, nib = 0, nta = 0, ntb = 0, nla = 0, nlb = 0;
-  unsigned next_a = 0, next_b = 0;
-  unsigned node = 0;
+  unsigned next_a = (unsigned)F.x, next_b = (unsigned)F.x;  // the field's root
+  unsigned node = (unsigned)F.x;
   while (node < n_nodes) {
     u64 q0, q1, q2, q3;
     load_rec(rec + node, q0, q1, q2, q3);
@@ -264,6 +268,7 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
     if (KAHAN) sum = sub2(sum, comp);
     float sa, sb;
     upk(sum, sa, sb);
+    const float scale = (float)(-G * invL[F.w]);
     out[cell] = __fmul_rn(sa, scale);
     out[cell + 1] = __fmul_rn(sb, scale);
   }
@@ -274,34 +279,40 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, unsigned n_nod
 // from 44 % to 57 % but ran 8 % slower on GB300, so the hardware schedule of a
 // plain grid is kept.)
 template <bool KAHAN, bool COUNTS, bool QUAD>
-__global__ void __launch_bounds__(kWalkThreads)
-    k_walk_pair(unsigned nunits, unsigned n_nodes, const WalkRec *__restrict__ rec,
+__global__ void __launch_bounds__(kMaxWalkThreads)
+    k_walk_pair(unsigned nunits, const WalkRec *__restrict__ rec,
                 const WalkQuad *__restrict__ qrec, const int4 *__restrict__ blk,
-                const int *__restrict__ orig, float scale,
-                float *__restrict__ out, int32_t *__restrict__ n_int,
-                int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
+                const int *__restrict__ orig, const int4 *__restrict__ fld,
+                const double *__restrict__ invL, double G, float *__restrict__ out,
+                int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
+                int32_t *__restrict__ n_leaf) {
   const int lane = threadIdx.x & 31;
-  const unsigned warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, n_nodes, rec, qrec, blk, orig, scale, out, n_int,
+  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, G, out, n_int,
                                    n_test, n_leaf);
 }
 
 // ---- one target per lane: binary64 interactions and/or the warp vote --------
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kWalkThreads)
-    k_walk_scalar(int nbricks, unsigned n_nodes, const WalkRec *__restrict__ rec,
+    k_walk_scalar(int nbricks, const WalkRec *__restrict__ rec,
                   const double4_32a *__restrict__ mom, const WalkQuad *__restrict__ qrec,
                   const double *__restrict__ q64, const int4 *__restrict__ blk,
-                  const int *__restrict__ orig, float scale_f, double scale_d,
-                  void *__restrict__ out, int32_t *__restrict__ n_int,
-                  int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
+                  const int *__restrict__ orig, const int4 *__restrict__ fld,
+                  const double *__restrict__ invL, double G, void *__restrict__ out,
+                  int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
+                  int32_t *__restrict__ n_leaf) {
   const int warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= nbricks) return;  // whole warps only
   const int p = warp >> 4;      // sorted block
   const int m = ((warp & 15) << 5) | lane;  // local Morton index of this lane's cell
   const int4 B = blk[p];
+  const int4 F = fld[p];        // this field's node range
+  const unsigned n_nodes = (unsigned)F.y;
+  const double scale_d = -G * invL[F.w];
+  const float scale_f = (float)scale_d;
   const int cx = (int)compact3(m), cy = (int)compact3(m >> 1), cz = (int)compact3(m >> 2);
   const int lc = B.x + 3;
   const float hh = pow2f(-(lc + 1));
@@ -312,8 +323,8 @@ __global__ void __launch_bounds__(kWalkThreads)
   float sum = 0.0f, comp = 0.0f;
   double sumd = 0.0;
   int ni = 0, nt = 0, nl = 0;
-  unsigned next = 0;
-  unsigned node = 0;
+  unsigned next = (unsigned)F.x;  // the field's root
+  unsigned node = (unsigned)F.x;
   while (node < n_nodes) {
     u64 q0, q1, q2, q3;
     load_rec(rec + node, q0, q1, q2, q3);
@@ -393,25 +404,26 @@ __global__ void __launch_bounds__(kWalkThreads)
 }
 
 template <bool KAHAN, bool COUNTS, bool QUAD>
-cudaError_t go_pair(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
-                    const WalkQuad *qrec, const int4 *blk, const int *orig, double scale,
-                    void *out, int32_t *ni, int32_t *nt, int32_t *nl = nullptr) {
+cudaError_t go_pair(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *qrec,
+                    const int4 *blk, const int *orig, const FieldArgs &fa, double G, void *out,
+                    int32_t *ni, int32_t *nt, int32_t *nl, int wpc) {
   const unsigned nunits = (unsigned)nb * 8u;
-  const int grid = (int)((nunits + kWarpsPerCta - 1) / kWarpsPerCta);
-  k_walk_pair<KAHAN, COUNTS, QUAD><<<grid, kWalkThreads, 0, s>>>(
-      nunits, n, rec, qrec, blk, orig, (float)scale, (float *)out, ni, nt, nl);
+  const int w = wpc > 0 ? wpc : kWarpsPerCta;
+  const int grid = (int)((nunits + w - 1) / w);
+  k_walk_pair<KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
+      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, G, (float *)out, ni, nt, nl);
   return cudaGetLastError();
 }
 
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
-cudaError_t go_scalar(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
-                      const double4_32a *mom, const WalkQuad *qrec, const double *q64,
-                      const int4 *blk, const int *orig, double scale, void *out, int32_t *ni,
-                      int32_t *nt, int32_t *nl = nullptr) {
+cudaError_t go_scalar(cudaStream_t s, int nb, const WalkRec *rec, const double4_32a *mom,
+                      const WalkQuad *qrec, const double *q64, const int4 *blk,
+                      const int *orig, const FieldArgs &fa, double G, void *out, int32_t *ni,
+                      int32_t *nt, int32_t *nl) {
   const int nbricks = nb * 16;
   const int grid = (nbricks + kWarpsPerCta - 1) / kWarpsPerCta;
   k_walk_scalar<F64, VOTE, KAHAN, COUNTS, QUAD><<<grid, kWalkThreads, 0, s>>>(
-      nbricks, n, rec, mom, qrec, q64, blk, orig, (float)scale, scale, out, ni, nt, nl);
+      nbricks, rec, mom, qrec, q64, blk, orig, fa.fld, fa.invL, G, out, ni, nt, nl);
   return cudaGetLastError();
 }
 
@@ -419,27 +431,28 @@ cudaError_t go_scalar(cudaStream_t s, int nb, unsigned n, const WalkRec *rec,
 // same decisions as every walk of the same criterion (the opening test does
 // not depend on precision, summation or the quadrupole term).
 template <bool QUAD>
-cudaError_t launch_walk_q(cudaStream_t s, const bh_options &opt, int nb, unsigned n,
-                          const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
-                          const double *q64, const int4 *blk, const int *orig, double scale,
-                          void *out) {
+cudaError_t launch_walk_q(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
+                          const double4_32a *mom, const WalkQuad *qrec, const double *q64,
+                          const int4 *blk, const int *orig, const FieldArgs &fa, double G,
+                          void *out, int wpc) {
   const bool vote = opt.criterion == BH_CRIT_WARP_VOTE;
   if (opt.precision == BH_PREC_F64)
-    return vote ? go_scalar<true, true, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64, blk,
-                                                            orig, scale, out, nullptr, nullptr)
-                : go_scalar<true, false, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64, blk,
-                                                             orig, scale, out, nullptr, nullptr);
+    return vote ? go_scalar<true, true, false, false, QUAD>(s, nb, rec, mom, qrec, q64, blk, orig,
+                                                            fa, G, out, nullptr, nullptr, nullptr)
+                : go_scalar<true, false, false, false, QUAD>(s, nb, rec, mom, qrec, q64, blk,
+                                                             orig, fa, G, out, nullptr, nullptr,
+                                                             nullptr);
   if (vote)
-    return opt.kahan ? go_scalar<false, true, true, false, QUAD>(s, nb, n, rec, mom, qrec, q64,
-                                                                 blk, orig, scale, out, nullptr,
-                                                                 nullptr)
-                     : go_scalar<false, true, false, false, QUAD>(s, nb, n, rec, mom, qrec, q64,
-                                                                  blk, orig, scale, out, nullptr,
-                                                                  nullptr);
-  return opt.kahan ? go_pair<true, false, QUAD>(s, nb, n, rec, qrec, blk, orig, scale, out,
-                                                nullptr, nullptr)
-                   : go_pair<false, false, QUAD>(s, nb, n, rec, qrec, blk, orig, scale, out,
-                                                 nullptr, nullptr);
+    return opt.kahan ? go_scalar<false, true, true, false, QUAD>(s, nb, rec, mom, qrec, q64, blk,
+                                                                 orig, fa, G, out, nullptr,
+                                                                 nullptr, nullptr)
+                     : go_scalar<false, true, false, false, QUAD>(s, nb, rec, mom, qrec, q64,
+                                                                  blk, orig, fa, G, out, nullptr,
+                                                                  nullptr, nullptr);
+  return opt.kahan ? go_pair<true, false, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, nullptr,
+                                                nullptr, nullptr, wpc)
+                   : go_pair<false, false, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out,
+                                                 nullptr, nullptr, nullptr, wpc);
 }
 
 }  // namespace
@@ -452,21 +465,19 @@ cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, int64_t n_nodes,
-                        const WalkRec *rec, const double4_32a *mom, const WalkQuad *qrec,
-                        const double *q64, const int4 *blk, const int *orig, double scale,
-                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf) {
-  const unsigned n = (unsigned)n_nodes;
+cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
+                        const double4_32a *mom, const WalkQuad *qrec, const double *q64,
+                        const int4 *blk, const int *orig, const FieldArgs &fa, double G,
+                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf, int wpc) {
   if (n_int)  // counting walk
     return opt.criterion == BH_CRIT_WARP_VOTE
-               ? go_scalar<false, true, false, true, false>(s, nb, n, rec, mom, qrec, q64, blk,
-                                                           orig, scale, out, n_int, n_test,
-                                                           n_leaf)
-               : go_pair<false, true, false>(s, nb, n, rec, qrec, blk, orig, scale, out, n_int,
-                                             n_test, n_leaf);
+               ? go_scalar<false, true, false, true, false>(s, nb, rec, mom, qrec, q64, blk, orig,
+                                                           fa, G, out, n_int, n_test, n_leaf)
+               : go_pair<false, true, false>(s, nb, rec, qrec, blk, orig, fa, G, out, n_int,
+                                             n_test, n_leaf, wpc);
   if (opt.quadrupole)
-    return launch_walk_q<true>(s, opt, nb, n, rec, mom, qrec, q64, blk, orig, scale, out);
-  return launch_walk_q<false>(s, opt, nb, n, rec, mom, qrec, q64, blk, orig, scale, out);
+    return launch_walk_q<true>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
+  return launch_walk_q<false>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
 }
 
 }  // namespace bhg

@@ -425,6 +425,31 @@ def random_blob_field(seed: int, block_level: int, nblobs=None) -> Workload:
     return Workload(m.name, m, rho, (0.5,), meta=dict(seed=seed, nblobs=k))
 
 
+def batch_fields(nfields=64, seed0=5000, levels=(1, 2, 3, 4)):
+    """Independent fields of uneven size for the batched solve: field i is a
+    uniform mesh of 16^3, 32^3, 64^3 or 128^3 cells (block level drawn from
+    ``levels`` with seed seed0 + i) holding 1-8 Gaussian blobs of lognormal
+    mass (sigma 1) and width 0.02-0.2.  Returns the list of Workloads."""
+    out = []
+    for i in range(nfields):
+        rng = np.random.Generator(np.random.PCG64(seed0 + i))
+        lev = int(rng.choice(levels))
+        out.append(random_blob_field(seed0 + i, lev))
+    return out
+
+
+def concat_fields(workloads):
+    """Concatenated block geometry and densities of several fields, as the
+    batched build takes them: (nblocks, level, ijk, box_lo, box_len, density)."""
+    nb = np.array([w.mesh.nblocks for w in workloads], dtype=np.int32)
+    level = np.concatenate([w.mesh.level for w in workloads]).astype(np.int32)
+    ijk = np.concatenate([w.mesh.ijk for w in workloads]).astype(np.int32)
+    lo = np.array([w.mesh.box_lo for w in workloads], dtype=np.float64)
+    ln = np.array([w.mesh.box_len for w in workloads], dtype=np.float64)
+    rho = np.concatenate([w.density.reshape(-1) for w in workloads])
+    return nb, level, ijk, lo, ln, rho
+
+
 def tiny_meshes() -> dict:
     """Small meshes for exhaustive checks: 1 block, 8 blocks, and mixed-level
     meshes (one octant refined once / twice) with ragged level structure."""
