@@ -36,6 +36,13 @@
  *     x = cell centre - R, computed here straight from that definition, and an
  *     accepted node contributes -G (M/d + (1/2) d^T Q d / d^5), d = r_t - R.
  *     The opening test is unchanged; cells carry no quadrupole.
+ *   - Optional learned correction (not in the paper): each accepted node's
+ *     term M/d is multiplied by (1 + s^2 y), y = MLP(x), where s = l/d and x
+ *     holds ten features of the (target, node) pair (see pair_features); the
+ *     MLP is 10 -> 64 -> 64 -> 1 with tanh-form GELU activations, evaluated
+ *     here in FP64 with the weights it is given.  The training residual of a
+ *     pair is eps = (sum over the node's cells of m / |r_t - r_c|)/(M/d) - 1,
+ *     the node's exact contribution against its monopole.
  *
  * Readings where the paper is silent (each also stated in the design notes):
  *   - Positions are taken in box units u = (x - lo)/L, so Phi = -(G/L) sum M/|du|.
@@ -583,6 +590,166 @@ int or_walk_vote(const void *p, double theta, double G, int quad, int64_t nbrick
       if (n_test) n_test[32 * q + l] = w->n_test[l];
     }
     free(w);
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------------ learned correction -- */
+#define MLP_IN 10
+#define MLP_H 64
+/* Weights layout (doubles): W1[10][64], b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define MLP_NW (MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+static double gelu(double x) {
+  const double c = 0.7978845608028654; /* sqrt(2/pi) */
+  return 0.5 * x * (1.0 + tanh(c * (x + 0.044715 * x * x * x)));
+}
+
+static double mlp_forward(const double *w, const double x[MLP_IN]) {
+  const double *W1 = w, *b1 = W1 + MLP_IN * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+  const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+  double h1[MLP_H], h2[MLP_H];
+  for (int j = 0; j < MLP_H; ++j) {
+    double a = b1[j];
+    for (int k = 0; k < MLP_IN; ++k) a += x[k] * W1[k * MLP_H + j];
+    h1[j] = gelu(a);
+  }
+  for (int j = 0; j < MLP_H; ++j) {
+    double a = b2[j];
+    for (int k = 0; k < MLP_H; ++k) a += h1[k] * W2[k * MLP_H + j];
+    h2[j] = gelu(a);
+  }
+  double y = b3[0];
+  for (int k = 0; k < MLP_H; ++k) y += h2[k] * W3[k];
+  return y;
+}
+
+/* Features of an accepted (target, node) pair: the direction u = d/|d|, the
+ * size ratio s = l/|d| and its square and cube, delta/l, the quadrupole
+ * along u and its norm, both over M l^2, and s^2 times the former (the
+ * leading term of the monopole's error).  Needs the quadrupoles. */
+static void pair_features(const onode *n, const double tu[3], double x[MLP_IN], double *s_out,
+                          double *mono) {
+  double d[3] = {tu[0] - n->R[0], tu[1] - n->R[1], tu[2] - n->R[2]};
+  double D = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  double u[3] = {d[0] / D, d[1] / D, d[2] / D};
+  double l = ldexp(1.0, -n->level);
+  double s = l / D;
+  double ml2 = n->M > 0.0 ? n->M * l * l : 1.0;
+  const double *Q = n->Q;
+  double quu = Q[0] * u[0] * u[0] + Q[1] * u[1] * u[1] + Q[2] * u[2] * u[2] +
+               2.0 * (Q[3] * u[0] * u[1] + Q[4] * u[0] * u[2] + Q[5] * u[1] * u[2]);
+  double qf = sqrt(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2] +
+                   2.0 * (Q[3] * Q[3] + Q[4] * Q[4] + Q[5] * Q[5]));
+  x[0] = u[0];
+  x[1] = u[1];
+  x[2] = u[2];
+  x[3] = s;
+  x[4] = s * s;
+  x[5] = s * s * s;
+  x[6] = n->delta / l;
+  x[7] = quu / ml2;
+  x[8] = qf / ml2;
+  x[9] = s * s * quu / ml2;
+  *s_out = s;
+  *mono = n->M / D;
+}
+
+typedef struct {
+  const otree *t;
+  int64_t self;
+  float tf[3];
+  double tu[3];
+  float inv_theta;
+  const double *w;          /* MLP weights (walk) or NULL (pair listing) */
+  neumaier sum;
+  int64_t n_int, n_test;
+  int64_t np, cap;          /* pair listing */
+  double *feat, *eps;
+  int64_t *node_out;
+} learn_state;
+
+static void walk_learned(learn_state *w, int64_t id) {
+  const onode *n = &w->t->node[id];
+  if (n->child[0] < 0) {
+    if (id != w->self) {
+      if (w->w) nm_add(&w->sum, n->M / dist64(w->tu, n->R));
+      w->n_int++;
+    }
+    return;
+  }
+  w->n_test++;
+  if (accept_f32(n, w->tf, w->inv_theta)) {
+    double x[MLP_IN], s, mono;
+    pair_features(n, w->tu, x, &s, &mono);
+    w->n_int++;
+    if (w->w) {
+      nm_add(&w->sum, mono * (1.0 + s * s * mlp_forward(w->w, x)));
+    } else {
+      if (w->np < w->cap) {
+        /* exact contribution of the node: its cells form the pre-order range
+           that starts right after it and ends before the next node of the
+           same or a shallower level */
+        neumaier ex = {0.0, 0.0};
+        for (int64_t k = id + 1; k < w->t->nnodes && w->t->node[k].level > n->level; ++k)
+          if (w->t->node[k].child[0] < 0)
+            nm_add(&ex, w->t->node[k].M / dist64(w->tu, w->t->node[k].R));
+        for (int a = 0; a < MLP_IN; ++a) w->feat[MLP_IN * w->np + a] = x[a];
+        w->eps[w->np] = nm_value(&ex) / mono - 1.0;
+        if (w->node_out) w->node_out[w->np] = id;
+      }
+      w->np++;
+    }
+    return;
+  }
+  for (int o = 0; o < 8; ++o) walk_learned(w, n->child[o]);
+}
+
+/* Training pairs of one target: features and eps of every accepted internal
+ * node of its per-cell walk.  Returns the number of pairs (the arrays hold
+ * the first `cap`), -1 on bad arguments. */
+int64_t or_learn_pairs(const void *p, double theta, int64_t target, int64_t cap, double *feat,
+                       double *eps, int64_t *node) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || !t->have_quad || target < 0 || target >= (int64_t)t->nblocks * 512)
+    return -1;
+  learn_state w;
+  memset(&w, 0, sizeof(w));
+  w.t = t;
+  w.self = t->leaf_of_cell[target];
+  w.inv_theta = (float)(1.0 / theta);
+  target_position(t, w.self, w.tu, w.tf);
+  w.cap = cap;
+  w.feat = feat;
+  w.eps = eps;
+  w.node_out = node;
+  walk_learned(&w, 0);
+  return w.np;
+}
+
+/* Per-cell walk with the learned correction of every accepted node. */
+int or_walk_learned(const void *p, double theta, double G, const double *weights,
+                    int64_t ntargets, const int64_t *targets, double *phi, int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || !isfinite(G) || !t->have_quad || !weights) return OR_ERR_ARG;
+  for (int64_t q = 0; q < ntargets; ++q)
+    if (targets[q] < 0 || targets[q] >= (int64_t)t->nblocks * 512) return OR_ERR_ARG;
+  float inv_theta = (float)(1.0 / theta);
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < ntargets; ++q) {
+    learn_state w;
+    memset(&w, 0, sizeof(w));
+    w.t = t;
+    w.self = t->leaf_of_cell[targets[q]];
+    w.inv_theta = inv_theta;
+    w.w = weights;
+    target_position(t, w.self, w.tu, w.tf);
+    walk_learned(&w, 0);
+    phi[q] = scale * nm_value(&w.sum);
   }
   return OR_OK;
 }

@@ -71,6 +71,10 @@ def _load():
             lib.or_direct_points.argtypes = [i64, P, P, dbl, i64, P, P]
             lib.or_direct_points.restype = i32
             lib.or_max_threads.restype = i32
+            lib.or_learn_pairs.argtypes = [P, dbl, i64, i64, P, P, P]
+            lib.or_learn_pairs.restype = i64
+            lib.or_walk_learned.argtypes = [P, dbl, dbl, P, i64, P, P, i32]
+            lib.or_walk_learned.restype = i32
             _lib = lib
     return _lib
 
@@ -193,6 +197,34 @@ class Tree:
             raise OracleError(st, "or_walk_vote")
         return phi, ni, nt
 
+    def learn_pairs(self, theta: float, target: int):
+        """Features, residual eps and node index of every accepted internal
+        node of one target's walk (the learned correction's training pairs)."""
+        self.quadrupoles()
+        lib = _load()
+        n = lib.or_learn_pairs(self._h, float(theta), int(target), 0, None, None, None)
+        if n < 0:
+            raise OracleError(OR_ERR_ARG, "or_learn_pairs")
+        f = np.empty((max(n, 1), 10))
+        e = np.empty(max(n, 1))
+        nd = np.empty(max(n, 1), np.int64)
+        lib.or_learn_pairs(self._h, float(theta), int(target), n, _ptr(f), _ptr(e), _ptr(nd))
+        return f[:n], e[:n], nd[:n]
+
+    def walk_learned(self, theta: float, weights, G: float = 1.0, targets=None,
+                     threads: int = 0) -> np.ndarray:
+        """Per-cell walk with each accepted node's term times (1 + s^2 MLP(x));
+        weights: flat FP64 vector in the layout of mlp_unflatten."""
+        self.quadrupoles()
+        t = self._targets(targets)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        phi = np.empty(t.shape[0])
+        st = _load().or_walk_learned(self._h, float(theta), float(G), _ptr(w), t.shape[0],
+                                     _ptr(t), _ptr(phi), int(threads))
+        if st != OR_OK:
+            raise OracleError(st, "or_walk_learned")
+        return phi
+
     def direct(self, G: float = 1.0, targets=None, threads: int = 0) -> np.ndarray:
         """Direct O(N^2) potential (Eq. 2 without the 1/2) at the given cells."""
         t = self._targets(targets)
@@ -227,3 +259,61 @@ def local_morton_order() -> np.ndarray:
     cy = sum(((m >> (3 * b + 1)) & 1) << b for b in range(3))
     cz = sum(((m >> (3 * b + 2)) & 1) << b for b in range(3))
     return cz * 64 + cy * 8 + cx
+
+
+# ------------------------------------------------------------------ MLP --
+MLP_IN, MLP_H = 10, 64
+MLP_NW = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def mlp_unflatten(w):
+    """Flat weights -> (W1[10,64], b1[64], W2[64,64], b2[64], W3[64], b3)."""
+    w = np.asarray(w, dtype=np.float64)
+    i = 0
+    out = []
+    for shape in ((MLP_IN, MLP_H), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_H,), (1,)):
+        k = int(np.prod(shape))
+        out.append(w[i:i + k].reshape(shape))
+        i += k
+    return out
+
+
+def gelu(a):
+    """tanh form of GELU."""
+    c = np.sqrt(2.0 / np.pi)
+    return 0.5 * a * (1.0 + np.tanh(c * (a + 0.044715 * a ** 3)))
+
+
+def gelu_grad(a):
+    c = np.sqrt(2.0 / np.pi)
+    t = np.tanh(c * (a + 0.044715 * a ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * a * (1.0 - t * t) * c * (1.0 + 3 * 0.044715 * a * a)
+
+
+def mlp_forward(w, x):
+    W1, b1, W2, b2, W3, b3 = mlp_unflatten(w)
+    a1 = x @ W1 + b1
+    h1 = gelu(a1)
+    a2 = h1 @ W2 + b2
+    h2 = gelu(a2)
+    return h2 @ W3 + b3[0], (a1, h1, a2, h2)
+
+
+def mlp_loss_grad(w, x, z):
+    """Mean squared error of MLP(x) against z and its gradient (flat), FP64."""
+    y, (a1, h1, a2, h2) = mlp_forward(w, x)
+    W1, b1, W2, b2, W3, b3 = mlp_unflatten(w)
+    n = x.shape[0]
+    r = y - z
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / n
+    gW3 = h2.T @ dy
+    gb3 = np.array([dy.sum()])
+    d2 = np.outer(dy, W3) * gelu_grad(a2)
+    gW2 = h1.T @ d2
+    gb2 = d2.sum(0)
+    d1 = (d2 @ W2.T) * gelu_grad(a1)
+    gW1 = x.T @ d1
+    gb1 = d1.sum(0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, gb3])
+    return loss, g

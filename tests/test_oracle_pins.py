@@ -449,3 +449,57 @@ def test_quadrupole_reduces_walk_error():
         assert eq < em / factor, (th, em, eq)
     # the opening decisions do not depend on the quadrupole term
     assert np.array_equal(t.walk(0.6, targets=tg)[1], t.walk(0.6, targets=tg, quad=True)[1])
+
+
+# ---------------------------------------------- learned correction (MLP) ---
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    w = rng.normal(0, 0.3, O.MLP_NW)
+    x = rng.normal(0, 1, (7, O.MLP_IN))
+    z = rng.normal(0, 1, 7)
+    loss, g = O.mlp_loss_grad(w, x, z)
+    idx = rng.choice(O.MLP_NW, 60, replace=False)
+    for i in idx:
+        e = np.zeros_like(w)
+        e[i] = 1e-6
+        fd = (O.mlp_loss_grad(w + e, x, z)[0] - O.mlp_loss_grad(w - e, x, z)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), i
+
+
+def test_gelu_is_the_tanh_form():
+    a = np.linspace(-4, 4, 9)
+    assert np.allclose(O.gelu(a), 0.5 * a * (1 + np.tanh(np.sqrt(2 / np.pi) * (a + 0.044715 * a ** 3))))
+    h = 1e-6
+    assert np.allclose(O.gelu_grad(a), (O.gelu(a + h) - O.gelu(a - h)) / (2 * h), atol=1e-8)
+
+
+def test_learned_walk_with_zero_network_is_the_monopole_walk(tiny):
+    m, rho = tiny["refined_twice"]
+    t = _tree(m, rho)
+    tg = np.arange(0, m.ncells, 17)
+    mono = t.walk(0.8, targets=tg)[0]
+    assert np.allclose(t.walk_learned(0.8, np.zeros(O.MLP_NW), targets=tg), mono, rtol=1e-14,
+                       atol=0)
+    w = np.zeros(O.MLP_NW)
+    w[-1] = 0.5                                    # y = 0.5 for every pair
+    lw = t.walk_learned(0.8, w, targets=tg)
+    assert np.all(np.abs(lw) > np.abs(mono))      # every node term grows by s^2/2
+
+
+def test_exact_residuals_turn_the_walk_into_the_direct_sum(tiny):
+    """walk + sum over accepted nodes of (M/d) eps = direct sum, per target:
+    eps is each node's exact error against its monopole."""
+    m, rho = tiny["diag_refined"]
+    t = _tree(m, rho)
+    e = t.export()
+    u, _ = _cell_geometry(m)
+    for tgt in np.random.default_rng(9).choice(m.ncells, 12, replace=False):
+        f, eps, nodes = t.learn_pairs(0.8, tgt)
+        assert len(nodes) > 0 and np.allclose(np.linalg.norm(f[:, :3], axis=1), 1.0)
+        mono = e["M"][nodes] / np.linalg.norm(u[tgt] - e["R"][nodes], axis=1)
+        walk = t.walk(0.8, targets=[tgt])[0][0]
+        d = t.direct(targets=[tgt])[0]
+        assert abs((walk - np.sum(mono * eps)) / d - 1.0) < 1e-12
+        far = f[:, 3] < 0.25                          # small s: eps ~ s^2 uQu/(2 M l^2)
+        if far.any():
+            assert np.all(np.abs(eps[far] - 0.5 * f[far, 9]) <= 0.2 * np.abs(eps[far]) + 1e-9)
