@@ -78,7 +78,12 @@ typedef struct {
                      unchanged).  Quadrupoles are reduced in binary32 for the
                      binary32 walk and in FP64 for the FP64 walk; they cost 32
                      (binary32) or 80 (FP64) more bytes per internal node. */
-  int reserved[4];
+  int learned;    /* 0 (default).  1: every accepted node's term M/d is
+                     multiplied by (1 + s^2 y), y = MLP(pair features), with the
+                     network set by bh_set_mlp and evaluated on the tensor
+                     cores (not in the paper; see bh_learn_pairs).  Needs the
+                     binary32 per-cell walk; excludes the quadrupole term. */
+  int reserved[3];
 } bh_options;
 
 /* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation,
@@ -236,6 +241,42 @@ bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const int32_t *ijk
                            const double *box_lo, double box_len, const void *density,
                            int density_is_fp64, double theta, double G, float *out,
                            void *cuda_stream);
+
+/* ---- learned residual correction (not in the paper) -------------------------
+ * Features x of an accepted (target, node) pair, s = l/|d|, u = d/|d|:
+ *   x = [u_x, u_y, u_z, s, s^2, s^3, delta/l, u^T Q u/(M l^2), |Q|_F/(M l^2),
+ *        s^2 u^T Q u/(M l^2)]
+ * Network: 10 -> 64 -> 64 -> 1, tanh-form GELU, weights flat in FP32 as
+ * W1[10][64], b1[64], W2[64][64], b2[64], W3[64], b3 (4865 floats). */
+
+/* Training pairs generated by the method itself: for each DEVICE target cell
+ * index (caller layout, int64), every internal node its per-cell walk at theta
+ * accepts, with the pair's features feat[10] and eps = (the node's exact
+ * contribution, summed over its cells in FP64)/(M/|d|) - 1.  feat (cap*10)
+ * and eps (cap) are DEVICE float arrays; node (DEVICE int64, cap, may be NULL)
+ * receives the node index of each pair (pairs come in no particular order);
+ * *count (HOST) receives the number of pairs found (only the first cap are
+ * written).  Needs a tree with quadrupole records (quadrupole or learned
+ * option).  Synchronises the stream. */
+bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int64_t *targets,
+                         int64_t cap, float *feat, float *eps, int64_t *node, int64_t *count);
+
+/* Gradient of the mean squared error of MLP(x) against z over n samples
+ * (DEVICE x[n][10], z[n], weights w), written to DEVICE grad[4865]; the loss
+ * to DEVICE *loss.  FP32.  Enqueued on cuda_stream. */
+bh_status bh_mlp_grad(int64_t n, const float *x, const float *z, const float *w, float *grad,
+                      float *loss, void *cuda_stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) of the DEVICE weights w with
+ * DEVICE moments m, v (4865 each, zero before step 1); step counts from 1. */
+bh_status bh_mlp_adam(const float *grad, float *w, float *m, float *v, int step, float lr,
+                      void *cuda_stream);
+
+/* Sets the network of the learned walk from HOST FP32 weights; the weights
+ * are rounded to bf16 (round to nearest even) for the tensor cores, biases
+ * stay FP32.  bh_get_mlp returns the weights in use (bf16 values widened). */
+bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host);
+bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host);
 
 /* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
 const char *bh_last_error(const bh_ctx *ctx);

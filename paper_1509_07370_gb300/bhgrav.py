@@ -24,14 +24,15 @@ BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
 EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_update_density", "bh_sync_status", "bh_autotune", "bh_solve_graph",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
-            "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_last_error",
+            "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
+            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_last_error",
             "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("criterion", ctypes.c_int),
                 ("kahan", ctypes.c_int), ("quadrupole", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("learned", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class BHError(RuntimeError):
@@ -75,6 +76,11 @@ def load(build_if_needed: bool = True):
         lib.bh_export_quadrupoles.argtypes = [P, P]
         lib.bh_solve_host.argtypes = [P, I, P, P, P, D, P, I, D, D, P]
         lib.bh_solve_noalloc.argtypes = [I, P, P, P, D, P, I, D, D, P, P]
+        lib.bh_learn_pairs.argtypes = [P, D, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P]
+        lib.bh_mlp_grad.argtypes = [ctypes.c_int64, P, P, P, P, P, P]
+        lib.bh_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, P]
+        lib.bh_set_mlp.argtypes = [P, P]
+        lib.bh_get_mlp.argtypes = [P, P]
         lib.bh_last_error.argtypes = [P]
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
@@ -83,7 +89,8 @@ def load(build_if_needed: bool = True):
                      "bh_sync_status", "bh_autotune", "bh_solve_graph", "bh_potential",
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
-                     "bh_solve_noalloc"):
+                     "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
+                     "bh_set_mlp", "bh_get_mlp"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -253,6 +260,61 @@ def bh_solve_noalloc(level, ijk, box_lo, box_len, density, theta: float, G: floa
     _check(None, st, "bh_solve_noalloc")
 
 
+MLP_NW = 10 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def bh_learn_pairs(ctx, theta: float, targets, cap: int, with_nodes: bool = False):
+    """Training pairs of the learned correction for the DEVICE int64 target
+    cell indices; returns (feat [n,10], eps [n], count[, node [n]]) (CUDA)."""
+    import torch
+    dev = targets.device
+    feat = torch.empty((max(cap, 1), 10), dtype=torch.float32, device=dev)
+    eps = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+    node = torch.empty(max(cap, 1), dtype=torch.int64, device=dev) if with_nodes else None
+    cnt = ctypes.c_int64()
+    st = load().bh_learn_pairs(ctx, float(theta), int(targets.numel()),
+                               ctypes.c_void_p(_dev_ptr(targets, torch.int64)), int(cap),
+                               ctypes.c_void_p(feat.data_ptr()), ctypes.c_void_p(eps.data_ptr()),
+                               ctypes.c_void_p(node.data_ptr()) if with_nodes else None,
+                               ctypes.byref(cnt))
+    _check(ctx, st, "bh_learn_pairs")
+    n = min(cnt.value, cap)
+    if with_nodes:
+        return feat[:n], eps[:n], cnt.value, node[:n]
+    return feat[:n], eps[:n], cnt.value
+
+
+def bh_mlp_grad(x, z, w, grad, loss, stream: int = 0) -> None:
+    import torch
+    st = load().bh_mlp_grad(int(z.numel()), ctypes.c_void_p(_dev_ptr(x, torch.float32)),
+                            ctypes.c_void_p(_dev_ptr(z, torch.float32)),
+                            ctypes.c_void_p(_dev_ptr(w, torch.float32)),
+                            ctypes.c_void_p(_dev_ptr(grad, torch.float32)),
+                            ctypes.c_void_p(_dev_ptr(loss, torch.float32)),
+                            ctypes.c_void_p(int(stream)))
+    _check(None, st, "bh_mlp_grad")
+
+
+def bh_mlp_adam(grad, w, m, v, step: int, lr: float, stream: int = 0) -> None:
+    import torch
+    st = load().bh_mlp_adam(*[ctypes.c_void_p(_dev_ptr(t, torch.float32)) for t in (grad, w, m, v)],
+                            int(step), ctypes.c_float(lr), ctypes.c_void_p(int(stream)))
+    _check(None, st, "bh_mlp_adam")
+
+
+def bh_set_mlp(ctx, w_host: np.ndarray) -> None:
+    w = np.ascontiguousarray(w_host, dtype=np.float32)
+    if w.size != MLP_NW:
+        raise ValueError(f"expected {MLP_NW} weights")
+    _check(ctx, load().bh_set_mlp(ctx, _np_ptr(w)), "bh_set_mlp")
+
+
+def bh_get_mlp(ctx) -> np.ndarray:
+    w = np.empty(MLP_NW, dtype=np.float32)
+    _check(ctx, load().bh_get_mlp(ctx, _np_ptr(w)), "bh_get_mlp")
+    return w
+
+
 def bh_last_error(ctx) -> str:
     return load().bh_last_error(ctx).decode()
 
@@ -272,11 +334,12 @@ class Solver:
     """
 
     def __init__(self, precision=BH_PREC_F32, criterion=BH_CRIT_PER_CELL, kahan=True,
-                 quadrupole=False, device=0, stream=None):
+                 quadrupole=False, learned=False, device=0, stream=None):
         import torch
         o = bh_default_options()
         o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
         o.quadrupole = int(bool(quadrupole))
+        o.learned = int(bool(learned))
         self.options = o
         self.device = torch.device("cuda", device)
         if stream is None:
@@ -363,6 +426,17 @@ class Solver:
         bh_export_nodes(self._ctx, **out)
         self._handoff(*out.values())
         return out
+
+    def learn_pairs(self, theta: float, targets, cap: int, with_nodes: bool = False):
+        out = bh_learn_pairs(self._ctx, theta, targets, cap, with_nodes)
+        self._handoff(*[t for t in out if hasattr(t, "record_stream")])
+        return out
+
+    def set_mlp(self, w):
+        bh_set_mlp(self._ctx, w)
+
+    def get_mlp(self):
+        return bh_get_mlp(self._ctx)
 
     def export_quadrupoles(self):
         import torch

@@ -10,14 +10,6 @@
 
 #include "bh_internal.cuh"
 
-struct bh_ctx {
-  bh_options opt;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bhg::Tree tree;
-  char err[512] = {0};
-};
-
 namespace {
 
 bh_status fail(bh_ctx *c, bh_status st, const char *fmt, ...) {
@@ -57,6 +49,7 @@ void free_blocks(bhg::Tree &t) {
   release(t.d_orig);
   release(t.d_fid);
   release(t.d_fld);
+  release(t.d_pos);
   t.nb_cap = 0;
 }
 
@@ -87,6 +80,7 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   BH_CUDA(cudaMalloc(&t.d_blk, n * sizeof(int4)));
   BH_CUDA(cudaMalloc(&t.d_orig, n * sizeof(int)));
   BH_CUDA(cudaMalloc(&t.d_fid, n * sizeof(int)));
+  BH_CUDA(cudaMalloc(&t.d_pos, n * sizeof(int)));
   BH_CUDA(cudaMalloc(&t.d_fld, n * sizeof(int4)));
   t.nb_cap = nb;
   return BH_OK;
@@ -94,8 +88,8 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
 
 bh_status ensure_nodes(bh_ctx *ctx, int64_t n_nodes) {
   bhg::Tree &t = ctx->tree;
-  const bool quad = ctx->opt.quadrupole != 0;
-  const bool quad64 = quad && ctx->opt.precision == BH_PREC_F64;
+  const bool quad = ctx->opt.quadrupole != 0 || ctx->opt.learned != 0;
+  const bool quad64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64;
   if (t.node_cap >= n_nodes && (!quad || t.quad_cap >= n_nodes)) return BH_OK;
   free_nodes(t);
   if (quad) {
@@ -165,7 +159,7 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64)
   cudaStream_t s = ctx->stream;
   // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
   double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
-  bhg::WalkQuad *qrec = ctx->opt.quadrupole ? t.d_qrec : nullptr;
+  bhg::WalkQuad *qrec = (ctx->opt.quadrupole || ctx->opt.learned) ? t.d_qrec : nullptr;
   const bhg::FieldArgs fa = field_args(t);
   BH_CUDA(bhg::launch_blocks(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
                              density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl,
@@ -245,7 +239,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
                                  fa));
   BH_CUDA(bhg::launch_sort_blocks(s, t.d_key, t.d_idx, t.d_flags, fa));
   BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
-                                     t.d_count, t.d_blk, t.d_orig, t.d_flags, fa));
+                                     t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, t.d_pos));
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
   BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
                                 t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig));
@@ -289,7 +283,13 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if (opt) o = *opt;
   if ((o.precision != BH_PREC_F32 && o.precision != BH_PREC_F64) ||
       (o.criterion != BH_CRIT_PER_CELL && o.criterion != BH_CRIT_WARP_VOTE) ||
-      (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1))
+      (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1) ||
+      (o.learned != 0 && o.learned != 1))
+    return BH_ERR_ARG;
+  // the learned walk is the binary32 per-cell walk, with the network in place
+  // of the quadrupole term
+  if (o.learned && (o.precision != BH_PREC_F32 || o.criterion != BH_CRIT_PER_CELL ||
+                    o.quadrupole))
     return BH_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -368,6 +368,25 @@ bh_status bh_sync_status(bh_ctx *ctx) {
   return BH_OK;
 }
 
+static bh_status prepare(bh_ctx *ctx, double theta);
+
+}  // extern "C"
+
+namespace bhg {
+bh_status ctx_fail(bh_ctx *c, bh_status st, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+bh_status ctx_prepare(bh_ctx *ctx, double theta) { return prepare(ctx, theta); }
+}  // namespace bhg
+
+extern "C" {
+
 static bh_status prepare(bh_ctx *ctx, double theta) {
   bhg::Tree &t = ctx->tree;
   if (!t.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
@@ -392,6 +411,11 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
+  if (ctx->opt.learned) {
+    if (!ctx->d_mlp) return fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
+    BH_CUDA(bhg::launch_walk_learned(ctx->stream, ctx, G, out));
+    return BH_OK;
+  }
   BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
                            t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr, nullptr,
                            t.wpc));
@@ -484,7 +508,7 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
   bh_ctx *ctx = const_cast<bh_ctx *>(cctx);
   if (!ctx) return BH_ERR_ARG;
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
-  if (!ctx->opt.quadrupole)
+  if (!ctx->opt.quadrupole && !ctx->opt.learned)
     return fail(ctx, BH_ERR_STATE, "the context was created without the quadrupole option");
   if (!Q) return fail(ctx, BH_ERR_ARG, "bh_export_quadrupoles: Q is null");
   bh_status st = use_device(ctx);
@@ -574,9 +598,14 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
       cap = enqueue_moments(ctx, density, density_is_fp64);
       if (cap == BH_OK)
         e = bhg::launch_prepare_s2(s, t.n_nodes, t.d_aux, t.d_rec, (float)(1.0 / theta));
+      if (cap == BH_OK && e == cudaSuccess && ctx->opt.learned && !ctx->d_mlp)
+        cap = fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
       if (cap == BH_OK && e == cudaSuccess)
-        e = bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
-                             t.d_orig, field_args(t), G, out, nullptr, nullptr, nullptr, t.wpc);
+        e = ctx->opt.learned
+                ? bhg::launch_walk_learned(s, ctx, G, out)
+                : bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
+                                   t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr,
+                                   nullptr, t.wpc);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);
@@ -650,6 +679,7 @@ void bh_destroy(bh_ctx *ctx) {
   release(ctx->tree.d_stage_in);
   release(ctx->tree.d_stage_out);
   release(ctx->tree.d_flags);
+  release(ctx->d_mlp);
   if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
   delete ctx;
 }

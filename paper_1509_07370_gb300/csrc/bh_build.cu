@@ -167,10 +167,11 @@ __global__ void k_tile_and_count(int nb, const unsigned long long *__restrict__ 
                                  const int *__restrict__ ijk, int *__restrict__ count,
                                  int4 *__restrict__ blk, int *__restrict__ orig,
                                  unsigned *flags, const int *__restrict__ fstart,
-                                 const int *__restrict__ fid) {
+                                 const int *__restrict__ fid, int *__restrict__ pos) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int b = idx[p];
+  if (pos) pos[b] = p;  // sorted position of caller block b
   const int lb = level[b];
   const unsigned long long kp = key[p];
   const int f = fid[b];
@@ -625,9 +626,10 @@ cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *
 
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk, int *count,
-                                  int4 *blk, int *orig, unsigned *flags, const FieldArgs &fa) {
+                                  int4 *blk, int *orig, unsigned *flags, const FieldArgs &fa,
+                                  int *pos) {
   k_tile_and_count<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, idx, level, ijk, count, blk, orig,
-                                                      flags, fa.fstart, fa.fid);
+                                                      flags, fa.fstart, fa.fid, pos);
   return cudaGetLastError();
 }
 

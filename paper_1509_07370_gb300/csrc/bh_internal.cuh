@@ -70,6 +70,7 @@ struct Tree {
   int *d_count = nullptr, *d_prestart = nullptr;
   int4 *d_blk = nullptr;
   int *d_orig = nullptr;
+  int *d_pos = nullptr;         // sorted position of each caller block
   unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total
   unsigned *h_flags = nullptr;  // pinned mirror of d_flags
   // fields
@@ -136,7 +137,7 @@ cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk,
                                   int *count, int4 *blk, int *orig, unsigned *flags,
-                                  const FieldArgs &fa);
+                                  const FieldArgs &fa, int *pos = nullptr);
 cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
                                  unsigned *flags);
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
@@ -194,4 +195,39 @@ __host__ __device__ inline int cell_offset(int m) {
   return 3 + 73 * (m >> 6) + 9 * ((m >> 3) & 7) + (m & 7);
 }
 
+// ---- learned correction (bh_learn.cu, bh_walk.cu) ---------------------------
+constexpr int kMlpIn = 10, kMlpH = 64;
+// FP32 master weights, flat: W1[10][64], b1[64], W2[64][64], b2[64], W3[64], b3
+constexpr int kMlpNW = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
+// Inference copy for the tensor-core walk: bf16 weights stored n-major
+// (w1t[n][k], k padded 10 -> 16; w2t[n][k]; w3t[n][k] with rows 1..7 zero),
+// FP32 biases.
+struct MlpDev {
+  uint16_t w1t[kMlpH * 16];
+  uint16_t w2t[kMlpH * kMlpH];
+  uint16_t w3t[8 * kMlpH];
+  float b1[kMlpH];
+  float b2[kMlpH];
+  float b3;
+  float pad[3];
+};
+
+}  // namespace bhg
+
+// The context (shared by the C-ABI translation units).
+struct bh_ctx {
+  bh_options opt;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bhg::Tree tree;
+  bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
+  char err[512] = {0};
+};
+
+namespace bhg {
+// Records a one-line reason on the context and returns st.
+bh_status ctx_fail(bh_ctx *c, bh_status st, const char *fmt, ...);
+// Checks theta and the tree, and prepares the opening radii for theta.
+bh_status ctx_prepare(bh_ctx *ctx, double theta);
+cudaError_t launch_walk_learned(cudaStream_t s, bh_ctx *ctx, double G, void *out);
 }  // namespace bhg

@@ -1,0 +1,401 @@
+// Learned residual correction of accepted nodes (not in the paper).
+//
+// The walk accepts a node and adds its monopole M/d.  The correction
+// multiplies that term by (1 + s^2 y), y = MLP(x), s = l/d, where x holds ten
+// features of the (target, node) pair:
+//   u = d/|d| (3), s, s^2, s^3, delta/l, u^T Q u / (M l^2), |Q|_F / (M l^2),
+//   s^2 u^T Q u / (M l^2)
+// (Q: the node's traceless quadrupole about its centre of mass, so the
+// quadrupole option's records are needed).  The network is 10 -> 64 -> 64 -> 1
+// with tanh-form GELU activations.
+//
+// This file holds what trains it, on the GPU:
+//   * k_pairs_list / k_pairs_eval: the method's own residuals -- for sampled
+//     target cells, every internal node their per-cell walk accepts (the same
+//     binary32 opening test as the walk), and for each pair the node's exact
+//     contribution summed over its cells in FP64: eps = exact/(M/d) - 1;
+//   * k_mlp_grad / k_mlp_adam: forward and backward passes of the MLP over a
+//     batch (mean squared error against z = eps/s^2) and an Adam update, in
+//     FP32 on the CUDA cores;
+// and bh_set_mlp, which rounds trained weights to bf16 for the tensor-core
+// evaluation inside the walk (bh_walk.cu).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bh_internal.cuh"
+
+namespace bhg {
+namespace {
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// Cell centre (box units, exact) of caller cell c.
+__device__ __forceinline__ void cell_centre(int64_t c, const int *pos, const int4 *blk, int &p,
+                                            float &tx, float &ty, float &tz) {
+  const int b = (int)(c >> 9), li = (int)(c & 511);
+  const int cx = li & 7, cy = (li >> 3) & 7, cz = li >> 6;
+  p = pos[b];
+  const int4 B = blk[p];
+  const float hh = pow2f(-(B.x + 3 + 1));
+  tx = __fmul_rn((float)(2 * (8 * B.y + cx) + 1), hh);
+  ty = __fmul_rn((float)(2 * (8 * B.z + cy) + 1), hh);
+  tz = __fmul_rn((float)(2 * (8 * B.w + cz) + 1), hh);
+}
+
+// One thread per target: its per-cell walk (single-lane version of the warp
+// walk, same binary32 test), listing every accepted internal node.
+__global__ void k_pairs_list(int ntargets, const int64_t *__restrict__ targets,
+                             const int *__restrict__ pos, const int4 *__restrict__ blk,
+                             const int4 *__restrict__ fld, const WalkRec *__restrict__ rec,
+                             int64_t cap, int64_t *__restrict__ pairs,
+                             unsigned long long *__restrict__ counter) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntargets) return;
+  const int64_t c = targets[i];
+  int p;
+  float tx, ty, tz;
+  cell_centre(c, pos, blk, p, tx, ty, tz);
+  const int4 F = fld[p];
+  unsigned node = (unsigned)F.x;
+  while (node < (unsigned)F.y) {
+    const WalkRec r = rec[node];
+    const float dx = __fsub_rn(tx, r.px), dy = __fsub_rn(ty, r.py), dz = __fsub_rn(tz, r.pz);
+    const float d2 = __fmaf_rn(dx, dx, __fmaf_rn(dz, dz, __fmul_rn(dy, dy)));
+    if (r.s2 > 0.0f && d2 > r.s2) {  // an accepted internal node
+      const unsigned long long slot = atomicAdd(counter, 1ull);
+      if ((int64_t)slot < cap) {
+        pairs[2 * slot] = c;
+        pairs[2 * slot + 1] = node;
+      }
+      node = r.skip;
+    } else {
+      node = node + 1;  // opened (internal) or a cell, whose skip is node + 1
+    }
+  }
+}
+
+// One CTA per pair: features and the exact residual eps in FP64.
+constexpr int kEvalThreads = 256;
+__global__ void __launch_bounds__(kEvalThreads)
+    k_pairs_eval(int64_t npairs, const int64_t *__restrict__ pairs, const int *__restrict__ pos,
+                 const int4 *__restrict__ blk, const WalkRec *__restrict__ rec,
+                 const double4_32a *__restrict__ mom, const float2 *__restrict__ aux,
+                 const WalkQuad *__restrict__ qrec, float *__restrict__ feat,
+                 float *__restrict__ eps, int64_t *__restrict__ node_out) {
+  __shared__ double part[kEvalThreads];
+  const int64_t q = blockIdx.x;
+  if (q >= npairs) return;
+  const int64_t c = pairs[2 * q];
+  const unsigned n = (unsigned)pairs[2 * q + 1];
+  int p;
+  float txf, tyf, tzf;
+  cell_centre(c, pos, blk, p, txf, tyf, tzf);
+  const double tx = txf, ty = tyf, tz = tzf;
+  const unsigned end = rec[n].skip;
+  double acc = 0.0;
+  for (unsigned k = n + 1 + threadIdx.x; k < end; k += kEvalThreads) {
+    if (rec[k].s2 > 0.0f) continue;  // internal: only cells count
+    const double4_32a m = mom[k];
+    const double ex = tx - m.x, ey = ty - m.y, ez = tz - m.z;
+    acc += m.w / sqrt(ex * ex + ey * ey + ez * ez);
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kEvalThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double4_32a m = mom[n];
+  const double dx = tx - m.x, dy = ty - m.y, dz = tz - m.z;
+  const double D = sqrt(dx * dx + dy * dy + dz * dz);
+  const double ux = dx / D, uy = dy / D, uz = dz / D;
+  const double l = (double)aux[n].x, delta = (double)aux[n].y;
+  const double s = l / D;
+  const WalkQuad w = qrec[n];
+  const double Qxx = 2.0 * w.hxx, Qyy = 2.0 * w.hyy, Qzz = 2.0 * w.hzz;
+  const double quu = Qxx * ux * ux + Qyy * uy * uy + Qzz * uz * uz +
+                     2.0 * (w.qxy * ux * uy + w.qxz * ux * uz + w.qyz * uy * uz);
+  const double qf = sqrt(Qxx * Qxx + Qyy * Qyy + Qzz * Qzz +
+                         2.0 * ((double)w.qxy * w.qxy + (double)w.qxz * w.qxz +
+                                (double)w.qyz * w.qyz));
+  const double ml2 = m.w > 0.0 ? m.w * l * l : 1.0;
+  float *f = feat + kMlpIn * q;
+  f[0] = (float)ux;
+  f[1] = (float)uy;
+  f[2] = (float)uz;
+  f[3] = (float)s;
+  f[4] = (float)(s * s);
+  f[5] = (float)(s * s * s);
+  f[6] = (float)(delta / l);
+  f[7] = (float)(quu / ml2);
+  f[8] = (float)(qf / ml2);
+  f[9] = (float)(s * s * quu / ml2);
+  eps[q] = (float)(part[0] / (m.w / D) - 1.0);
+  if (node_out) node_out[q] = n;
+}
+
+// ---- MLP training (FP32, CUDA cores) ---------------------------------------
+// 64 samples per CTA of 256 threads; 4 threads per sample split the hidden
+// units; the CTA's weight gradients are summed over its samples and added
+// to the global gradient with one atomic per weight.
+constexpr int kMlpSamples = 64;
+constexpr int kMlpThreads = 256;
+
+__device__ __forceinline__ float gelu_f(float a) {
+  const float c = 0.7978845608028654f;
+  return 0.5f * a * (1.0f + tanhf(c * (a + 0.044715f * a * a * a)));
+}
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  const float c = 0.7978845608028654f;
+  const float t = tanhf(c * (a + 0.044715f * a * a * a));
+  return 0.5f * (1.0f + t) + 0.5f * a * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * a * a);
+}
+
+struct MlpSmem {
+  float w[kMlpNW];
+  float x[kMlpSamples][kMlpIn];
+  float a1[kMlpSamples][kMlpH], h1[kMlpSamples][kMlpH], a2[kMlpSamples][kMlpH];
+  float d1[kMlpSamples][kMlpH], d2[kMlpSamples][kMlpH];
+  float dy[kMlpSamples];
+  float red[kMlpThreads / 32];
+};
+
+__global__ void __launch_bounds__(kMlpThreads)
+    k_mlp_grad(int64_t n, const float *__restrict__ x, const float *__restrict__ z,
+               const float *__restrict__ w, float *__restrict__ grad, float *__restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
+  const int t = threadIdx.x;
+  const int64_t base = (int64_t)blockIdx.x * kMlpSamples;
+  for (int i = t; i < kMlpNW; i += kMlpThreads) S.w[i] = w[i];
+  for (int i = t; i < kMlpSamples * kMlpIn; i += kMlpThreads) {
+    const int64_t g = base + i / kMlpIn;
+    S.x[i / kMlpIn][i % kMlpIn] = g < n ? x[base * kMlpIn + i] : 0.0f;
+  }
+  __syncthreads();
+  const float *W1 = S.w, *b1 = W1 + kMlpIn * kMlpH, *W2 = b1 + kMlpH, *b2 = W2 + kMlpH * kMlpH;
+  const float *W3 = b2 + kMlpH, *b3 = W3 + kMlpH;
+  const int smp = t >> 2, qtr = t & 3;       // sample, quarter of the hidden units
+  const int64_t g = base + smp;
+  const bool valid = g < n;
+  for (int j = qtr * 16; j < qtr * 16 + 16; ++j) {
+    float a = b1[j];
+    for (int k = 0; k < kMlpIn; ++k) a += S.x[smp][k] * W1[k * kMlpH + j];
+    S.a1[smp][j] = a;
+    S.h1[smp][j] = gelu_f(a);
+  }
+  __syncthreads();
+  float y = 0.0f;
+  for (int j = qtr * 16; j < qtr * 16 + 16; ++j) {
+    float a = b2[j];
+    for (int k = 0; k < kMlpH; ++k) a += S.h1[smp][k] * W2[k * kMlpH + j];
+    S.a2[smp][j] = a;
+    y += gelu_f(a) * W3[j];
+  }
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += b3[0];
+  const float r = valid ? y - z[g] : 0.0f;
+  const float dy = 2.0f * r / (float)n;
+  if (qtr == 0) S.dy[smp] = dy;
+  for (int j = qtr * 16; j < qtr * 16 + 16; ++j) S.d2[smp][j] = dy * W3[j] * gelu_grad_f(S.a2[smp][j]);
+  __syncthreads();
+  for (int i = qtr * 16; i < qtr * 16 + 16; ++i) {
+    float a = 0.0f;
+    for (int j = 0; j < kMlpH; ++j) a += W2[i * kMlpH + j] * S.d2[smp][j];
+    S.d1[smp][i] = a * gelu_grad_f(S.a1[smp][i]);
+  }
+  // loss: sum of r^2 / n over the CTA
+  float l2 = (qtr == 0) ? r * r / (float)n : 0.0f;
+  for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+  if ((t & 31) == 0) S.red[t >> 5] = l2;
+  __syncthreads();
+  if (t == 0) {
+    float tot = 0.0f;
+    for (int k = 0; k < kMlpThreads / 32; ++k) tot += S.red[k];
+    atomicAdd(loss, tot);
+  }
+  // weight gradients of this CTA's samples
+  for (int e = t; e < kMlpNW; e += kMlpThreads) {
+    float acc = 0.0f;
+    if (e < kMlpIn * kMlpH) {                                   // W1[k][j]
+      const int k = e / kMlpH, j = e % kMlpH;
+      for (int s = 0; s < kMlpSamples; ++s) acc += S.x[s][k] * S.d1[s][j];
+    } else if (e < kMlpIn * kMlpH + kMlpH) {                    // b1[j]
+      const int j = e - kMlpIn * kMlpH;
+      for (int s = 0; s < kMlpSamples; ++s) acc += S.d1[s][j];
+    } else if (e < kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH) {    // W2[i][j]
+      const int ij = e - (kMlpIn * kMlpH + kMlpH), i = ij / kMlpH, j = ij % kMlpH;
+      for (int s = 0; s < kMlpSamples; ++s) acc += S.h1[s][i] * S.d2[s][j];
+    } else if (e < kMlpIn * kMlpH + 2 * kMlpH + kMlpH * kMlpH) {  // b2[j]
+      const int j = e - (kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH);
+      for (int s = 0; s < kMlpSamples; ++s) acc += S.d2[s][j];
+    } else if (e < kMlpNW - 1) {                                // W3[j]
+      const int j = e - (kMlpIn * kMlpH + 2 * kMlpH + kMlpH * kMlpH);
+      for (int s = 0; s < kMlpSamples; ++s) acc += gelu_f(S.a2[s][j]) * S.dy[s];
+    } else {                                                    // b3
+      for (int s = 0; s < kMlpSamples; ++s) acc += S.dy[s];
+    }
+    atomicAdd(&grad[e], acc);
+  }
+}
+
+__global__ void k_mlp_adam(const float *__restrict__ grad, float *__restrict__ w,
+                           float *__restrict__ m, float *__restrict__ v, float lr, float b1t,
+                           float b2t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpNW) return;
+  const float beta1 = 0.9f, beta2 = 0.999f;
+  const float g = grad[i];
+  const float mi = beta1 * m[i] + (1.0f - beta1) * g;
+  const float vi = beta2 * v[i] + (1.0f - beta2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + 1e-8f);
+}
+
+uint16_t to_bf16(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float from_bf16(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+}  // namespace bhg
+
+using namespace bhg;
+
+extern "C" {
+
+bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int64_t *targets,
+                         int64_t cap, float *feat, float *eps, int64_t *node, int64_t *count) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->opt.quadrupole && !ctx->opt.learned)
+    return ctx_fail(ctx, BH_ERR_STATE, "bh_learn_pairs: the context needs the quadrupole option");
+  if (ntargets < 0 || (ntargets > 0 && !targets) || cap < 0 || (cap > 0 && (!feat || !eps)) ||
+      !count)
+    return ctx_fail(ctx, BH_ERR_ARG, "bh_learn_pairs: bad arguments");
+  bh_status st = ctx_prepare(ctx, theta);
+  if (st != BH_OK) return st;
+  Tree &t = ctx->tree;
+  cudaStream_t s = ctx->stream;
+  int64_t *d_pairs = nullptr;
+  unsigned long long *d_count = nullptr;
+  const int64_t pcap = cap > 0 ? cap : 1;
+  cudaError_t e = cudaMalloc(&d_pairs, (size_t)pcap * 2 * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess && ntargets > 0) {
+    k_pairs_list<<<(unsigned)((ntargets + 127) / 128), 128, 0, s>>>(
+        (int)ntargets, targets, t.d_pos, t.d_blk, t.d_fld, t.d_rec, cap, d_pairs, d_count);
+    e = cudaGetLastError();
+  }
+  unsigned long long h_count = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_count, d_count, sizeof(h_count), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const int64_t np = (int64_t)h_count < cap ? (int64_t)h_count : cap;
+  if (e == cudaSuccess && np > 0) {
+    k_pairs_eval<<<(unsigned)np, kEvalThreads, 0, s>>>(np, d_pairs, t.d_pos, t.d_blk, t.d_rec,
+                                                        t.d_mom, t.d_aux, t.d_qrec, feat, eps,
+                                                        node);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_pairs);
+  cudaFree(d_count);
+  if (e != cudaSuccess)
+    return ctx_fail(ctx, BH_ERR_CUDA, "bh_learn_pairs: %s", cudaGetErrorString(e));
+  *count = (int64_t)h_count;
+  return BH_OK;
+}
+
+bh_status bh_mlp_grad(int64_t n, const float *x, const float *z, const float *w, float *grad,
+                      float *loss, void *cuda_stream) {
+  if (n <= 0 || !x || !z || !w || !grad || !loss) return BH_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int smem = (int)sizeof(MlpSmem);
+  if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaMemsetAsync(grad, 0, kMlpNW * sizeof(float), s) != cudaSuccess ||
+      cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) {
+    cudaGetLastError();
+    return BH_ERR_CUDA;
+  }
+  k_mlp_grad<<<(unsigned)((n + kMlpSamples - 1) / kMlpSamples), kMlpThreads, smem, s>>>(
+      n, x, z, w, grad, loss);
+  if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+  return BH_OK;
+}
+
+bh_status bh_mlp_adam(const float *grad, float *w, float *m, float *v, int step, float lr,
+                      void *cuda_stream) {
+  if (!grad || !w || !m || !v || step < 1 || !(lr > 0.0f)) return BH_ERR_ARG;
+  const float b1t = powf(0.9f, (float)step), b2t = powf(0.999f, (float)step);
+  k_mlp_adam<<<(kMlpNW + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(grad, w, m, v, lr, b1t,
+                                                                          b2t);
+  if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+  return BH_OK;
+}
+
+bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!w_host) return ctx_fail(ctx, BH_ERR_ARG, "bh_set_mlp: weights are null");
+  MlpDev h;
+  std::memset(&h, 0, sizeof(h));
+  const float *W1 = w_host, *b1 = W1 + kMlpIn * kMlpH, *W2 = b1 + kMlpH;
+  const float *b2 = W2 + kMlpH * kMlpH, *W3 = b2 + kMlpH, *b3 = W3 + kMlpH;
+  for (int j = 0; j < kMlpH; ++j) {
+    for (int k = 0; k < kMlpIn; ++k) h.w1t[j * 16 + k] = to_bf16(W1[k * kMlpH + j]);
+    for (int k = 0; k < kMlpH; ++k) h.w2t[j * kMlpH + k] = to_bf16(W2[k * kMlpH + j]);
+    h.w3t[j] = to_bf16(W3[j]);
+    h.b1[j] = b1[j];
+    h.b2[j] = b2[j];
+  }
+  h.b3 = b3[0];
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
+  if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(ctx, BH_ERR_OOM, "bh_set_mlp: no device memory");
+  }
+  if (cudaMemcpy(ctx->d_mlp, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(ctx, BH_ERR_CUDA, "bh_set_mlp: copy failed");
+  }
+  return BH_OK;
+}
+
+bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host) {
+  if (!ctx || !w_host) return BH_ERR_ARG;
+  if (!ctx->d_mlp) return BH_ERR_STATE;
+  MlpDev h;
+  if (cudaMemcpy(&h, ctx->d_mlp, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return BH_ERR_CUDA;
+  }
+  float *W1 = w_host, *b1 = W1 + kMlpIn * kMlpH, *W2 = b1 + kMlpH;
+  float *b2 = W2 + kMlpH * kMlpH, *W3 = b2 + kMlpH, *b3 = W3 + kMlpH;
+  for (int j = 0; j < kMlpH; ++j) {
+    for (int k = 0; k < kMlpIn; ++k) W1[k * kMlpH + j] = from_bf16(h.w1t[j * 16 + k]);
+    for (int k = 0; k < kMlpH; ++k) W2[k * kMlpH + j] = from_bf16(h.w2t[j * kMlpH + k]);
+    W3[j] = from_bf16(h.w3t[j]);
+    b1[j] = h.b1[j];
+    b2[j] = h.b2[j];
+  }
+  b3[0] = h.b3;
+  return BH_OK;
+}
+
+}  // extern "C"

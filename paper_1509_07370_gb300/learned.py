@@ -1,0 +1,99 @@
+"""Training of the learned residual correction on the GPU.
+
+The walk accepts a node and adds its monopole M/d; the learned walk adds
+(M/d)(1 + s^2 y) with y = MLP(x) of ten pair features (see include/bhgrav.h).
+The network learns z = eps / s^2, where eps is the node's exact error against
+its monopole.  Everything runs in the library's own kernels:
+  * bh_learn_pairs lists, for sampled target cells of seeded training fields,
+    every internal node their walk accepts and the exact residual of each pair;
+  * bh_mlp_grad / bh_mlp_adam run the forward and backward passes and the
+    optimiser steps.
+Training fields: homogeneous oblate spheroids (the Maclaurin family of the
+accuracy test) with seeded semi-axis a1 in [0.12, 0.3] and eccentricity in
+[0.3, 0.95], on meshes of 16^3 cells refined twice at the surface.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import bhgrav as bh
+from . import meshgen as mg
+
+NW = bh.MLP_NW
+
+
+def training_field(seed: int) -> mg.Workload:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a1 = float(rng.uniform(0.12, 0.3))
+    e = float(rng.uniform(0.3, 0.95))
+    return mg.maclaurin(base_level=1, extra_levels=2, a1=a1, e=e, rho_out=1e-4)
+
+
+def init_weights(seed: int = 0) -> np.ndarray:
+    """Glorot-uniform weights, zero biases, in the flat layout."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fan_in, fan_out in ((10, 64), (64, 64), (64, 1)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: int,
+             cap: int = 1 << 20):
+    """(features, z) of the accepted pairs of `ntargets` random cells."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tg = torch.as_tensor(rng.choice(ncells, min(ntargets, ncells), replace=False),
+                         dtype=torch.int64, device=solver.device)
+    feat, eps, _ = solver.learn_pairs(theta, tg, cap)
+    s = feat[:, 3]
+    return feat, eps / (s * s)
+
+
+def make_dataset(nfields: int = 200, theta: float = 0.8, targets_per_field: int = 64,
+                 seed0: int = 9000, device: int = 0):
+    """Method-generated training pairs from `nfields` seeded fields."""
+    import torch
+    xs, zs = [], []
+    for i in range(nfields):
+        w = training_field(seed0 + i)
+        s = bh.Solver(quadrupole=True, device=device)
+        s.build(w.mesh.level, w.mesh.ijk,
+                torch.as_tensor(w.density.reshape(-1), dtype=torch.float32,
+                                device=s.device))
+        x, z = pairs_of(s, w.ncells, theta, targets_per_field, seed0 + 100000 + i)
+        xs.append(x)
+        zs.append(z)
+        s.close()
+    return torch.cat(xs), torch.cat(zs)
+
+
+def train(x, z, epochs: int = 8, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+          w0: np.ndarray | None = None, stream: int = 0):
+    """Adam on the mean squared error of MLP(x) against z; returns the FP32
+    weights and the per-epoch mean losses."""
+    import torch
+    dev = x.device
+    w = torch.as_tensor(init_weights(seed) if w0 is None else w0, device=dev).contiguous()
+    m = torch.zeros(NW, device=dev)
+    v = torch.zeros(NW, device=dev)
+    g = torch.empty(NW, device=dev)
+    loss = torch.empty(1, device=dev)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    n = z.numel()
+    step = 0
+    history = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=gen).to(dev)
+        tot = 0.0
+        for b0 in range(0, n, batch):
+            idx = perm[b0:b0 + batch]
+            xb, zb = x[idx].contiguous(), z[idx].contiguous()
+            bh.bh_mlp_grad(xb, zb, w, g, loss, stream)
+            step += 1
+            bh.bh_mlp_adam(g, w, m, v, step, lr, stream)
+            tot += float(loss.item()) * idx.numel()
+        history.append(tot / n)
+    return w.cpu().numpy(), history

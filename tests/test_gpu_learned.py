@@ -1,0 +1,119 @@
+"""The learned residual correction on the GPU, against the CPU oracle.
+
+Bars:
+  * training pairs: the same accepted nodes as the oracle's walk (exact, the
+    decisions are bit-exact), features within 1e-5 (the GPU reads binary32
+    quadrupoles), eps within 1e-6 absolute (both sum the node's cells in FP64);
+  * gradients of the loss: within 1e-4 of the largest gradient component
+    (FP32 accumulation over the batch vs the oracle's FP64);
+  * the learned walk against the oracle's FP64 evaluation with the same
+    bf16-rounded weights: within 2 % of the largest network contribution
+    (learned walk minus monopole walk) plus 1e-5 of the potential -- the
+    tensor-core path rounds the features and the hidden activations to bf16
+    (8 significant bits, relative 2^-9 each, through two 64-wide layers) and
+    uses the hardware tanh approximation, so each node's correction carries
+    about 1 % error; corrections of different nodes can cancel in a cell, so
+    the bound scales with their size, not with a cell's net correction;
+  * what the trained network gains: smaller max error against the direct sum
+    than the plain walk at the same theta, on a field it was not trained on.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_1509_07370_gb300 import bhgrav as B  # noqa: E402
+from paper_1509_07370_gb300 import learned as L  # noqa: E402
+from paper_1509_07370_gb300 import meshgen as mg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _field():
+    return mg.maclaurin(base_level=1, extra_levels=2, a1=0.22, e=0.85)
+
+
+def _gpu(w, learned=False):
+    s = B.Solver(quadrupole=not learned, learned=learned)
+    s.build(w.mesh.level, w.mesh.ijk, torch.as_tensor(w.density.reshape(-1)).cuda())
+    return s
+
+
+def test_training_pairs_match_oracle():
+    w = _field()
+    s = _gpu(w)
+    t = O.Tree.from_workload(w)
+    for tgt in np.random.default_rng(3).choice(w.ncells, 8, replace=False):
+        f, e, n, nd = s.learn_pairs(0.8, torch.tensor([tgt], device="cuda"), 4096,
+                                    with_nodes=True)
+        order = torch.argsort(nd)
+        f, e, nd = (x[order].cpu().numpy() for x in (f, e, nd))
+        fo, eo, ndo = t.learn_pairs(0.8, tgt)
+        o = np.argsort(ndo)
+        assert n == len(ndo) and np.array_equal(nd, ndo[o])
+        assert np.abs(f - fo[o]).max() <= 1e-5
+        assert np.abs(e - eo[o]).max() <= 1e-6
+
+
+def test_mlp_gradient_matches_oracle():
+    rng = np.random.default_rng(5)
+    w = L.init_weights(7) + rng.normal(0, 0.02, B.MLP_NW).astype(np.float32)
+    x = rng.normal(0, 1, (1000, 10)).astype(np.float32)
+    z = rng.normal(0, 0.3, 1000).astype(np.float32)
+    g = torch.empty(B.MLP_NW, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    B.bh_mlp_grad(torch.as_tensor(x).cuda(), torch.as_tensor(z).cuda(),
+                  torch.as_tensor(w).cuda(), g, loss)
+    torch.cuda.synchronize()
+    lo, go = O.mlp_loss_grad(w.astype(np.float64), x.astype(np.float64), z.astype(np.float64))
+    assert abs(float(loss.item()) / lo - 1) < 1e-5
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-4 * np.abs(go).max()
+
+
+def test_adam_step_lowers_the_loss():
+    rng = np.random.default_rng(1)
+    x = torch.as_tensor(rng.normal(0, 1, (4096, 10)).astype(np.float32)).cuda()
+    z = (x[:, 3] * 0.5 - x[:, 7] * 0.2).contiguous()
+    w, hist = L.train(x, z, epochs=6, batch=1024, lr=3e-3, seed=2)
+    assert hist[-1] < 0.2 * hist[0]
+
+
+def test_learned_walk_matches_oracle():
+    w = _field()
+    x, z = L.pairs_of(_gpu(w), w.ncells, 0.8, 256, seed=11)
+    wts, _ = L.train(x, z, epochs=3, batch=2048, seed=3)
+    s = _gpu(w, learned=True)
+    s.set_mlp(wts)
+    phi = s.potential(0.8).cpu().numpy()
+    wb = s.get_mlp().astype(np.float64)                   # the bf16 weights in use
+    t = O.Tree.from_workload(w)
+    tg = np.random.default_rng(2).choice(w.ncells, 600, replace=False)
+    learned = t.walk_learned(0.8, wb, targets=tg)
+    mono = t.walk(0.8, targets=tg)[0]
+    corr = np.abs(learned - mono)
+    assert corr.max() > 1e-6 * np.abs(mono).max()        # the network does something
+    assert np.all(np.abs(phi[tg] - learned) <= 0.02 * corr.max() + 1e-5 * np.abs(learned))
+
+
+def test_trained_network_beats_the_plain_walk_at_the_same_theta():
+    xs, zs = [], []
+    for i in range(24):
+        f = L.training_field(9000 + i)
+        x, z = L.pairs_of(_gpu(f), f.ncells, 0.8, 64, seed=i)
+        xs.append(x)
+        zs.append(z)
+    wts, hist = L.train(torch.cat(xs), torch.cat(zs), epochs=4, batch=4096, seed=0)
+    test = mg.maclaurin(base_level=2, extra_levels=2)     # not a training field
+    s = _gpu(test, learned=True)
+    s.set_mlp(wts)
+    phi_l = s.potential(0.8).cpu().numpy()
+    plain = B.Solver()
+    plain.build(test.mesh.level, test.mesh.ijk, torch.as_tensor(test.density.reshape(-1)).cuda())
+    phi_p = plain.potential(0.8).cpu().numpy()
+    t = O.Tree.from_workload(test)
+    tg = np.random.default_rng(4).choice(test.ncells, 1500, replace=False)
+    d = t.direct(targets=tg)
+    err_l = np.abs(phi_l[tg] / d - 1).max()
+    err_p = np.abs(phi_p[tg] / d - 1).max()
+    assert err_l < 0.5 * err_p, (err_l, err_p)
