@@ -50,15 +50,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="maclaurin",
-                    choices=["maclaurin", "cloud_core", "uniform_sphere", "batched"])
+                    choices=["maclaurin", "cloud_core", "uniform_sphere", "batched", "learned"])
     ap.add_argument("--theta", type=float, default=None,
-                    help="default 0.7 (quadrupole headline); 0.5 for --workload batched")
+                    help="default 0.7 (quadrupole headline); 0.5 for --workload batched; "
+                         "0.8 for --workload learned")
     ap.add_argument("--monopole", action="store_true",
                     help="plain monopole nodes (default: with the quadrupole term)")
     ap.add_argument("--vote", action="store_true",
                     help="the paper's warp vote instead of the per-cell test")
-    ap.add_argument("--plain-theta", type=float, default=0.3,
-                    help="theta of the plain monopole walk timed for vs_plain")
+    ap.add_argument("--plain-theta", type=float, default=None,
+                    help="theta of the plain monopole walk timed for vs_plain "
+                         "(default 0.3; 0.4 for --workload learned)")
+    ap.add_argument("--train-fields", type=int, default=200,
+                    help="--workload learned: seeded training fields")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -69,7 +73,7 @@ def parse():
 
 def workload(name):
     from paper_1509_07370_gb300 import meshgen as mg
-    if name == "maclaurin":
+    if name in ("maclaurin", "learned"):
         return mg.maclaurin()
     if name == "cloud_core":
         return mg.cloud_core()
@@ -407,14 +411,196 @@ def batched_arm(args):
     s.close()
 
 
+def learned_oracle_leg(w, theta, wts, plain_theta, phi, cpu_seconds):
+    """The CPU oracle's learned walk (FP64, same bf16-rounded weights) timed on
+    a sample of targets, and the max relative errors against the direct sum of
+    the learned walk and of the plain monopole walk at both thetas."""
+    from oracle import oracle as O
+    rho = w.density.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    tree = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+    tree.quadrupoles()
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(4321)
+    n = w.ncells
+    probe = rng.choice(n, 200, replace=False)
+    tree.walk_learned(theta, wts, targets=probe[:16])
+    t0 = time.perf_counter()
+    tree.walk_learned(theta, wts, targets=probe)
+    per = (time.perf_counter() - t0) / len(probe)
+    k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
+    tg = np.sort(rng.choice(n, k, replace=False))
+    t0 = time.perf_counter()
+    ref = tree.walk_learned(theta, wts, targets=tg)
+    t_walk = time.perf_counter() - t0
+    m = min(k, 2000)
+    d = tree.direct(targets=tg[:m])
+
+    def rel(a):
+        return float(np.max(np.abs(a[tg[:m]] / d - 1.0)))
+    acc = {"learned_max_rel_vs_direct": rel(phi["learned"]),
+           "plain_max_rel_vs_direct": rel(phi["plain"]),
+           "plain_same_theta_max_rel_vs_direct": rel(phi["same"]),
+           "learned_max_abs_vs_oracle_learned": float(np.max(np.abs(phi["learned"][tg] - ref))),
+           "learned_max_rel_vs_oracle_learned": float(np.max(np.abs(phi["learned"][tg] / ref - 1))),
+           "theta": theta, "plain_theta": plain_theta,
+           "cells_compared": int(k), "cells_vs_direct": int(m)}
+    return {"value": n / (t_build + t_walk * n / k), "unit": "cells/s",
+            "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"tree+FP64 moments+quadrupoles of all {n} cells; learned walk (FP64 MLP) "
+                      f"of {k} random cells (seed 4321, theta {theta}) extrapolated to {n}; "
+                      f"build {t_build:.2f}s, walk {t_walk:.2f}s",
+            "accuracy": acc}
+
+
+def learned_arm(args):
+    """Learned residual correction on the Maclaurin spheroid (2,039,808 cells):
+    the walk at theta 0.8 whose accepted nodes' terms are corrected by the
+    MLP, against the plain monopole walk at theta 0.4 and, for the gain, at
+    0.8.  The network is first trained on the GPU (untimed, reported) from
+    the accepted pairs of seeded spheroid fields."""
+    import torch
+    from paper_1509_07370_gb300 import bhgrav as bh
+    from paper_1509_07370_gb300 import learned as L
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    x, z = L.make_dataset(nfields=args.train_fields, theta=args.theta, device=local)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    wts, hist = L.train(x, z, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    npairs = int(z.numel())
+    del x, z
+
+    w = workload("learned")
+    n = w.ncells
+    mesh = w.mesh
+    rho32 = np.ascontiguousarray(w.density.reshape(-1), dtype=np.float32)
+    d_rho = torch.as_tensor(rho32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    phi = {}
+    clk = ClockSampler(local)
+    for key, theta, learned, steps in (("learned", args.theta, True, args.steps),
+                                       ("plain", args.plain_theta, False, args.steps),
+                                       ("same", args.theta, False, max(5, args.steps // 3))):
+        s = bh.Solver(learned=learned, device=local, stream=stream)
+        if learned:
+            s.set_mlp(wts)
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        st, bt, wt = timed_steps(s, mesh, d_rho, theta, out, steps, args.warmup, flush, stream,
+                                 clk if learned else None)
+        ni, nt, nc = s.walk_counts(theta, with_cells=True)
+        res[key] = {"theta": theta, "steps": steps, "ms_per_step": float(np.mean(st)),
+                    "value": n / (float(np.mean(st)) * 1e-3),
+                    "phases_ms": {"build": float(np.mean(bt)), "potential": float(np.mean(wt))},
+                    "interactions": int(ni.sum(dtype=torch.int64).item()),
+                    "cell_interactions": int(nc.sum(dtype=torch.int64).item()),
+                    "tests": int(nt.sum(dtype=torch.int64).item())}
+        phi[key] = out.double().cpu().numpy()
+        if learned:
+            wts_dev = s.get_mlp().astype(np.float64)
+            _, nn, maxlev = s.tree_size()
+            e2e = None
+            if not args.no_e2e:
+                h_rho = torch.from_numpy(rho32).pin_memory().numpy()
+                h_out = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+                for _ in range(max(1, args.warmup)):
+                    s.solve_host(mesh.level, mesh.ijk, h_rho, theta, 1.0, h_out)
+                ts = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    s.solve_host(mesh.level, mesh.ijk, h_rho, theta, 1.0, h_out)
+                    ts.append(time.perf_counter() - t1)
+                e2e = {"value": n / float(np.mean(ts)), "unit": "cells/s",
+                       "h2d_bytes_per_step": int(rho32.nbytes + mesh.level.nbytes
+                                                 + mesh.ijk.nbytes),
+                       "d2h_bytes_per_step": int(h_out.nbytes)}
+        s.close()
+    L_ = res["learned"]
+    walk_s = L_["phases_ms"]["potential"] * 1e-3
+    n_node = L_["interactions"] - L_["cell_interactions"]
+    mlp_flops = 2 * (10 * 64 + 64 * 64 + 64) * n_node      # algorithmic MACs x 2
+    gelu_ops = 128 * 9 * n_node                             # 128 GELUs of 9 FP32 ops
+    walk_ops = (FLOP_PER_INTERACTION * L_["interactions"] + FLOP_PER_TEST * L_["tests"]
+                + gelu_ops)
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
+    alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
+    bf16_peak = measured_peak("bf16_tflops") * 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = learned_oracle_leg(w, args.theta, wts_dev, args.plain_theta, phi, args.cpu_seconds)
+    line = {
+        "metric": "cell potentials/sec", "value": L_["value"], "unit": "cells/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": L_["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name + " learned", "cells": n, "nodes": nn,
+                   "theta": args.theta,
+                   "walk": "binary32, Kahan sum, per-cell opening test, monopole nodes times "
+                           "(1 + s^2 MLP(x)); MLP 10-64-64-1 GELU, bf16 weights and "
+                           "activations, FP32 accumulate (mma.sync m16n8k16)",
+                   "training": {"fields": args.train_fields, "pairs": npairs,
+                                "epochs": len(hist), "loss_first_last": [hist[0], hist[-1]],
+                                "data_s": t_data, "train_s": t_train, "theta": args.theta},
+                   "moments": "f64", "l2": "flushed between steps (256 MiB write)"},
+        "phases_ms": L_["phases_ms"],
+        "walk_work": {"interactions_per_cell": L_["interactions"] / n,
+                      "node_interactions_per_cell": n_node / n,
+                      "tests_per_cell": L_["tests"] / n},
+        "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + learned walk)",
+                     "achieved": walk_ops / walk_s / 1e12, "peak": alu_peak / 1e12,
+                     "unit": "TFLOP/s", "frac": walk_ops / walk_s / alu_peak, "traffic": None,
+                     "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz",
+                     "ops": "8 per interaction, 7 per test, 128 x 9 per MLP evaluation (GELU)",
+                     "tensor": {"mlp_flops": mlp_flops,
+                                "achieved": mlp_flops / walk_s / 1e12,
+                                "peak": bf16_peak / 1e12,
+                                "frac": mlp_flops / walk_s / bf16_peak,
+                                "peak_basis": "measured bf16 dense (burst)"}},
+        "vs_plain": {"theta": args.plain_theta, "walk": "binary32, Kahan sum, per-cell, monopole",
+                     **{k: v for k, v in res["plain"].items() if k != "theta"},
+                     "speedup": L_["value"] / res["plain"]["value"]},
+        "vs_same_theta": {"theta": args.theta, "walk": "the plain walk, no network",
+                          **{k: v for k, v in res["same"].items() if k != "theta"},
+                          "speedup": L_["value"] / res["same"]["value"]},
+        "clocks": clocks, "e2e": e2e,
+        "gpu_launches": (6 + (maxlev - 3) + 2) * args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measured_peak(key):
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}.get(key, float("nan"))
+
+
 def main():
     args = parse()
     if args.theta is None:
-        args.theta = 0.5 if args.workload == "batched" else 0.7
+        args.theta = {"batched": 0.5, "learned": 0.8}.get(args.workload, 0.7)
+    if args.plain_theta is None:
+        args.plain_theta = 0.4 if args.workload == "learned" else 0.3
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batched":
         return batched_arm(args)
+    if args.workload == "learned":
+        return learned_arm(args)
     import torch
     import torch.distributed as dist
     from paper_1509_07370_gb300 import bhgrav as bh
