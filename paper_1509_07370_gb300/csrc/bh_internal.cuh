@@ -199,13 +199,18 @@ __host__ __device__ inline int cell_offset(int m) {
 constexpr int kMlpIn = 10, kMlpH = 64;
 // FP32 master weights, flat: W1[10][64], b1[64], W2[64][64], b2[64], W3[64], b3
 constexpr int kMlpNW = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
-// Inference copy for the tensor-core walk: bf16 weights stored n-major
-// (w1t[n][k], k padded 10 -> 16; w2t[n][k]; w3t[n][k] with rows 1..7 zero),
-// FP32 biases.
+// Inference copy for the tensor-core walk, in the B-fragment order of
+// mma.sync m16n8k16 (bf16): for each (n-tile, k-tile), 32 lanes x {b0, b1};
+// lane (g = lane / 4, t = lane % 4) holds W[k0 + 2t .. k0 + 2t + 1][n0 + g] in
+// b0 and W[k0 + 2t + 8 .. k0 + 2t + 9][n0 + g] in b1, the lower k in the low
+// half.  Layer 1: K = 16 (inputs 10..15 zero), 8 n-tiles; layer 2: 8 n-tiles x
+// 4 k-tiles; layer 3: 4 k-tiles of one n-tile whose column 0 is the output.
+// The walk carries activations as 2 GELU(a), so layer-2 and layer-3 weights
+// are stored halved (exact in bf16).  Biases FP32.
 struct MlpDev {
-  uint16_t w1t[kMlpH * 16];
-  uint16_t w2t[kMlpH * kMlpH];
-  uint16_t w3t[8 * kMlpH];
+  uint32_t w1f[8][32][2];
+  uint32_t w2f[8][4][32][2];
+  uint32_t w3f[4][32][2];
   float b1[kMlpH];
   float b2[kMlpH];
   float b3;

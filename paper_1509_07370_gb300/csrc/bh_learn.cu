@@ -259,7 +259,8 @@ __global__ void k_mlp_adam(const float *__restrict__ grad, float *__restrict__ w
 uint16_t to_bf16(float f) {  // round to nearest even
   uint32_t u;
   std::memcpy(&u, &f, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+  if ((u & 0x7f800000u) == 0x7f800000u)  // inf stays inf, nan stays nan
+    return (uint16_t)((u >> 16) | ((u & 0x007fffffu) ? 0x40u : 0u));
   u += 0x7fffu + ((u >> 16) & 1u);
   return (uint16_t)(u >> 16);
 }
@@ -269,6 +270,15 @@ float from_bf16(uint16_t h) {
   std::memcpy(&f, &u, 4);
   return f;
 }
+uint16_t bf16_half(uint16_t h) { return to_bf16(0.5f * from_bf16(h)); }  // exact
+
+// Place of weight W[k][n] in the B fragments of its (n-tile, k-tile)
+// (layout described with MlpDev): lane 4 (n % 8) + (k % 8) / 2, register
+// (k % 16) / 8, half k % 2.
+int frag_lane(int k, int n) { return 4 * (n & 7) + ((k & 7) >> 1); }
+int frag_reg(int k) { return (k & 15) >> 3; }
+void frag_put(uint32_t &word, int k, uint16_t v) { word |= (uint32_t)v << (16 * (k & 1)); }
+uint16_t frag_get(uint32_t word, int k) { return (uint16_t)(word >> (16 * (k & 1))); }
 
 }  // namespace
 }  // namespace bhg
@@ -357,13 +367,17 @@ bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host) {
   std::memset(&h, 0, sizeof(h));
   const float *W1 = w_host, *b1 = W1 + kMlpIn * kMlpH, *W2 = b1 + kMlpH;
   const float *b2 = W2 + kMlpH * kMlpH, *W3 = b2 + kMlpH, *b3 = W3 + kMlpH;
-  for (int j = 0; j < kMlpH; ++j) {
-    for (int k = 0; k < kMlpIn; ++k) h.w1t[j * 16 + k] = to_bf16(W1[k * kMlpH + j]);
-    for (int k = 0; k < kMlpH; ++k) h.w2t[j * kMlpH + k] = to_bf16(W2[k * kMlpH + j]);
-    h.w3t[j] = to_bf16(W3[j]);
-    h.b1[j] = b1[j];
-    h.b2[j] = b2[j];
+  for (int n = 0; n < kMlpH; ++n) {
+    for (int k = 0; k < kMlpIn; ++k)
+      frag_put(h.w1f[n >> 3][frag_lane(k, n)][frag_reg(k)], k, to_bf16(W1[k * kMlpH + n]));
+    for (int k = 0; k < kMlpH; ++k)
+      frag_put(h.w2f[n >> 3][k >> 4][frag_lane(k, n)][frag_reg(k)], k,
+               bf16_half(to_bf16(W2[k * kMlpH + n])));
+    h.b1[n] = b1[n];
+    h.b2[n] = b2[n];
   }
+  for (int k = 0; k < kMlpH; ++k)
+    frag_put(h.w3f[k >> 4][frag_lane(k, 0)][frag_reg(k)], k, bf16_half(to_bf16(W3[k])));
   h.b3 = b3[0];
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
   if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) {
@@ -387,13 +401,17 @@ bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host) {
   }
   float *W1 = w_host, *b1 = W1 + kMlpIn * kMlpH, *W2 = b1 + kMlpH;
   float *b2 = W2 + kMlpH * kMlpH, *W3 = b2 + kMlpH, *b3 = W3 + kMlpH;
-  for (int j = 0; j < kMlpH; ++j) {
-    for (int k = 0; k < kMlpIn; ++k) W1[k * kMlpH + j] = from_bf16(h.w1t[j * 16 + k]);
-    for (int k = 0; k < kMlpH; ++k) W2[k * kMlpH + j] = from_bf16(h.w2t[j * kMlpH + k]);
-    W3[j] = from_bf16(h.w3t[j]);
-    b1[j] = h.b1[j];
-    b2[j] = h.b2[j];
+  for (int n = 0; n < kMlpH; ++n) {
+    for (int k = 0; k < kMlpIn; ++k)
+      W1[k * kMlpH + n] = from_bf16(frag_get(h.w1f[n >> 3][frag_lane(k, n)][frag_reg(k)], k));
+    for (int k = 0; k < kMlpH; ++k)
+      W2[k * kMlpH + n] =
+          2.0f * from_bf16(frag_get(h.w2f[n >> 3][k >> 4][frag_lane(k, n)][frag_reg(k)], k));
+    b1[n] = h.b1[n];
+    b2[n] = h.b2[n];
   }
+  for (int k = 0; k < kMlpH; ++k)
+    W3[k] = 2.0f * from_bf16(frag_get(h.w3f[k >> 4][frag_lane(k, 0)][frag_reg(k)], k));
   b3[0] = h.b3;
   return BH_OK;
 }

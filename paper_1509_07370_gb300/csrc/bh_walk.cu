@@ -33,7 +33,7 @@
 // The opening test is evaluated in binary32 with the operation order stated
 // in the public header; the interaction uses the same d2 (binary32, Kahan
 // sum) or recomputes d in binary64 from the FP64 moments.
-#include "bh_internal.cuh"
+#include "bh_walk_common.cuh"
 
 namespace bhg {
 namespace {
@@ -41,8 +41,6 @@ namespace {
 constexpr int kWalkThreads = 256;               // default CTA: 8 warps = one block
 constexpr int kWarpsPerCta = kWalkThreads / 32;
 constexpr int kMaxWalkThreads = 512;            // largest tunable CTA
-constexpr unsigned kFull = 0xffffffffu;
-typedef unsigned long long u64;
 
 __global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, WalkRec *__restrict__ rec,
                              float inv_theta) {
@@ -53,89 +51,7 @@ __global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, WalkRec 
   rec[i].s2 = __fmul_rn(s, s);
 }
 
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-
-// ---- packed binary32 pairs and raw loads (inline PTX) -----------------------
-__device__ __forceinline__ u64 pk(float lo, float hi) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk(u64 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-  u64 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-  u64 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-  u64 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-// 1/sqrt(x) on the special-function unit.  Only called where the value is
-// used for x >= 2^-44 (an accepted node or another cell), so flushing
-// subnormal inputs changes nothing.
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-// One 32-byte walk record as four 64-bit lanes:
-//   q0 = {Px, Px}, q1 = {Py, Pz}, q2 = {M, M}, q3 = {s2, skip}
-__device__ __forceinline__ void load_rec(const WalkRec *p, u64 &q0, u64 &q1, u64 &q2, u64 &q3) {
-  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-      : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
-      : "l"(p));
-}
-
-// One 32-byte quadrupole record: w0 = {Qxx/2, Qxx/2}, w1 = {Qyy/2, Qzz/2},
-// w2 = {Qxy, Qxz}, w3 = {Qyz, 0}.
-__device__ __forceinline__ void load_quad(const WalkQuad *p, u64 &w0, u64 &w1, u64 &w2, u64 &w3) {
-  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-      : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-      : "l"(p));
-}
-
 // ---- per-cell binary32 walk, two x-neighbour targets per lane ---------------
-// Adds the pair `term` to the running (Kahan-compensated) pair sums.
-template <bool KAHAN>
-__device__ __forceinline__ void accumulate2(u64 &sum, u64 &comp, u64 term) {
-  if (KAHAN) {
-    const u64 y = sub2(term, comp);
-    const u64 t = add2(sum, y);
-    comp = sub2(sub2(t, sum), y);
-    sum = t;
-  } else {
-    sum = add2(sum, term);
-  }
-}
-
-// Squared distances of the two targets (tx2 = {txa, txb}, ty, tz) to the
-// record's binary32 centre of mass, with the fixed rounding of the opening
-// test: d2 = fma(dx, dx, fma(dz, dz, dy*dy)); the (dy, dz) part is shared.
-__device__ __forceinline__ void dist2(u64 tx2, float ty, float tz, u64 q0, u64 q1, float &d2a,
-                                      float &d2b, u64 &dx2, float &dy, float &dz) {
-  float py, pz;
-  upk(q1, py, pz);
-  dx2 = sub2(tx2, q0);
-  dy = __fsub_rn(ty, py);
-  dz = __fsub_rn(tz, pz);
-  const float h = __fmaf_rn(dz, dz, __fmul_rn(dy, dy));
-  upk(fma2(dx2, dx2, pk(h, h)), d2a, d2b);
-}
-
 // Interaction pair of an accepted node with the quadrupole term:
 // rinv (M + (d^T Q d / 2) rinv^4), i.e. M/d + (1/2) d^T Q d / d^5.
 __device__ __forceinline__ u64 quad_term2(const WalkQuad *qr, u64 mm, u64 rr, u64 dx2, float dy,
@@ -427,246 +343,6 @@ cudaError_t go_scalar(cudaStream_t s, int nb, const WalkRec *rec, const double4_
   return cudaGetLastError();
 }
 
-// ---- learned correction: the MLP on the tensor cores inside the walk --------
-// At a step where any of the warp's 64 targets accepts an internal node, the
-// warp evaluates y = MLP(x) for all 64 rows (row 2*lane+i = the lane's target
-// i; rows of targets that do not accept are computed and ignored) with
-// mma.sync m16n8k16 bf16 -> FP32: X[64x16] W1[16x64], H1[64x64] W2[64x64],
-// H2[64x64] W3[64x8].  Activations pass through per-warp shared memory as
-// bf16; weights are staged once per CTA.  The accepted term becomes
-// (M/d)(1 + s^2 y).  (The warp-synchronous mma.sync form is used because the
-// network runs per warp step inside the walk; a CTA-wide tcgen05 MMA would
-// have to gather rows across warps that walk different nodes.)
-constexpr int kLearnWarps = 8;
-struct LearnSmem {
-  MlpDev w;
-  uint16_t x[kLearnWarps][64 * 16];
-  uint16_t h[kLearnWarps][64 * 64];
-  float y[kLearnWarps][64];
-};
-
-__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-__device__ __forceinline__ float tanh_approx(float x) {
-  float r;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float gelu_t(float a) {
-  return 0.5f * a * (1.0f + tanh_approx(0.7978845608028654f * (a + 0.044715f * a * a * a)));
-}
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// A fragment (16 rows from m0, 16 k from k0) of a row-major bf16 matrix with
-// row stride ld (elements).
-__device__ __forceinline__ void load_a(uint32_t a[4], const uint16_t *M, int ld, int m0, int k0,
-                                       int gid, int tig) {
-  const uint16_t *r0 = M + (m0 + gid) * ld + k0 + 2 * tig;
-  const uint16_t *r1 = r0 + 8 * ld;
-  a[0] = *reinterpret_cast<const uint32_t *>(r0);
-  a[1] = *reinterpret_cast<const uint32_t *>(r1);
-  a[2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-  a[3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-}
-
-// y for the warp's 64 rows of X (written to y[64]).
-__device__ void mlp_warp(const MlpDev &W, uint16_t *X, uint16_t *H, float *Y, int lane) {
-  const int gid = lane >> 2, tig = lane & 3;
-  // layer 1 (K = 16): H = gelu(X W1 + b1)
-  for (int mt = 0; mt < 4; ++mt) {
-    uint32_t a[4];
-    load_a(a, X, 16, mt * 16, 0, gid, tig);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      const uint16_t *b = W.w1t + (nt * 8 + gid) * 16 + 2 * tig;
-      mma_bf16(c, a, *reinterpret_cast<const uint32_t *>(b),
-               *reinterpret_cast<const uint32_t *>(b + 8));
-      const int col = nt * 8 + 2 * tig;
-      const float b0 = W.b1[col], b1 = W.b1[col + 1];
-      *reinterpret_cast<uint32_t *>(H + (mt * 16 + gid) * 64 + col) =
-          bf16x2(gelu_t(c[0] + b0), gelu_t(c[1] + b1));
-      *reinterpret_cast<uint32_t *>(H + (mt * 16 + gid + 8) * 64 + col) =
-          bf16x2(gelu_t(c[2] + b0), gelu_t(c[3] + b1));
-    }
-  }
-  __syncwarp();
-  // layer 2 (K = 64), rows of one m-tile at a time, in place
-  for (int mt = 0; mt < 4; ++mt) {
-    uint32_t a[4][4];
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) load_a(a[kt], H, 64, mt * 16, kt * 16, gid, tig);
-    __syncwarp();
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      const uint16_t *b = W.w2t + (nt * 8 + gid) * 64 + 2 * tig;
-#pragma unroll
-      for (int kt = 0; kt < 4; ++kt)
-        mma_bf16(c, a[kt], *reinterpret_cast<const uint32_t *>(b + kt * 16),
-                 *reinterpret_cast<const uint32_t *>(b + kt * 16 + 8));
-      const int col = nt * 8 + 2 * tig;
-      const float b0 = W.b2[col], b1 = W.b2[col + 1];
-      *reinterpret_cast<uint32_t *>(H + (mt * 16 + gid) * 64 + col) =
-          bf16x2(gelu_t(c[0] + b0), gelu_t(c[1] + b1));
-      *reinterpret_cast<uint32_t *>(H + (mt * 16 + gid + 8) * 64 + col) =
-          bf16x2(gelu_t(c[2] + b0), gelu_t(c[3] + b1));
-    }
-    __syncwarp();
-  }
-  // layer 3 (N = 1, padded to 8): y = H2 W3 + b3
-  for (int mt = 0; mt < 4; ++mt) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    const uint16_t *b = W.w3t + gid * 64 + 2 * tig;
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-      uint32_t a[4];
-      load_a(a, H, 64, mt * 16, kt * 16, gid, tig);
-      mma_bf16(c, a, *reinterpret_cast<const uint32_t *>(b + kt * 16),
-               *reinterpret_cast<const uint32_t *>(b + kt * 16 + 8));
-    }
-    if (tig == 0) {  // column 0 of the output tile
-      Y[mt * 16 + gid] = c[0] + W.b3;
-      Y[mt * 16 + gid + 8] = c[2] + W.b3;
-    }
-  }
-  __syncwarp();
-}
-
-// Features of one (target, node) pair in binary32 (see bh_learn.cu), written
-// as one bf16 row of 16 (10 used).
-__device__ __forceinline__ void feature_row(uint16_t *row, float dx, float dy, float dz, float r,
-                                            float l, float dl, float inv_ml2, float qf,
-                                            const WalkQuad &q) {
-  const float ux = dx * r, uy = dy * r, uz = dz * r;
-  const float s = l * r;
-  const float quu = 2.0f * (ux * (q.hxx * ux + q.qxy * uy + q.qxz * uz) +
-                            uy * (q.hyy * uy + q.qyz * uz)) + 2.0f * q.hzz * uz * uz;
-  const float f7 = quu * inv_ml2;
-  uint32_t *w = reinterpret_cast<uint32_t *>(row);
-  w[0] = bf16x2(ux, uy);
-  w[1] = bf16x2(uz, s);
-  w[2] = bf16x2(s * s, s * s * s);
-  w[3] = bf16x2(dl, f7);
-  w[4] = bf16x2(qf * inv_ml2, s * s * f7);
-  w[5] = 0u;
-  w[6] = 0u;
-  w[7] = 0u;
-}
-
-template <bool KAHAN>
-__global__ void __launch_bounds__(kLearnWarps * 32)
-    k_walk_learned(unsigned nunits, const WalkRec *__restrict__ rec,
-                   const WalkQuad *__restrict__ qrec, const float2 *__restrict__ aux,
-                   const int4 *__restrict__ blk, const int *__restrict__ orig,
-                   const int4 *__restrict__ fld, const double *__restrict__ invL, double G,
-                   const MlpDev *__restrict__ mlp, float *__restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  LearnSmem &S = *reinterpret_cast<LearnSmem *>(smem_raw);
-  {
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(mlp);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(&S.w);
-    for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 4); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned u = blockIdx.x * kLearnWarps + wid;
-  if (u >= nunits) return;  // whole warps only, after the CTA-wide staging
-  uint16_t *X = S.x[wid];
-  uint16_t *H = S.h[wid];
-  float *Y = S.y[wid];
-  const unsigned p = u >> 3;
-  const int4 F = fld[p];
-  const unsigned n_nodes = (unsigned)F.y;
-  const int ma = (int)((u & 7) << 6) | (lane << 1);
-  const int4 B = blk[p];
-  const int cx = (int)compact3(ma), cy = (int)compact3(ma >> 1), cz = (int)compact3(ma >> 2);
-  const float hh = pow2f(-(B.x + 3 + 1));
-  const float txa = __fmul_rn((float)(2 * (8 * B.y + cx) + 1), hh);
-  const float txb = __fmul_rn((float)(2 * (8 * B.y + cx) + 3), hh);
-  const float ty = __fmul_rn((float)(2 * (8 * B.z + cy) + 1), hh);
-  const float tz = __fmul_rn((float)(2 * (8 * B.w + cz) + 1), hh);
-  const u64 tx2 = pk(txa, txb);
-  u64 sum = 0ull, comp = 0ull;
-  unsigned next_a = (unsigned)F.x, next_b = (unsigned)F.x;
-  unsigned node = (unsigned)F.x;
-  while (node < n_nodes) {
-    u64 q0, q1, q2, q3;
-    load_rec(rec + node, q0, q1, q2, q3);
-    float s2, skf;
-    upk(q3, s2, skf);
-    const unsigned skip = __float_as_uint(skf);
-    float d2a, d2b, dy, dz;
-    u64 dx2;
-    dist2(tx2, ty, tz, q0, q1, d2a, d2b, dx2, dy, dz);
-    const bool mine_a = next_a == node, mine_b = next_b == node;
-    const bool take_a = mine_a && d2a > s2;
-    const bool take_b = mine_b && d2b > s2;
-    float ra = rsqrt_approx(d2a), rb = rsqrt_approx(d2b);
-    ra = take_a ? ra : 0.0f;
-    rb = take_b ? rb : 0.0f;
-    u64 fac = pk(1.0f, 1.0f);  // 1 + s^2 y
-    if (__any_sync(kFull, take_a || take_b) && s2 > 0.0f) {
-      const float2 lv = aux[node];          // node side, delta
-      const WalkQuad q = qrec[node];
-      float mf, mf2;
-      upk(q2, mf, mf2);
-      const float inv_ml2 = mf > 0.0f ? 1.0f / (mf * lv.x * lv.x) : 1.0f;
-      const float qf = sqrtf(4.0f * (q.hxx * q.hxx + q.hyy * q.hyy + q.hzz * q.hzz) +
-                             2.0f * (q.qxy * q.qxy + q.qxz * q.qxz + q.qyz * q.qyz));
-      float dxa, dxb;
-      upk(dx2, dxa, dxb);
-      feature_row(X + (2 * lane) * 16, dxa, dy, dz, ra, lv.x, lv.y / lv.x, inv_ml2, qf, q);
-      feature_row(X + (2 * lane + 1) * 16, dxb, dy, dz, rb, lv.x, lv.y / lv.x, inv_ml2, qf, q);
-      __syncwarp();
-      mlp_warp(S.w, X, H, Y, lane);
-      const float sa = lv.x * ra, sb = lv.x * rb;
-      fac = pk(1.0f + sa * sa * Y[2 * lane], 1.0f + sb * sb * Y[2 * lane + 1]);
-    }
-    accumulate2<KAHAN>(sum, comp, mul2(mul2(q2, pk(ra, rb)), fac));
-    if (skip == node + 9u) {  // bottom node: its 8 cells in one step (monopole)
-      const bool open_a = mine_a && !take_a, open_b = mine_b && !take_b;
-      if (__any_sync(kFull, open_a || open_b)) {
-#pragma unroll 2
-        for (unsigned c = node + 1; c < node + 9u; ++c) {
-          u64 c0, c1, c2, c3;
-          load_rec(rec + c, c0, c1, c2, c3);
-          float e2a, e2b, ey, ez;
-          u64 ex2;
-          dist2(tx2, ty, tz, c0, c1, e2a, e2b, ex2, ey, ez);
-          float sa = rsqrt_approx(e2a), sb = rsqrt_approx(e2b);
-          sa = (open_a && e2a > 0.0f) ? sa : 0.0f;
-          sb = (open_b && e2b > 0.0f) ? sb : 0.0f;
-          accumulate2<KAHAN>(sum, comp, mul2(c2, pk(sa, sb)));
-        }
-      }
-      next_a = max(next_a, skip);
-      next_b = max(next_b, skip);
-    } else {
-      const unsigned n1 = node + 1;
-      next_a = max(next_a, take_a ? skip : n1);
-      next_b = max(next_b, take_b ? skip : n1);
-    }
-    node = __reduce_min_sync(kFull, min(next_a, next_b));
-  }
-  const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx;
-  if (KAHAN) sum = sub2(sum, comp);
-  float sa, sb;
-  upk(sum, sa, sb);
-  const float scale = (float)(-G * invL[F.w]);
-  out[cell] = __fmul_rn(sa, scale);
-  out[cell + 1] = __fmul_rn(sb, scale);
-}
-
 // Picks the kernel instance for the options.  The counting walk takes the
 // same decisions as every walk of the same criterion (the opening test does
 // not depend on precision, summation or the quadrupole term).
@@ -718,34 +394,6 @@ cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const Wal
   if (opt.quadrupole)
     return launch_walk_q<true>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
   return launch_walk_q<false>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
-}
-
-cudaError_t launch_walk_learned(cudaStream_t s, bh_ctx *ctx, double G, void *out) {
-  const Tree &t = ctx->tree;
-  const unsigned nunits = (unsigned)t.nb * 8u;
-  const int smem = (int)sizeof(LearnSmem);
-  FieldArgs fa;
-  fa.fld = t.d_fld;
-  fa.invL = t.d_invL;
-  cudaError_t e;
-  const bool kahan = ctx->opt.kahan != 0;
-  if (kahan)
-    e = cudaFuncSetAttribute(k_walk_learned<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-  else
-    e = cudaFuncSetAttribute(k_walk_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-  if (e != cudaSuccess) return e;
-  const unsigned grid = (nunits + kLearnWarps - 1) / kLearnWarps;
-  if (kahan)
-    k_walk_learned<true><<<grid, kLearnWarps * 32, smem, s>>>(
-        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, G, ctx->d_mlp,
-        (float *)out);
-  else
-    k_walk_learned<false><<<grid, kLearnWarps * 32, smem, s>>>(
-        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, G, ctx->d_mlp,
-        (float *)out);
-  return cudaGetLastError();
 }
 
 }  // namespace bhg

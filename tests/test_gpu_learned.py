@@ -11,8 +11,8 @@ Bars:
     (learned walk minus monopole walk) plus 1e-5 of the potential -- the
     tensor-core path rounds the features and the hidden activations to bf16
     (8 significant bits, relative 2^-9 each, through two 64-wide layers) and
-    uses the hardware tanh approximation, so each node's correction carries
-    about 1 % error; corrections of different nodes can cancel in a cell, so
+    takes the GELU's tanh from the SFU's bf16 approximation, so each node's
+    correction carries about 1 % error; corrections of different nodes can cancel in a cell, so
     the bound scales with their size, not with a cell's net correction;
   * what the trained network gains: smaller max error against the direct sum
     than the plain walk at the same theta, on a field it was not trained on.
