@@ -185,24 +185,46 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None):
     ref, ni, nt = tree.walk(theta, targets=tg, quad=quad)
     t_walk = time.perf_counter() - t0
     t_step = t_build + t_walk * (n / k)
+    t0 = time.perf_counter()
+    tree.walk(theta, targets=probe, quad=quad, threads=1)
+    per1 = (time.perf_counter() - t0) / len(probe)
     out = {"value": n / t_step, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
+           "value_1core": n / (t_build + per1 * n),
            "sample": f"tree+FP64 moments of all {n} cells; per-cell walk of {k} random cells "
                      f"(seed 1234, {'quadrupole' if quad else 'monopole'}, theta {theta}) "
-                     f"extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s"}
+                     f"extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s; "
+                     f"value_1core: the walk of {len(probe)} cells on one thread"}
     if phi_gpu is not None:
-        m = min(k, 2000)
-        d = tree.direct(targets=tg[:m])
+        dt = direct_targets(w, rng)
+        t0 = time.perf_counter()
+        d = tree.direct(targets=dt)
+        t_direct = time.perf_counter() - t0
+        wd = tree.walk(theta, targets=dt, quad=quad)[0]
         out["accuracy"] = {
             "max_rel_vs_oracle_walk": float(np.max(np.abs(phi_gpu[tg] / ref - 1.0))),
-            "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[tg[:m]] / d - 1.0))),
-            "oracle_walk_max_rel_vs_direct": float(np.max(np.abs(ref[:m] / d - 1.0))),
-            "cells_compared": int(k), "cells_vs_direct": int(m)}
+            "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[dt] / d - 1.0))),
+            "oracle_walk_max_rel_vs_direct": float(np.max(np.abs(wd / d - 1.0))),
+            "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
+            "direct_sample": "2,000 random cells (seed 1234) + every cell of the 8 densest "
+                             "blocks",
+            "direct_cells_per_s": len(dt) / t_direct}
         if plain is not None:
             phi_plain, plain_theta = plain
             out["accuracy"]["plain_max_rel_vs_direct"] = float(
-                np.max(np.abs(phi_plain[tg[:m]] / d - 1.0)))
+                np.max(np.abs(phi_plain[dt] / d - 1.0)))
             out["accuracy"]["plain_theta"] = plain_theta
     return out
+
+
+def direct_targets(w, rng, nrandom=2000, ndense=8):
+    """Cells compared with the direct sum: a random sample plus every cell of
+    the densest blocks (where the error of the walk tends to peak)."""
+    n = w.ncells
+    rnd = rng.choice(n, min(n, nrandom), replace=False)
+    mean = w.density.reshape(-1, 512).mean(axis=1)
+    dense = np.argsort(-mean, kind="stable")[:ndense]
+    cells = (dense[:, None] * 512 + np.arange(512)[None, :]).reshape(-1)
+    return np.unique(np.concatenate([rnd, cells]))
 
 
 def reference_arm(args):
@@ -433,18 +455,19 @@ def learned_oracle_leg(w, theta, wts, plain_theta, phi, cpu_seconds):
     t0 = time.perf_counter()
     ref = tree.walk_learned(theta, wts, targets=tg)
     t_walk = time.perf_counter() - t0
-    m = min(k, 2000)
-    d = tree.direct(targets=tg[:m])
+    dt = direct_targets(w, rng)
+    d = tree.direct(targets=dt)
 
     def rel(a):
-        return float(np.max(np.abs(a[tg[:m]] / d - 1.0)))
+        return float(np.max(np.abs(a[dt] / d - 1.0)))
     acc = {"learned_max_rel_vs_direct": rel(phi["learned"]),
            "plain_max_rel_vs_direct": rel(phi["plain"]),
            "plain_same_theta_max_rel_vs_direct": rel(phi["same"]),
            "learned_max_abs_vs_oracle_learned": float(np.max(np.abs(phi["learned"][tg] - ref))),
            "learned_max_rel_vs_oracle_learned": float(np.max(np.abs(phi["learned"][tg] / ref - 1))),
            "theta": theta, "plain_theta": plain_theta,
-           "cells_compared": int(k), "cells_vs_direct": int(m)}
+           "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
+           "direct_sample": "2,000 random cells + every cell of the 8 densest blocks"}
     return {"value": n / (t_build + t_walk * n / k), "unit": "cells/s",
             "cores": O.max_threads(), "kind": "oracle",
             "sample": f"tree+FP64 moments+quadrupoles of all {n} cells; learned walk (FP64 MLP) "
@@ -580,6 +603,19 @@ def learned_arm(args):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def build_roofline(ncells, nnodes, quad, build_ms):
+    """The build against HBM: algorithmic bytes = the density read (4 B per
+    cell) + per node the walk record, FP64 moments, {l, delta} and level
+    (32 + 32 + 8 + 1 B) + a 32-B quadrupole record per internal node."""
+    n_int = nnodes - ncells
+    traffic = 4 * ncells + 73 * nnodes + (32 * n_int if quad else 0)
+    peak = measured_peak("hbm_gbs")
+    gbs = traffic / (build_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "bh_build (keys, topology, FP64 moments)",
+            "algorithmic_bytes": traffic, "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "note": "limited by FP64 arithmetic, not by HBM"}
 
 
 def measured_peak(key):
@@ -733,6 +769,8 @@ def main():
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms))},
+            "walk_only_value": n / walk_s,
+            "build_roofline": build_roofline(n, nn, quad, float(np.mean(build_ms))),
             "walk_work": {"interactions": n_int, "cell_interactions": n_cell, "tests": n_test,
                           "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n},
             "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",

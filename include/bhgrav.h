@@ -83,7 +83,11 @@ typedef struct {
                      network set by bh_set_mlp and evaluated on the tensor
                      cores (not in the paper; see bh_learn_pairs).  Needs the
                      binary32 per-cell walk; excludes the quadrupole term. */
-  int reserved[3];
+  int timing;     /* 0 (default).  1: bh_build, bh_build_batch, bh_update_density
+                     and bh_potential bracket their device work with CUDA events
+                     on the context's stream, for bh_stats (not while the
+                     stream is being captured into a graph). */
+  int reserved[2];
 } bh_options;
 
 /* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation,
@@ -277,6 +281,31 @@ bh_status bh_mlp_adam(const float *grad, float *w, float *m, float *v, int step,
  * stay FP32.  bh_get_mlp returns the weights in use (bf16 values widened). */
 bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host);
 bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host);
+
+/* ---- statistics (not in the paper) ---------------------------------------- */
+typedef struct {
+  int64_t n_cells;           /* leaf cells of the current tree, all fields (0: no tree) */
+  int64_t n_nodes;           /* nodes: cells + internal nodes, (N - 1)/7 of them per field */
+  int32_t n_blocks;          /* leaf blocks */
+  int32_t n_fields;          /* fields of the last bh_build (1) or bh_build_batch */
+  int32_t max_level;         /* deepest cell level (block level + 3) */
+  int32_t built;             /* 1 once a tree is built and validated */
+  double last_theta;         /* theta of the last bh_potential (0: none yet) */
+  double build_ms;           /* device time of the last bh_build / bh_build_batch /
+                                bh_update_density; -1 unless the timing option is on */
+  double potential_ms;       /* device time of the last bh_potential (opening radii +
+                                walk); -1 unless the timing option is on */
+  int64_t interactions;      /* totals over all cells of the last bh_walk_counts call: */
+  int64_t tests;             /*   interactions, opening tests of internal nodes and */
+  int64_t cell_interactions; /*   interactions with single cells; -1 if none yet */
+  int64_t device_bytes;      /* device memory held by the context's tree buffers */
+} bh_stats_t;
+
+/* Sizes of the current tree, the device times of the last build and
+ * potential (timing option) and the work totals of the last bh_walk_counts.
+ * Waits for the recorded events and copies 24 bytes from the device, so it
+ * synchronises with the work it reports on.  BH_ERR_ARG on null pointers. */
+bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out);
 
 /* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
 const char *bh_last_error(const bh_ctx *ctx);

@@ -25,14 +25,25 @@ EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_update_density", "bh_sync_status", "bh_autotune", "bh_solve_graph",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
-            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_last_error",
-            "bh_destroy")
+            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_stats",
+            "bh_last_error", "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("criterion", ctypes.c_int),
                 ("kahan", ctypes.c_int), ("quadrupole", ctypes.c_int),
-                ("learned", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("learned", ctypes.c_int), ("timing", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
+
+
+class bh_stats_t(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("n_blocks", ctypes.c_int32), ("n_fields", ctypes.c_int32),
+                ("max_level", ctypes.c_int32), ("built", ctypes.c_int32),
+                ("last_theta", ctypes.c_double), ("build_ms", ctypes.c_double),
+                ("potential_ms", ctypes.c_double), ("interactions", ctypes.c_int64),
+                ("tests", ctypes.c_int64), ("cell_interactions", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
 
 
 class BHError(RuntimeError):
@@ -81,6 +92,7 @@ def load(build_if_needed: bool = True):
         lib.bh_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, P]
         lib.bh_set_mlp.argtypes = [P, P]
         lib.bh_get_mlp.argtypes = [P, P]
+        lib.bh_stats.argtypes = [P, ctypes.POINTER(bh_stats_t)]
         lib.bh_last_error.argtypes = [P]
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
@@ -90,7 +102,7 @@ def load(build_if_needed: bool = True):
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
-                     "bh_set_mlp", "bh_get_mlp"):
+                     "bh_set_mlp", "bh_get_mlp", "bh_stats"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -315,6 +327,14 @@ def bh_get_mlp(ctx) -> np.ndarray:
     return w
 
 
+def bh_stats(ctx) -> dict:
+    """Tree sizes, device times of the last build / potential (timing option,
+    else -1) and work totals of the last bh_walk_counts (else -1)."""
+    out = bh_stats_t()
+    _check(ctx, load().bh_stats(ctx, ctypes.byref(out)), "bh_stats")
+    return {name: getattr(out, name) for name, _ in bh_stats_t._fields_}
+
+
 def bh_last_error(ctx) -> str:
     return load().bh_last_error(ctx).decode()
 
@@ -334,12 +354,13 @@ class Solver:
     """
 
     def __init__(self, precision=BH_PREC_F32, criterion=BH_CRIT_PER_CELL, kahan=True,
-                 quadrupole=False, learned=False, device=0, stream=None):
+                 quadrupole=False, learned=False, timing=False, device=0, stream=None):
         import torch
         o = bh_default_options()
         o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
         o.quadrupole = int(bool(quadrupole))
         o.learned = int(bool(learned))
+        o.timing = int(bool(timing))
         self.options = o
         self.device = torch.device("cuda", device)
         if stream is None:
@@ -434,6 +455,9 @@ class Solver:
 
     def set_mlp(self, w):
         bh_set_mlp(self._ctx, w)
+
+    def stats(self) -> dict:
+        return bh_stats(self._ctx)
 
     def get_mlp(self):
         return bh_get_mlp(self._ctx)

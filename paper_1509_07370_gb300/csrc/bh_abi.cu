@@ -170,6 +170,52 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64)
   return BH_OK;
 }
 
+// Records event i of the timing option on the context's stream; not while
+// the stream is being captured into a graph (replays are not timed).
+bool timing_mark(bh_ctx *ctx, int i) {
+  if (!ctx->opt.timing) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!ctx->ev[i] && cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ev[i] = nullptr;
+    return false;
+  }
+  if (cudaEventRecord(ctx->ev[i], ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+// Totals of the per-cell counts of a counting walk: out[0] += sum n_int,
+// out[1] += sum n_test, out[2] += sum n_cell (if given).
+__global__ void k_sum_counts(int64_t n, const int32_t *__restrict__ a,
+                             const int32_t *__restrict__ b, const int32_t *__restrict__ c,
+                             unsigned long long *out) {
+  unsigned long long sa = 0, sb = 0, sc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    sa += (unsigned)a[i];
+    sb += (unsigned)b[i];
+    if (c) sc += (unsigned)c[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_down_sync(0xffffffffu, sa, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+    sc += __shfl_down_sync(0xffffffffu, sc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, sa);
+    atomicAdd(out + 1, sb);
+    if (c) atomicAdd(out + 2, sc);
+  }
+}
+
 // Tree and moments of nfields meshes (one field = bh_build).  Synchronises
 // once to report geometry and density errors.
 bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
@@ -227,6 +273,8 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   t.h_L = L;
   cudaStream_t s = ctx->stream;
   const bhg::FieldArgs fa = field_args(t);
+  ctx->build_timed = false;
+  const bool timed = timing_mark(ctx, 0);
   BH_CUDA(cudaMemsetAsync(t.d_flags, 0, 4 * sizeof(unsigned), s));
   BH_CUDA(cudaMemcpyAsync(t.d_level, level, nb * sizeof(int), cudaMemcpyHostToDevice, s));
   BH_CUDA(cudaMemcpyAsync(t.d_ijk, ijk, 3 * (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -244,6 +292,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
                                 t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig));
   if ((st = enqueue_moments(ctx, density, density_is_fp64)) != BH_OK) return st;
+  ctx->build_timed = timed && timing_mark(ctx, 1);
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
   const unsigned e = t.h_flags[0];
@@ -284,7 +333,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if ((o.precision != BH_PREC_F32 && o.precision != BH_PREC_F64) ||
       (o.criterion != BH_CRIT_PER_CELL && o.criterion != BH_CRIT_WARP_VOTE) ||
       (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1) ||
-      (o.learned != 0 && o.learned != 1))
+      (o.learned != 0 && o.learned != 1) || (o.timing != 0 && o.timing != 1))
     return BH_ERR_ARG;
   // the learned walk is the binary32 per-cell walk, with the network in place
   // of the quadrupole term
@@ -345,11 +394,15 @@ bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp6
     return fail(ctx, BH_ERR_ARG, "bh_update_density: bad density");
   bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
+  ctx->build_timed = false;
+  const bool timed = timing_mark(ctx, 0);
   BH_CUDA(cudaMemsetAsync(ctx->tree.d_flags, 0, sizeof(unsigned), ctx->stream));
   // the records are rewritten (s2 included, and delta changes with the
   // density): the next walk must prepare s2 again
   ctx->tree.s2_inv_theta = -1.0f;
-  return enqueue_moments(ctx, density, density_is_fp64);
+  st = enqueue_moments(ctx, density, density_is_fp64);
+  ctx->build_timed = st == BH_OK && timed && timing_mark(ctx, 1);
+  return st;
 }
 
 bh_status bh_sync_status(bh_ctx *ctx) {
@@ -408,17 +461,22 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
   if (!out) return fail(ctx, BH_ERR_ARG, "bh_potential: out is null");
   if (!std::isfinite(G)) return fail(ctx, BH_ERR_ARG, "bh_potential: G must be finite");
-  bh_status st = prepare(ctx, theta);
+  if (ctx->opt.learned && !ctx->d_mlp)
+    return fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
+  ctx->potential_timed = false;
+  bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
+  const bool timed = timing_mark(ctx, 2);
+  if ((st = prepare(ctx, theta)) != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  if (ctx->opt.learned) {
-    if (!ctx->d_mlp) return fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
+  if (ctx->opt.learned)
     BH_CUDA(bhg::launch_walk_learned(ctx->stream, ctx, G, out));
-    return BH_OK;
-  }
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
-                           t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr, nullptr,
-                           t.wpc));
+  else
+    BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
+                             t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr,
+                             nullptr, t.wpc));
+  ctx->potential_timed = timed && timing_mark(ctx, 3);
+  ctx->last_theta = theta;
   return BH_OK;
 }
 
@@ -434,6 +492,15 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
                            t.d_blk, t.d_orig, field_args(t), 0.0, nullptr, n_int, n_test, n_cell,
                            t.wpc));
+  // totals for bh_stats
+  ctx->counts_valid = false;
+  if (!ctx->d_counts) BH_CUDA(cudaMalloc(&ctx->d_counts, 3 * sizeof(unsigned long long)));
+  BH_CUDA(cudaMemsetAsync(ctx->d_counts, 0, 3 * sizeof(unsigned long long), ctx->stream));
+  const int64_t ncell = (int64_t)t.nb * bhg::kCellsPerBlock;
+  k_sum_counts<<<4 * 152, 256, 0, ctx->stream>>>(ncell, n_int, n_test, n_cell, ctx->d_counts);
+  BH_CUDA(cudaGetLastError());
+  ctx->counts_valid = true;
+  ctx->counts_have_cells = n_cell != nullptr;
   return BH_OK;
 }
 
@@ -666,6 +733,56 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
   return BH_OK;
 }
 
+bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
+  if (!ctx || !out) return BH_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  const bhg::Tree &t = ctx->tree;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return BH_ERR_CUDA;
+  }
+  out->built = t.built ? 1 : 0;
+  if (t.built) {
+    out->n_cells = (int64_t)t.nb * bhg::kCellsPerBlock;
+    out->n_nodes = t.n_nodes;
+    out->n_blocks = t.nb;
+    out->n_fields = t.nfields;
+    out->max_level = t.max_block_level + 3;
+  }
+  out->last_theta = ctx->last_theta;
+  out->build_ms = out->potential_ms = -1.0;
+  float ms = 0.0f;
+  if (ctx->build_timed && cudaEventSynchronize(ctx->ev[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess)
+    out->build_ms = ms;
+  if (ctx->potential_timed && cudaEventSynchronize(ctx->ev[3]) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess)
+    out->potential_ms = ms;
+  cudaGetLastError();
+  out->interactions = out->tests = out->cell_interactions = -1;
+  if (ctx->counts_valid) {
+    unsigned long long c[3];
+    if (cudaMemcpyAsync(c, ctx->d_counts, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return BH_ERR_CUDA;
+    }
+    out->interactions = (int64_t)c[0];
+    out->tests = (int64_t)c[1];
+    out->cell_interactions = ctx->counts_have_cells ? (int64_t)c[2] : -1;
+  }
+  int64_t b = t.nb_cap * (int64_t)(4 + 12 + 8 + 8 + 4 + 4 + 4 + 4 + 16 + 4 + 4 + 4 + 16);
+  b += t.node_cap * (int64_t)(sizeof(double4_32a) + sizeof(bhg::WalkRec) + sizeof(float2) + 1);
+  b += t.quad_cap * (int64_t)sizeof(bhg::WalkQuad) + (t.d_q64 ? t.quad_cap * 48 : 0);
+  b += t.nf_cap * (int64_t)(sizeof(int) + 2 * sizeof(double)) + (t.nf_cap ? 4 : 0);
+  b += t.stage_in_bytes + t.stage_out_bytes + 4 * sizeof(unsigned);
+  if (ctx->d_mlp) b += sizeof(bhg::MlpDev);
+  if (ctx->d_counts) b += 3 * sizeof(unsigned long long);
+  out->device_bytes = b;
+  return BH_OK;
+}
+
 const char *bh_last_error(const bh_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
 void bh_destroy(bh_ctx *ctx) {
@@ -680,6 +797,9 @@ void bh_destroy(bh_ctx *ctx) {
   release(ctx->tree.d_stage_out);
   release(ctx->tree.d_flags);
   release(ctx->d_mlp);
+  release(ctx->d_counts);
+  for (cudaEvent_t &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
   delete ctx;
 }

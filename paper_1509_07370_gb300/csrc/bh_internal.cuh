@@ -226,6 +226,14 @@ struct bh_ctx {
   cudaStream_t stream = nullptr;
   bhg::Tree tree;
   bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
+  // statistics (bh_stats): events of the timing option (build start/end,
+  // potential start/end), theta of the last potential, device totals of the
+  // last bh_walk_counts
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool build_timed = false, potential_timed = false;
+  double last_theta = 0.0;
+  unsigned long long *d_counts = nullptr;
+  bool counts_valid = false, counts_have_cells = false;
   char err[512] = {0};
 };
 

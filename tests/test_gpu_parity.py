@@ -344,3 +344,29 @@ def test_errors_reported():
         s.potential(0.5, G=float("inf"))
     assert e.value.status == B.BH_ERR_ARG
     assert np.all(np.isfinite(s.potential(0.5).cpu().numpy()))   # still usable
+
+
+def test_stats_sizes_timings_and_work_totals():
+    """bh_stats: tree sizes equal bh_tree_size, device times with the timing
+    option are positive (and -1 without it), the work totals equal the sums
+    of bh_walk_counts' per-cell arrays."""
+    mesh, rho = _mesh("refined_twice")
+    s = B.Solver(timing=True)
+    assert s.stats()["built"] == 0 and s.stats()["build_ms"] == -1.0
+    _build(s, mesh, rho)
+    out = s.potential(0.5)
+    torch.cuda.synchronize()
+    st = s.stats()
+    nc, nn, ml = s.tree_size()
+    assert (st["n_cells"], st["n_nodes"], st["max_level"]) == (nc, nn, ml)
+    assert st["n_blocks"] == len(mesh.level) and st["n_fields"] == 1 and st["built"] == 1
+    assert st["build_ms"] > 0.0 and st["potential_ms"] > 0.0 and st["last_theta"] == 0.5
+    assert st["interactions"] == -1 and st["device_bytes"] > 0
+    ni, nt, ncell = s.walk_counts(0.5, with_cells=True)
+    st = s.stats()
+    assert st["interactions"] == int(ni.sum(dtype=torch.int64))
+    assert st["tests"] == int(nt.sum(dtype=torch.int64))
+    assert st["cell_interactions"] == int(ncell.sum(dtype=torch.int64))
+    plain = _build(B.Solver(), mesh, rho)
+    plain.potential(0.5, out=out)
+    assert plain.stats()["build_ms"] == -1.0 and plain.stats()["potential_ms"] == -1.0
