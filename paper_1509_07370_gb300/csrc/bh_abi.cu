@@ -115,6 +115,7 @@ void free_fields(bhg::Tree &t) {
   release(t.d_fstart);
   release(t.d_invL);
   release(t.d_L);
+  release(t.d_mmax);
   t.nf_cap = 0;
 }
 
@@ -130,13 +131,11 @@ void drop_graph(bhg::Tree &t) {
 bh_status ensure_fields(bh_ctx *ctx, int nfields) {
   bhg::Tree &t = ctx->tree;
   if (t.nf_cap >= nfields) return BH_OK;
-  release(t.d_fstart);
-  release(t.d_invL);
-  release(t.d_L);
-  t.nf_cap = 0;
+  free_fields(t);
   BH_CUDA(cudaMalloc(&t.d_fstart, (size_t)(nfields + 1) * sizeof(int)));
   BH_CUDA(cudaMalloc(&t.d_invL, (size_t)nfields * sizeof(double)));
   BH_CUDA(cudaMalloc(&t.d_L, (size_t)nfields * sizeof(double)));
+  BH_CUDA(cudaMalloc(&t.d_mmax, (size_t)nfields * sizeof(unsigned long long)));
   t.nf_cap = nfields;
   return BH_OK;
 }
@@ -149,6 +148,7 @@ bhg::FieldArgs field_args(bhg::Tree &t) {
   fa.fld = t.d_fld;
   fa.invL = t.d_invL;
   fa.L = t.d_L;
+  fa.mmax = t.d_mmax;
   return fa;
 }
 
@@ -161,12 +161,16 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64)
   double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
   bhg::WalkQuad *qrec = (ctx->opt.quadrupole || ctx->opt.learned) ? t.d_qrec : nullptr;
   const bhg::FieldArgs fa = field_args(t);
+  // binary32 mass unit of every field (largest cell mass), then the moments
+  BH_CUDA(cudaMemsetAsync(t.d_mmax, 0, (size_t)t.nfields * sizeof(unsigned long long), s));
+  BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa));
   BH_CUDA(bhg::launch_blocks(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
                              density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl,
                              q64, qrec, t.d_flags));
   for (int lev = t.max_block_level - 1; lev >= 0; --lev)
     BH_CUDA(bhg::launch_top_moments(s, t.nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
-                                    t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags));
+                                    t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags,
+                                    fa));
   return BH_OK;
 }
 
@@ -229,6 +233,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   if (density_is_fp64 != 0 && density_is_fp64 != 1)
     return fail(ctx, BH_ERR_ARG, "%s: density_is_fp64 must be 0 or 1", who);
   std::vector<int> fstart(nfields + 1, 0);
+  std::vector<int64_t> fnode(nfields + 1, 0);
   std::vector<double> invL(nfields), L(nfields);
   int64_t nb64 = 0, n_nodes = 0, tops = 0;
   for (int f = 0; f < nfields; ++f) {
@@ -242,6 +247,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
       return fail(ctx, BH_ERR_GEOMETRY, "%s: %d blocks cannot tile a cube (need 1 + 7k)", who,
                   nbf);
     fstart[f] = (int)nb64;
+    fnode[f] = n_nodes;
     nb64 += nbf;
     tops += (nbf - 1) / 7;
     n_nodes += (int64_t)bhg::kNodesPerBlock * nbf + (nbf - 1) / 7;
@@ -254,6 +260,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
                 (long long)nb64);
   const int nb = (int)nb64;
   fstart[nfields] = nb;
+  fnode[nfields] = n_nodes;
   int max_level = 0;
   for (int b = 0; b < nb; ++b) {
     if (level[b] < 0 || level[b] > bhg::kMaxBlockLevel)
@@ -271,6 +278,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   t.n_nodes = n_nodes;
   t.max_block_level = max_level;
   t.h_L = L;
+  t.h_fnode = fnode;
   cudaStream_t s = ctx->stream;
   const bhg::FieldArgs fa = field_args(t);
   ctx->build_timed = false;
@@ -535,22 +543,25 @@ __global__ void k_export(int64_t n, const double4_32a *mom, const bhg::WalkRec *
 namespace {
 // Quadrupoles are stored for internal nodes only; cells (node side 0) get
 // zeros.  FP64 values if they were built (FP64 walk), else the binary32 ones.
-__global__ void k_export_quad(int64_t n, const double *q64, const bhg::WalkQuad *qrec,
-                              const float2 *aux, double *Q) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Nodes [i0, i1) of one field, whose binary32 mass unit is 2^e.
+__global__ void k_export_quad(int64_t i0, int64_t i1, const double *q64,
+                              const bhg::WalkQuad *qrec, const float2 *aux,
+                              const unsigned long long *mmax, int field, double *Q) {
+  const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= i1) return;
   const bool cell = aux[i].x == 0.0f;
   double v[6] = {0, 0, 0, 0, 0, 0};
   if (!cell && q64) {
     for (int a = 0; a < 6; ++a) v[a] = q64[6 * i + a];
-  } else if (!cell) {
+  } else if (!cell) {  // binary32 record in the field's mass unit 2^e
     const bhg::WalkQuad w = qrec[i];
-    v[0] = 2.0 * w.hxx;
-    v[1] = 2.0 * w.hyy;
-    v[2] = 2.0 * w.hzz;
-    v[3] = w.qxy;
-    v[4] = w.qxz;
-    v[5] = w.qyz;
+    const double u = bhg::pow2i(bhg::mass_exponent(mmax[field]));
+    v[0] = 2.0 * w.hxx * u;
+    v[1] = 2.0 * w.hyy * u;
+    v[2] = 2.0 * w.hzz * u;
+    v[3] = w.qxy * u;
+    v[4] = w.qxz * u;
+    v[5] = w.qyz * u;
   }
   for (int a = 0; a < 6; ++a) Q[6 * i + a] = v[a];
 }
@@ -581,10 +592,13 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
   bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
   const int threads = 256;
-  k_export_quad<<<(unsigned)((ctx->tree.n_nodes + threads - 1) / threads), threads, 0,
-                  ctx->stream>>>(ctx->tree.n_nodes, ctx->tree.d_q64, ctx->tree.d_qrec,
-                                 ctx->tree.d_aux, Q);
-  BH_CUDA(cudaGetLastError());
+  const bhg::Tree &t = ctx->tree;
+  for (int f = 0; f < t.nfields; ++f) {
+    const int64_t i0 = t.h_fnode[f], i1 = t.h_fnode[f + 1];
+    k_export_quad<<<(unsigned)((i1 - i0 + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        i0, i1, t.d_q64, t.d_qrec, t.d_aux, t.d_mmax, f, Q);
+    BH_CUDA(cudaGetLastError());
+  }
   return BH_OK;
 }
 

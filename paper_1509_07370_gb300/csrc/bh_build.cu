@@ -313,11 +313,12 @@ __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double
   return w;
 }
 
+// inv_unit = 2^-e of the field's binary32 mass unit (the record's mass).
 __device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int level,
                                                const Moment &r, double4_32a *mom, WalkRec *rec,
-                                               float2 *aux, uint8_t *lvl) {
+                                               float2 *aux, uint8_t *lvl, double inv_unit) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
-  rec[id] = make_rec(r.x, r.y, r.z, r.m, skip);
+  rec[id] = make_rec(r.x, r.y, r.z, r.m * inv_unit, skip);
   aux[id] = make_float2(pow2f(-level), __double2float_rn(r.delta));
   if (lvl) lvl[id] = (uint8_t)level;
 }
@@ -340,11 +341,11 @@ __device__ __forceinline__ void add_shifted(double Q[6], const double *Qc, doubl
 
 // Binary32 version, used when the walk is binary32: the quadrupole term is a
 // small correction rounded to binary32 anyway, and GB300 runs FP64 far slower
-// than FP32.  The shift s is formed in FP64 (a difference of nearby centres of
-// mass) and then rounded.
-__device__ __forceinline__ void add_shifted_f(float Q[6], const float *Qc, double m, double sx,
+// than FP32.  fm is the child's mass in the field's binary32 mass unit; the
+// shift s is formed in FP64 (a difference of nearby centres of mass) and
+// then rounded.
+__device__ __forceinline__ void add_shifted_f(float Q[6], const float *Qc, float fm, double sx,
                                               double sy, double sz) {
-  const float fm = __double2float_rn(m);
   const float x = __double2float_rn(sx), y = __double2float_rn(sy), z = __double2float_rn(sz);
   const float s2 = x * x + y * y + z * z;
   Q[0] += fm * (3.0f * x * x - s2);
@@ -379,18 +380,20 @@ __device__ __forceinline__ void load_quad_f(const WalkQuad &w, float Q[6]) {
   Q[5] = w.qyz;
 }
 
-// FP64 quadrupole and its binary32 walk record {Qxx/2 (twice), Qyy/2, Qzz/2,
-// Qxy, Qxz, Qyz, 0}: the halves fold the 1/2 of the quadrupole term.
+// FP64 quadrupole (physical) and its binary32 walk record {Qxx/2 (twice),
+// Qyy/2, Qzz/2, Qxy, Qxz, Qyz, 0} in the field's mass unit (inv_unit = 2^-e):
+// the halves fold the 1/2 of the quadrupole term.
 __device__ __forceinline__ void store_quad(int64_t id, const double Q[6], double *q64,
-                                           WalkQuad *qrec) {
+                                           WalkQuad *qrec, double inv_unit) {
   for (int a = 0; a < 6; ++a) q64[6 * id + a] = Q[a];
+  const double u = inv_unit;
   WalkQuad w;
-  w.hxx = w.hxx2 = __double2float_rn(0.5 * Q[0]);
-  w.hyy = __double2float_rn(0.5 * Q[1]);
-  w.hzz = __double2float_rn(0.5 * Q[2]);
-  w.qxy = __double2float_rn(Q[3]);
-  w.qxz = __double2float_rn(Q[4]);
-  w.qyz = __double2float_rn(Q[5]);
+  w.hxx = w.hxx2 = __double2float_rn(0.5 * Q[0] * u);
+  w.hyy = __double2float_rn(0.5 * Q[1] * u);
+  w.hzz = __double2float_rn(0.5 * Q[2] * u);
+  w.qxy = __double2float_rn(Q[3] * u);
+  w.qxz = __double2float_rn(Q[4] * u);
+  w.qyz = __double2float_rn(Q[5] * u);
   w.pad = 0.0f;
   qrec[id] = w;
 }
@@ -402,11 +405,13 @@ __global__ void __launch_bounds__(kBlockThreads)
     k_blocks(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
              const int *__restrict__ count, const int *__restrict__ prestart,
              const T *__restrict__ density, const double *__restrict__ Lf,
-             const int *__restrict__ fid, int64_t n_nodes,
+             const int *__restrict__ fid, const unsigned long long *__restrict__ mmax,
+             int64_t n_nodes,
              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec, float2 *__restrict__ aux,
              uint8_t *__restrict__ lvl, double *__restrict__ q64, WalkQuad *__restrict__ qrec,
              unsigned *flags) {
   __shared__ double cm[512], cxs[512], cys[512], czs[512];  // cells, local Morton order
+  __shared__ float cmu[512];                                // cell mass, binary32 unit
   __shared__ double gm[64], gx[64], gy[64], gz[64];         // level lb+2 nodes
   __shared__ double pm[8], px[8], py[8], pz[8];             // level lb+1 nodes
   __shared__ double gq[64][6], pq[8][6];                    // their quadrupoles (FP64)
@@ -424,7 +429,9 @@ __global__ void __launch_bounds__(kBlockThreads)
     return;
   }
   const int lc = lb + 3;
-  const double L = Lf[fid[orig[p]]];          // box side of this block's field
+  const int field = fid[orig[p]];
+  const double L = Lf[field];                  // box side of this block's field
+  const double inv_unit = pow2i(-mass_exponent(mmax[field]));  // binary32 mass unit
   const double hs = pow2d(-lc);               // cell side, box units
   const double h = __dmul_rn(L, hs);          // cell side, physical
   const double vol = __dmul_rn(__dmul_rn(h, h), h);
@@ -439,13 +446,15 @@ __global__ void __launch_bounds__(kBlockThreads)
     const double uy = __dmul_rn((double)(8 * B.z + cy) + 0.5, hs);
     const double uz = __dmul_rn((double)(8 * B.w + cz) + 0.5, hs);
     const double mass = __dmul_rn(r, vol);
+    const double mass_u = mass * inv_unit;
     cm[m] = mass;
+    cmu[m] = __double2float_rn(mass_u);
     cxs[m] = ux;
     cys[m] = uy;
     czs[m] = uz;
     const int64_t id = root + cell_offset(m);
     mom[id] = make_double4_32a(ux, uy, uz, mass);
-    rec[id] = make_rec(ux, uy, uz, mass, id + 1);
+    rec[id] = make_rec(ux, uy, uz, mass_u, id + 1);
     aux[id] = make_float2(0.0f, 0.0f);
     lvl[id] = (uint8_t)lc;
   }
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     gy[q] = r.y;
     gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -476,12 +485,12 @@ __global__ void __launch_bounds__(kBlockThreads)
         add_shifted(Q, nullptr, cm[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
       }
       for (int a = 0; a < 6; ++a) gq[q][a] = Q[a];
-      store_quad(id, Q, q64, qrec);
+      store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
         const int k = 8 * q + o;
-        add_shifted_f(Q, nullptr, cm[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
+        add_shifted_f(Q, nullptr, cmu[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
       }
       for (int a = 0; a < 6; ++a) gqf[q][a] = Q[a];
       store_quad_f(id, Q, qrec);
@@ -504,7 +513,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     py[c] = r.y;
     pz[c] = r.z;
     const int64_t id = root + 1 + 73 * c;
-    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl);
+    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -512,12 +521,13 @@ __global__ void __launch_bounds__(kBlockThreads)
         add_shifted(Q, gq[k], gm[k], gx[k] - r.x, gy[k] - r.y, gz[k] - r.z);
       }
       for (int a = 0; a < 6; ++a) pq[c][a] = Q[a];
-      store_quad(id, Q, q64, qrec);
+      store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
         const int k = 8 * c + o;
-        add_shifted_f(Q, gqf[k], gm[k], gx[k] - r.x, gy[k] - r.y, gz[k] - r.z);
+        add_shifted_f(Q, gqf[k], __double2float_rn(gm[k] * inv_unit), gx[k] - r.x, gy[k] - r.y,
+                      gz[k] - r.z);
       }
       for (int a = 0; a < 6; ++a) pqf[c][a] = Q[a];
       store_quad_f(id, Q, qrec);
@@ -533,15 +543,16 @@ __global__ void __launch_bounds__(kBlockThreads)
 #pragma unroll
     for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl);
+    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl, inv_unit);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) add_shifted(Q, pq[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
-      store_quad(root, Q, q64, qrec);
+      store_quad(root, Q, q64, qrec, inv_unit);
     } else if (quad32) {
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o)
-        add_shifted_f(Q, pqf[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
+        add_shifted_f(Q, pqf[o], __double2float_rn(pm[o] * inv_unit), px[o] - r.x, py[o] - r.y,
+                      pz[o] - r.z);
       store_quad_f(root, Q, qrec);
     }
   }
@@ -554,7 +565,9 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
                               const int *__restrict__ prestart, int64_t n_nodes,
                               double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
                               float2 *__restrict__ aux, double *__restrict__ q64,
-                              WalkQuad *__restrict__ qrec, unsigned *flags) {
+                              WalkQuad *__restrict__ qrec, unsigned *flags,
+                              const int4 *__restrict__ fld,
+                              const unsigned long long *__restrict__ mmax) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int cnt = count[p];
@@ -581,7 +594,8 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
   }
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
   const int64_t skip = rec[id].skip;
-  store_internal(id, skip, level, r, mom, rec, aux, nullptr);
+  const double inv_unit = pow2i(-mass_exponent(mmax[fld[p].w]));
+  store_internal(id, skip, level, r, mom, rec, aux, nullptr, inv_unit);
   if (q64) {
     double Q[6] = {0, 0, 0, 0, 0, 0};
     c = id + 1;
@@ -590,7 +604,7 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
       add_shifted(Q, q64 + 6 * c, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
       c = rec[c].skip;
     }
-    store_quad(id, Q, q64, qrec);
+    store_quad(id, Q, q64, qrec, inv_unit);
   } else if (qrec) {
     float Q[6] = {0, 0, 0, 0, 0, 0};
     c = id + 1;
@@ -598,11 +612,38 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
       const double4_32a ch = mom[c];
       float Qc[6];
       load_quad_f(qrec[c], Qc);
-      add_shifted_f(Q, Qc, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
+      add_shifted_f(Q, Qc, __double2float_rn(ch.w * inv_unit), ch.x - r.x, ch.y - r.y,
+                    ch.z - r.z);
       c = rec[c].skip;
     }
     store_quad_f(id, Q, qrec);
   }
+}
+
+// Largest cell mass m = rho h^3 of each field (FP64, rounded as in k_blocks),
+// as an atomic max on its bits (a non-negative double orders like its bits).
+// One CTA per caller block; invalid levels and densities are skipped here
+// and reported by the other kernels.
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_mass_max(int nb, const int *__restrict__ level, const T *__restrict__ density,
+               const double *__restrict__ Lf, const int *__restrict__ fid,
+               unsigned long long *__restrict__ mmax) {
+  const int b = blockIdx.x;
+  const int lb = level[b];
+  if (lb < 0 || lb > kMaxBlockLevel) return;
+  const int field = fid[b];
+  const double h = __dmul_rn(Lf[field], pow2d(-(lb + 3)));
+  const double vol = __dmul_rn(__dmul_rn(h, h), h);
+  const T *rho = density + (int64_t)b * kCellsPerBlock;
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < kCellsPerBlock; i += kBlockThreads) {
+    const double r = (double)rho[i];
+    if (r >= 0.0 && !isinf(r)) mx = fmax(mx, r);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomicMax(mmax + field, (unsigned long long)__double_as_longlong(__dmul_rn(mx, vol)));
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -657,20 +698,34 @@ cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *or
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                    (const double *)density, fa.L, fa.fid,
-                                                   n_nodes, mom, rec, aux, lvl, q64, qrec, flags);
+                                                   fa.mmax, n_nodes, mom, rec, aux, lvl, q64,
+                                                   qrec, flags);
   else
     k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                  (const float *)density, fa.L, fa.fid, n_nodes,
-                                                  mom, rec, aux, lvl, q64, qrec, flags);
+                                                  (const float *)density, fa.L, fa.fid, fa.mmax,
+                                                  n_nodes, mom, rec, aux, lvl, q64, qrec, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
+                            int density_is_fp64, const FieldArgs &fa) {
+  if (density_is_fp64)
+    k_mass_max<double><<<nb, kBlockThreads, 0, s>>>(nb, level, (const double *)density, fa.L,
+                                                     fa.fid, fa.mmax);
+  else
+    k_mass_max<float><<<nb, kBlockThreads, 0, s>>>(nb, level, (const float *)density, fa.L,
+                                                    fa.fid, fa.mmax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags) {
+                               double *q64, WalkQuad *qrec, unsigned *flags,
+                               const FieldArgs &fa) {
   k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
-                                                   n_nodes, mom, rec, aux, q64, qrec, flags);
+                                                   n_nodes, mom, rec, aux, q64, qrec, flags,
+                                                   fa.fld, fa.mmax);
   return cudaGetLastError();
 }
 

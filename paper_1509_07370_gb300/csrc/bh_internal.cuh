@@ -6,7 +6,8 @@
 //   mom  double4 {Rx, Ry, Rz, M}  FP64 centre of mass (box units) and mass
 //   rec  WalkRec (32 bytes)       what the walk reads, in one 256-bit load:
 //                                 the centre of mass and mass rounded to
-//                                 binary32 (Px and M stored twice so that they
+//                                 binary32, the mass in its field's binary32
+//                                 mass unit (below) (Px and M stored twice so that they
 //                                 form ready-made pairs for packed f32x2
 //                                 arithmetic), the squared opening radius s2
 //                                 for the current theta (0 for cells), and the
@@ -16,10 +17,23 @@
 //   lvl  uint8                    node level
 // Leaf blocks are renumbered in Morton order of their lower corner ("sorted
 // position" p); blk[p] = {level, bi, bj, bk}, orig[p] = caller block index.
+//
+// Binary32 mass unit.  Binary32 records (walk and quadrupole records) hold
+// masses divided by 2^e_f, with e_f = (binary exponent of the largest cell
+// mass of field f) - 40, so that the largest cell mass lies in [2^40, 2^41)
+// whatever the physical units (cgs included).  Then, with at most 2^24 cells
+// per field and distances down to 2^-21 of the box, no binary32 sum exceeds
+// ~2^86, and the quadrupole term of the deepest nodes (cells of 2^-21 of the
+// box, d^T Q d / 2 ~ m l^2 d^2 ~ 2^-88 for a cell 1e-12 as heavy as the
+// heaviest one) stays far above the binary32 underflow (2^-126).  Scaling by
+// a power of two is exact, so the binary32 walk computes the same numbers as
+// with unscaled masses wherever those were in range; it multiplies its sum
+// back by 2^e_f.  FP64 moments (mom, q64) stay physical.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -50,10 +64,11 @@ struct __align__(32) WalkRec {
 };
 static_assert(sizeof(WalkRec) == 32, "walk record must be 32 bytes");
 
-// Quadrupole walk record (only built with the quadrupole option): half the
-// diagonal of Q (Qxx/2 twice, for packed pairs), and the off-diagonal terms,
-// so that d^T Q d / 2 = dx (Qxx/2 dx + Qxy dy + Qxz dz) + dy (Qyy/2 dy + Qyz dz)
-//                       + Qzz/2 dz^2.
+// Quadrupole walk record (quadrupole or learned option), box units and the
+// field's binary32 mass unit: half the diagonal of Q (Qxx/2 twice, for packed
+// pairs), and the off-diagonal terms, so that
+//   d^T Q d / 2 = dx (Qxx/2 dx + Qxy dy + Qxz dz) + dy (Qyy/2 dy + Qyz dz)
+//                 + Qzz/2 dz^2.
 struct __align__(32) WalkQuad {
   float hxx, hxx2;
   float hyy, hzz;
@@ -80,8 +95,10 @@ struct Tree {
   int4 *d_fld = nullptr;        // per sorted block
   double *d_invL = nullptr;     // per field
   double *d_L = nullptr;        // per field
+  unsigned long long *d_mmax = nullptr;  // per field, largest cell mass (bits)
   int nf_cap = 0;
   std::vector<double> h_L;      // per field, host copy
+  std::vector<int64_t> h_fnode; // first node of each field, then the total
   // batched solve: CUDA graph of (moments for new densities + walk)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -125,7 +142,28 @@ struct FieldArgs {
   int4 *fld;
   const double *invL;
   const double *L;   // box side per field
+  unsigned long long *mmax;  // per field: bits of the largest FP64 cell mass
 };
+
+// The binary32 mass unit 2^e of a field from the bits of its largest cell
+// mass (a non-negative double): e = its binary exponent - 40; 0 for zero.
+__host__ __device__ inline int mass_exponent(unsigned long long bits) {
+  const int E = (int)((bits >> 52) & 0x7ff);
+  if (E == 0) return 0;                   // zero (or subnormal) masses
+  const int e = E - 1023 - 40;
+  return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+}
+// 2^e as a double, |e| <= 1022.
+__host__ __device__ inline double pow2i(int e) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)(1023 + e) << 52);
+#else
+  const unsigned long long u = (unsigned long long)(1023 + e) << 52;
+  double d;
+  memcpy(&d, &u, sizeof d);
+  return d;
+#endif
+}
 
 // ---- build kernels (bh_build.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
@@ -144,6 +182,10 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
                              unsigned *flags, const FieldArgs &fa, const int *orig);
+// Largest cell mass of every field (atomic max on fa.mmax, which the caller
+// zeroes first); caller block order.
+cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
+                            int density_is_fp64, const FieldArgs &fa);
 cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                           const int *count, const int *prestart, const void *density,
                           int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
@@ -152,13 +194,14 @@ cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *or
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags);
+                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa);
 
 // ---- walk kernels (bh_walk.cu) ---------------------------------------------
 cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
                               float inv_theta);
 // out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
-// Potential scale of field f: -G * invL[f].  wpc = warps per CTA of the
+// Potential scale of field f: -G * invL[f] (times the field's mass unit for
+// the binary32 walk).  wpc = warps per CTA of the
 // per-cell binary32 walk (0 = default), a tunable launch shape.
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
                         const double4_32a *mom, const WalkQuad *qrec, const double *q64,

@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kEvalThreads)
     k_pairs_eval(int64_t npairs, const int64_t *__restrict__ pairs, const int *__restrict__ pos,
                  const int4 *__restrict__ blk, const WalkRec *__restrict__ rec,
                  const double4_32a *__restrict__ mom, const float2 *__restrict__ aux,
-                 const WalkQuad *__restrict__ qrec, float *__restrict__ feat,
+                 const WalkQuad *__restrict__ qrec, const int4 *__restrict__ fld,
+                 const unsigned long long *__restrict__ mmax, float *__restrict__ feat,
                  float *__restrict__ eps, int64_t *__restrict__ node_out) {
   __shared__ double part[kEvalThreads];
   const int64_t q = blockIdx.x;
@@ -120,7 +121,8 @@ __global__ void __launch_bounds__(kEvalThreads)
   const double qf = sqrt(Qxx * Qxx + Qyy * Qyy + Qzz * Qzz +
                          2.0 * ((double)w.qxy * w.qxy + (double)w.qxz * w.qxz +
                                 (double)w.qyz * w.qyz));
-  const double ml2 = m.w > 0.0 ? m.w * l * l : 1.0;
+  // the record's Q is in the field's binary32 mass unit 2^e
+  const double ml2 = m.w > 0.0 ? m.w * pow2i(-mass_exponent(mmax[fld[p].w])) * l * l : 1.0;
   float *f = feat + kMlpIn * q;
   f[0] = (float)ux;
   f[1] = (float)uy;
@@ -318,8 +320,8 @@ bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int6
   const int64_t np = (int64_t)h_count < cap ? (int64_t)h_count : cap;
   if (e == cudaSuccess && np > 0) {
     k_pairs_eval<<<(unsigned)np, kEvalThreads, 0, s>>>(np, d_pairs, t.d_pos, t.d_blk, t.d_rec,
-                                                        t.d_mom, t.d_aux, t.d_qrec, feat, eps,
-                                                        node);
+                                                        t.d_mom, t.d_aux, t.d_qrec, t.d_fld,
+                                                        t.d_mmax, feat, eps, node);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

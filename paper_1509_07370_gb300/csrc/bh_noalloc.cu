@@ -52,7 +52,8 @@ constexpr size_t kOffFstart = up256(kOffFlags + 4 * sizeof(unsigned));   // one 
 constexpr size_t kOffFid = up256(kOffFstart + 2 * sizeof(int));
 constexpr size_t kOffFld = up256(kOffFid + sizeof(int) * kNoAllocMaxBlocks);
 constexpr size_t kOffBox = up256(kOffFld + sizeof(int4) * kNoAllocMaxBlocks);  // L, 1/L
-constexpr size_t kOffMom = up256(kOffBox + 2 * sizeof(double));
+constexpr size_t kOffMmax = up256(kOffBox + 2 * sizeof(double));  // largest cell mass
+constexpr size_t kOffMom = up256(kOffMmax + sizeof(unsigned long long));
 constexpr size_t kOffRec = up256(kOffMom + sizeof(double4_32a) * kNoAllocMaxNodes);
 constexpr size_t kOffAux = up256(kOffRec + sizeof(WalkRec) * kNoAllocMaxNodes);
 constexpr size_t kOffLvl = up256(kOffAux + sizeof(float2) * kNoAllocMaxNodes);
@@ -70,7 +71,7 @@ struct Geometry {  // passed by value as a kernel parameter (1 KB)
 // Copies the block geometry from the kernel parameter into the scratch,
 // describes the single field, and clears the error flags of this call.
 __global__ void k_stage_geometry(Geometry g, int nb, int *level, int *ijk, unsigned *flags,
-                                 int *fstart, double *box, double L) {
+                                 int *fstart, double *box, double L, unsigned long long *mmax) {
   const int t = threadIdx.x;
   if (t < 4) flags[t] = 0u;
   if (t == 0) {
@@ -78,6 +79,7 @@ __global__ void k_stage_geometry(Geometry g, int nb, int *level, int *ijk, unsig
     fstart[1] = nb;
     box[0] = L;
     box[1] = 1.0 / L;
+    *mmax = 0ull;
   }
   for (int i = t; i < nb; i += blockDim.x) level[i] = g.level[i];
   for (int i = t; i < 3 * nb; i += blockDim.x) ijk[i] = g.ijk[i];
@@ -165,8 +167,10 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   fa.fld = (int4 *)(base + kOffFld);
   fa.L = d_box;
   fa.invL = d_box + 1;
+  fa.mmax = (unsigned long long *)(base + kOffMmax);
 
-  k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags, d_fstart, d_box, box_len);
+  k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags, d_fstart, d_box, box_len,
+                                     fa.mmax);
   NA_CUDA(cudaGetLastError());
   NA_CUDA(launch_block_keys(s, nb, d_level, d_ijk, d_key[0], d_idx[0], d_flags, fa));
   NA_CUDA(launch_sort_blocks(s, d_key, d_idx, d_flags, fa));
@@ -175,11 +179,12 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   NA_CUDA(launch_prestart_scan(s, nb, d_count, d_prestart, d_flags));
   NA_CUDA(launch_top_nodes(s, nb, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_rec, d_aux,
                            d_lvl, d_flags, fa, d_orig));
+  NA_CUDA(launch_mass_max(s, nb, d_level, density, density_is_fp64, fa));
   NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64, fa,
                         n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
   for (int lev = max_level - 1; lev >= 0; --lev)
     NA_CUDA(launch_top_moments(s, nb, lev, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_mom,
-                               d_rec, d_aux, nullptr, nullptr, d_flags));
+                               d_rec, d_aux, nullptr, nullptr, d_flags, fa));
   // the walk must only run on a valid tree: check the flags first
   unsigned h_flags[4] = {0, 0, 0, 0};
   NA_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));

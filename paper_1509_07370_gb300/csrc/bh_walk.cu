@@ -85,7 +85,8 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, const WalkRec 
                                             const int4 *__restrict__ blk,
                                             const int *__restrict__ orig,
                                             const int4 *__restrict__ fld,
-                                            const double *__restrict__ invL, double G,
+                                            const double *__restrict__ invL,
+                                            const unsigned long long *__restrict__ mmax, double G,
                                             float *__restrict__ out, int32_t *__restrict__ n_int,
                                             int32_t *__restrict__ n_test,
                                             int32_t *__restrict__ n_leaf) {
@@ -184,7 +185,8 @@ __device__ __forceinline__ void walk_octant(unsigned u, int lane, const WalkRec 
     if (KAHAN) sum = sub2(sum, comp);
     float sa, sb;
     upk(sum, sa, sb);
-    const float scale = (float)(-G * invL[F.w]);
+    // -G/L times the field's binary32 mass unit 2^e (exact), rounded once
+    const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));
     out[cell] = __fmul_rn(sa, scale);
     out[cell + 1] = __fmul_rn(sb, scale);
   }
@@ -199,14 +201,14 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
     k_walk_pair(unsigned nunits, const WalkRec *__restrict__ rec,
                 const WalkQuad *__restrict__ qrec, const int4 *__restrict__ blk,
                 const int *__restrict__ orig, const int4 *__restrict__ fld,
-                const double *__restrict__ invL, double G, float *__restrict__ out,
-                int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
-                int32_t *__restrict__ n_leaf) {
+                const double *__restrict__ invL, const unsigned long long *__restrict__ mmax,
+                double G, float *__restrict__ out, int32_t *__restrict__ n_int,
+                int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
   const int lane = threadIdx.x & 31;
   const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, G, out, n_int,
-                                   n_test, n_leaf);
+  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
+                                   n_int, n_test, n_leaf);
 }
 
 // ---- one target per lane: binary64 interactions and/or the warp vote --------
@@ -216,7 +218,8 @@ __global__ void __launch_bounds__(kWalkThreads)
                   const double4_32a *__restrict__ mom, const WalkQuad *__restrict__ qrec,
                   const double *__restrict__ q64, const int4 *__restrict__ blk,
                   const int *__restrict__ orig, const int4 *__restrict__ fld,
-                  const double *__restrict__ invL, double G, void *__restrict__ out,
+                  const double *__restrict__ invL, const unsigned long long *__restrict__ mmax,
+                  double G, void *__restrict__ out,
                   int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
                   int32_t *__restrict__ n_leaf) {
   const int warp = blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
@@ -227,8 +230,9 @@ __global__ void __launch_bounds__(kWalkThreads)
   const int4 B = blk[p];
   const int4 F = fld[p];        // this field's node range
   const unsigned n_nodes = (unsigned)F.y;
-  const double scale_d = -G * invL[F.w];
-  const float scale_f = (float)scale_d;
+  const double scale_d = -G * invL[F.w];  // FP64 walk: physical FP64 moments
+  // binary32 walk: the records' masses are in the field's unit 2^e
+  const float scale_f = (float)(scale_d * pow2i(mass_exponent(mmax[F.w])));
   const int cx = (int)compact3(m), cy = (int)compact3(m >> 1), cz = (int)compact3(m >> 2);
   const int lc = B.x + 3;
   const float hh = pow2f(-(lc + 1));
@@ -327,7 +331,7 @@ cudaError_t go_pair(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *
   const int w = wpc > 0 ? wpc : kWarpsPerCta;
   const int grid = (int)((nunits + w - 1) / w);
   k_walk_pair<KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
-      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, G, (float *)out, ni, nt, nl);
+      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
   return cudaGetLastError();
 }
 
@@ -339,7 +343,7 @@ cudaError_t go_scalar(cudaStream_t s, int nb, const WalkRec *rec, const double4_
   const int nbricks = nb * 16;
   const int grid = (nbricks + kWarpsPerCta - 1) / kWarpsPerCta;
   k_walk_scalar<F64, VOTE, KAHAN, COUNTS, QUAD><<<grid, kWalkThreads, 0, s>>>(
-      nbricks, rec, mom, qrec, q64, blk, orig, fa.fld, fa.invL, G, out, ni, nt, nl);
+      nbricks, rec, mom, qrec, q64, blk, orig, fa.fld, fa.invL, fa.mmax, G, out, ni, nt, nl);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,8 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 }
 
 // Appends one row: features of the pair (binary32, then bf16), c, target.
+// Quadrupole and mass share the field's binary32 mass unit, so their ratio
+// u^T Q u / (M l^2) is the physical one.
 __device__ __forceinline__ void queue_row(WarpQueue &Q, int row, float dx, float dy, float dz,
                                           float r, float l, float dl, float inv_ml2, float qf,
                                           const WalkQuad &q, float coef, int target) {
@@ -161,7 +163,8 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
     k_walk_learned(unsigned nunits, const WalkRec *__restrict__ rec,
                    const WalkQuad *__restrict__ qrec, const float2 *__restrict__ aux,
                    const int4 *__restrict__ blk, const int *__restrict__ orig,
-                   const int4 *__restrict__ fld, const double *__restrict__ invL, double G,
+                   const int4 *__restrict__ fld, const double *__restrict__ invL,
+                   const unsigned long long *__restrict__ mmax, double G,
                    const MlpDev *__restrict__ mlp, float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LearnSmem &S = *reinterpret_cast<LearnSmem *>(smem_raw);
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
   if (KAHAN) sum = sub2(sum, comp);
   float sa, sb;
   upk(sum, sa, sb);
-  const float scale = (float)(-G * invL[F.w]);
+  const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));
   out[cell] = __fmul_rn(sa, scale);
   out[cell + 1] = __fmul_rn(sb, scale);
 }
@@ -306,11 +309,13 @@ cudaError_t launch_walk_learned(cudaStream_t s, bh_ctx *ctx, double G, void *out
   const unsigned grid = (nunits + kLWarps - 1) / kLWarps;
   if (kahan)
     k_walk_learned<true><<<grid, kLWarps * 32, smem, s>>>(
-        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, G, ctx->d_mlp,
+        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
+        ctx->d_mlp,
         (float *)out);
   else
     k_walk_learned<false><<<grid, kLWarps * 32, smem, s>>>(
-        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, G, ctx->d_mlp,
+        nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
+        ctx->d_mlp,
         (float *)out);
   return cudaGetLastError();
 }

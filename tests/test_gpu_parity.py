@@ -370,3 +370,84 @@ def test_stats_sizes_timings_and_work_totals():
     plain = _build(B.Solver(), mesh, rho)
     plain.potential(0.5, out=out)
     assert plain.stats()["build_ms"] == -1.0 and plain.stats()["potential_ms"] == -1.0
+
+
+# ------------------------------------------------ units and extreme depths ---
+def test_physical_units_do_not_overflow_the_binary32_walk():
+    """cgs units: rho ~ 1e-18 g/cm^3 in a 10 pc box holds ~3e40 g, beyond the
+    binary32 range (3.4e38): the binary32 records carry masses in a per-field
+    power-of-two unit, so the binary32 walks still match the FP64 oracle."""
+    mesh, rho = _mesh("refined_twice")
+    L, G = 3.0857e19, 6.674e-8
+    m = mg.Mesh(mesh.level, mesh.ijk, box_lo=(-L / 2, -L / 2, -L / 2), box_len=L)
+    rho_cgs = rho * 1e-18
+    t = _oracle(m, rho_cgs)
+    ref, _, _ = t.walk(0.5, G=G)
+    assert np.abs(t.export()["M"][0]) > 1e39
+    for quad in (False, True):
+        s = B.Solver(quadrupole=quad)
+        _build(s, m, rho_cgs)
+        phi = s.potential(0.5, G=G).cpu().numpy()
+        want = t.walk(0.5, G=G, quad=True)[0] if quad else ref
+        assert np.all(np.isfinite(phi)) and _rel(phi, want).max() <= F32_TOL
+    s = _build(_solver(prec=B.BH_PREC_F64), m, rho_cgs)
+    assert _rel(s.potential(0.5, G=G).cpu().numpy(), ref).max() <= F64_TOL
+
+
+def _chain18():
+    if "chain18" not in MESHES:
+        m = mg.refined_mesh(1, 18, lambda lev, ijk: np.all(ijk == 0, axis=1), name="chain18")
+        MESHES["chain18"] = (m, mg.random_density(m, seed=18))
+    return MESHES["chain18"]
+
+
+def test_deepest_levels_tree_decisions_and_potentials():
+    """One corner refined down to block level 18 (cells of 2^-21 of the box,
+    the end of the 63-bit key lattice; 911 blocks): tree and moments
+    bit-exact, decisions bit-exact, monopole and quadrupole binary32 walks
+    within 1e-5 of the oracle on the deepest cells and a random sample (the
+    binary32 mass unit keeps ½ d^T Q d of nodes 2^-20 wide far from the
+    binary32 underflow)."""
+    mesh, rho = _chain18()
+    assert int(mesh.level.max()) == 18
+    s = _build(_solver(), mesh, rho)
+    t = _oracle(mesh, rho)
+    e = t.export()
+    g = {k: v.cpu().numpy() for k, v in s.export_nodes().items()}
+    assert np.array_equal(g["M"], e["M"]) and np.array_equal(g["R"], e["R"])
+    assert np.array_equal(g["skip"], _subtree_end(e["parent"]))
+    deep = np.flatnonzero(np.repeat(mesh.level == 18, 512))
+    tg = np.unique(np.concatenate([deep, np.random.default_rng(5).choice(mesh.ncells, 3000,
+                                                                         replace=False)]))
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+    ref, oi, ot = t.walk(0.6, targets=tg)
+    assert np.array_equal(ni[tg], oi) and np.array_equal(nt[tg], ot)
+    phi = s.potential(0.6).cpu().numpy()
+    assert _rel(phi[tg], ref).max() <= F32_TOL
+    sq = B.Solver(quadrupole=True)
+    _build(sq, mesh, rho)
+    refq = t.walk(0.6, targets=tg, quad=True)[0]
+    assert _rel(sq.potential(0.6).cpu().numpy()[tg], refq).max() <= F32_TOL
+
+
+def test_zero_density_regions_and_all_zero_field():
+    """Massless blocks and cells (nodes of zero mass sit at their geometric
+    centre): bit-exact tree, potentials within 1e-5; an all-zero field gives
+    zero potential."""
+    mesh, rho = _mesh("diag_refined")
+    z = rho.copy()
+    rng = np.random.default_rng(3)
+    z[rng.random(mesh.nblocks) < 0.4] = 0.0
+    z[rng.random(z.shape) < 0.3] = 0.0
+    s = _build(_solver(), mesh, z)
+    t = _oracle(mesh, z)
+    e = t.export()
+    g = {k: v.cpu().numpy() for k, v in s.export_nodes().items()}
+    assert np.array_equal(g["M"], e["M"]) and np.array_equal(g["R"], e["R"])
+    ref, _, _ = t.walk(0.5)
+    phi = s.potential(0.5).cpu().numpy()
+    assert _rel(phi, ref).max() <= F32_TOL
+    sq = _build(B.Solver(quadrupole=True), mesh, z)
+    assert _rel(sq.potential(0.5).cpu().numpy(), t.walk(0.5, quad=True)[0]).max() <= F32_TOL
+    s0 = _build(_solver(), mesh, np.zeros_like(rho))
+    assert np.all(s0.potential(0.5).cpu().numpy() == 0.0)
