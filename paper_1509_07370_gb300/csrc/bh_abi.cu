@@ -149,6 +149,7 @@ bhg::FieldArgs field_args(bhg::Tree &t) {
   fa.invL = t.d_invL;
   fa.L = t.d_L;
   fa.mmax = t.d_mmax;
+  fa.inv_theta = t.last_inv_theta;
   return fa;
 }
 
@@ -315,7 +316,8 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
     return fail(ctx, BH_ERR_ARG, "%s: density has a negative or non-finite value", who);
   for (int a = 0; a < 3; ++a) t.lo[a] = box_lo[a];
   t.L = box_len[0];
-  t.s2_inv_theta = -1.0f;
+  // the moment kernels prepared s2 for the last walk's theta, if any
+  t.s2_inv_theta = fa.inv_theta > 0.0f ? fa.inv_theta : -1.0f;
   t.built = true;
   return BH_OK;
 }
@@ -406,8 +408,9 @@ bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp6
   const bool timed = timing_mark(ctx, 0);
   BH_CUDA(cudaMemsetAsync(ctx->tree.d_flags, 0, sizeof(unsigned), ctx->stream));
   // the records are rewritten (s2 included, and delta changes with the
-  // density): the next walk must prepare s2 again
-  ctx->tree.s2_inv_theta = -1.0f;
+  // density), with s2 for the last walk's theta if there was one
+  const float inv_theta = ctx->tree.last_inv_theta;
+  ctx->tree.s2_inv_theta = inv_theta > 0.0f ? inv_theta : -1.0f;
   st = enqueue_moments(ctx, density, density_is_fp64);
   ctx->build_timed = st == BH_OK && timed && timing_mark(ctx, 1);
   return st;
@@ -456,6 +459,7 @@ static bh_status prepare(bh_ctx *ctx, double theta) {
   bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
   const float inv_theta = (float)(1.0 / theta);
+  t.last_inv_theta = inv_theta;
   if (inv_theta != t.s2_inv_theta) {
     BH_CUDA(bhg::launch_prepare_s2(ctx->stream, t.n_nodes, t.d_aux, t.d_rec, inv_theta));
     t.s2_inv_theta = inv_theta;
@@ -706,7 +710,7 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
     t.graph_G = G;
   }
   BH_CUDA(cudaGraphLaunch(t.graph_exec, ctx->stream));
-  t.s2_inv_theta = (float)(1.0 / theta);
+  t.s2_inv_theta = t.last_inv_theta = (float)(1.0 / theta);
   return BH_OK;
 }
 

@@ -314,12 +314,21 @@ __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double
 }
 
 // inv_unit = 2^-e of the field's binary32 mass unit (the record's mass).
+// inv_theta > 0: also the squared opening radius s2 = fl(fl(l fl(1/theta)) +
+// delta)^2 from the same binary32 l and delta as k_prepare_s2 (identical).
 __device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int level,
                                                const Moment &r, double4_32a *mom, WalkRec *rec,
-                                               float2 *aux, uint8_t *lvl, double inv_unit) {
+                                               float2 *aux, uint8_t *lvl, double inv_unit,
+                                               float inv_theta) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
-  rec[id] = make_rec(r.x, r.y, r.z, r.m * inv_unit, skip);
-  aux[id] = make_float2(pow2f(-level), __double2float_rn(r.delta));
+  WalkRec w = make_rec(r.x, r.y, r.z, r.m * inv_unit, skip);
+  const float l = pow2f(-level), delta = __double2float_rn(r.delta);
+  if (inv_theta > 0.0f) {
+    const float s = __fadd_rn(__fmul_rn(l, inv_theta), delta);
+    w.s2 = __fmul_rn(s, s);
+  }
+  rec[id] = w;
+  aux[id] = make_float2(l, delta);
   if (lvl) lvl[id] = (uint8_t)level;
 }
 
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(kBlockThreads)
              const int *__restrict__ count, const int *__restrict__ prestart,
              const T *__restrict__ density, const double *__restrict__ Lf,
              const int *__restrict__ fid, const unsigned long long *__restrict__ mmax,
-             int64_t n_nodes,
+             float inv_theta, int64_t n_nodes,
              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec, float2 *__restrict__ aux,
              uint8_t *__restrict__ lvl, double *__restrict__ q64, WalkQuad *__restrict__ qrec,
              unsigned *flags) {
@@ -477,7 +486,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     gy[q] = r.y;
     gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -513,7 +522,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     py[c] = r.y;
     pz[c] = r.z;
     const int64_t id = root + 1 + 73 * c;
-    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit);
+    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -543,7 +552,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 #pragma unroll
     for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl, inv_unit);
+    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) add_shifted(Q, pq[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
@@ -567,7 +576,7 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
                               float2 *__restrict__ aux, double *__restrict__ q64,
                               WalkQuad *__restrict__ qrec, unsigned *flags,
                               const int4 *__restrict__ fld,
-                              const unsigned long long *__restrict__ mmax) {
+                              const unsigned long long *__restrict__ mmax, float inv_theta) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int cnt = count[p];
@@ -583,11 +592,13 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
   const double cz = __dmul_rn((double)(compact3(kp >> 2) >> sh) + 0.5, hl);
   double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
   int64_t c = id + 1;
+  int64_t child[8];  // found by following skip pointers, kept for the quadrupoles
   for (int o = 0; o < 8; ++o) {
     if (c <= 0 || c >= n_nodes) {
       atomicOr(flags, kErrIndex);
       return;
     }
+    child[o] = c;
     const double4_32a ch = mom[c];
     accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
     c = rec[c].skip;
@@ -595,26 +606,22 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
   const int64_t skip = rec[id].skip;
   const double inv_unit = pow2i(-mass_exponent(mmax[fld[p].w]));
-  store_internal(id, skip, level, r, mom, rec, aux, nullptr, inv_unit);
+  store_internal(id, skip, level, r, mom, rec, aux, nullptr, inv_unit, inv_theta);
   if (q64) {
     double Q[6] = {0, 0, 0, 0, 0, 0};
-    c = id + 1;
     for (int o = 0; o < 8; ++o) {
-      const double4_32a ch = mom[c];
-      add_shifted(Q, q64 + 6 * c, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
-      c = rec[c].skip;
+      const double4_32a ch = mom[child[o]];
+      add_shifted(Q, q64 + 6 * child[o], ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
     }
     store_quad(id, Q, q64, qrec, inv_unit);
   } else if (qrec) {
     float Q[6] = {0, 0, 0, 0, 0, 0};
-    c = id + 1;
     for (int o = 0; o < 8; ++o) {
-      const double4_32a ch = mom[c];
+      const double4_32a ch = mom[child[o]];
       float Qc[6];
-      load_quad_f(qrec[c], Qc);
+      load_quad_f(qrec[child[o]], Qc);
       add_shifted_f(Q, Qc, __double2float_rn(ch.w * inv_unit), ch.x - r.x, ch.y - r.y,
                     ch.z - r.z);
-      c = rec[c].skip;
     }
     store_quad_f(id, Q, qrec);
   }
@@ -698,12 +705,13 @@ cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *or
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                    (const double *)density, fa.L, fa.fid,
-                                                   fa.mmax, n_nodes, mom, rec, aux, lvl, q64,
-                                                   qrec, flags);
+                                                   fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux,
+                                                   lvl, q64, qrec, flags);
   else
     k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                   (const float *)density, fa.L, fa.fid, fa.mmax,
-                                                  n_nodes, mom, rec, aux, lvl, q64, qrec, flags);
+                                                  fa.inv_theta, n_nodes, mom, rec, aux, lvl, q64,
+                                                  qrec, flags);
   return cudaGetLastError();
 }
 
@@ -725,7 +733,7 @@ cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned
                                const FieldArgs &fa) {
   k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
                                                    n_nodes, mom, rec, aux, q64, qrec, flags,
-                                                   fa.fld, fa.mmax);
+                                                   fa.fld, fa.mmax, fa.inv_theta);
   return cudaGetLastError();
 }
 

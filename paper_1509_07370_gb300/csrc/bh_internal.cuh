@@ -128,6 +128,7 @@ struct Tree {
   double L = 1.0;
   bool built = false;
   float s2_inv_theta = -1.0f;  // inverse theta the s2 field was prepared for
+  float last_inv_theta = 0.0f; // of the last walk: builds prepare s2 for it
 };
 
 // Several fields (independent meshes) built and walked together: their
@@ -143,6 +144,9 @@ struct FieldArgs {
   const double *invL;
   const double *L;   // box side per field
   unsigned long long *mmax;  // per field: bits of the largest FP64 cell mass
+  // > 0: the moment kernels also write the squared opening radius of every
+  // internal node for this 1/theta (as k_prepare_s2 would); 0: they write 0
+  float inv_theta;
 };
 
 // The binary32 mass unit 2^e of a field from the bits of its largest cell

@@ -168,6 +168,7 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   fa.L = d_box;
   fa.invL = d_box + 1;
   fa.mmax = (unsigned long long *)(base + kOffMmax);
+  fa.inv_theta = 0.0f;  // s2 is prepared below
 
   k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags, d_fstart, d_box, box_len,
                                      fa.mmax);
