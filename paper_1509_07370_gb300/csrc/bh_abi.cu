@@ -168,10 +168,10 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64)
   BH_CUDA(bhg::launch_blocks(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
                              density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl,
                              q64, qrec, t.d_flags));
-  for (int lev = t.max_block_level - 1; lev >= 0; --lev)
-    BH_CUDA(bhg::launch_top_moments(s, t.nb, lev, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
-                                    t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec, t.d_flags,
-                                    fa));
+  const int64_t n_top = t.n_nodes - (int64_t)bhg::kNodesPerBlock * t.nb;
+  BH_CUDA(bhg::launch_top_tree(s, t.nb, t.max_block_level, n_top, t.d_key[0], t.d_blk, t.d_count,
+                               t.d_prestart, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec,
+                               t.d_flags, fa));
   return BH_OK;
 }
 
@@ -360,7 +360,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   ctx->opt = o;
   ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
-  if (cudaSetDevice(device) != cudaSuccess ||
+  if (cudaSetDevice(device) != cudaSuccess || bhg::prepare_learned_kernels() != cudaSuccess ||
       cudaMalloc(&ctx->tree.d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->tree.h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();

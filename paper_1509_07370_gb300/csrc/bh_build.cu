@@ -19,7 +19,9 @@
 //      (k_top_nodes);
 //   4. one CTA per block reduces its 512 cells to 64, 8 and 1 nodes in shared
 //      memory (k_blocks), and one short launch per level reduces the top
-//      nodes, deepest level first (k_top_moments).
+//      nodes, deepest level first (k_top_moments).  (A single CTA walking the
+//      levels with barriers was no faster: each level's cost is the latency
+//      of its FP64 chain, not the launch.)
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
@@ -567,22 +569,20 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
 }
 
-// Top nodes of one level: children are top nodes one level down or block roots,
-// found by following skip pointers from the first child (the next node).
-__global__ void k_top_moments(int nb, int level, const unsigned long long *__restrict__ key,
-                              const int4 *__restrict__ blk, const int *__restrict__ count,
-                              const int *__restrict__ prestart, int64_t n_nodes,
-                              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
-                              float2 *__restrict__ aux, double *__restrict__ q64,
-                              WalkQuad *__restrict__ qrec, unsigned *flags,
-                              const int4 *__restrict__ fld,
-                              const unsigned long long *__restrict__ mmax, float inv_theta) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nb) return;
+// The top node of sorted block p at `level` (the block starts cnt = count[p]
+// top nodes, levels lb - cnt .. lb - 1): its children are top nodes one level
+// down or block roots, found by following skip pointers from the first child
+// (the next node).
+__device__ __forceinline__ void top_moment(int p, int level, const unsigned long long *key,
+                                           const int4 *blk, const int *count,
+                                           const int *prestart, int64_t n_nodes,
+                                           double4_32a *mom, WalkRec *rec, float2 *aux,
+                                           double *q64, WalkQuad *qrec, unsigned *flags,
+                                           const int4 *fld, const unsigned long long *mmax,
+                                           float inv_theta) {
   const int cnt = count[p];
   const int lb = blk[p].x;
   const int j0 = lb - cnt;
-  if (cnt == 0 || level < j0 || level >= lb) return;
   const int64_t id = (int64_t)prestart[p] + (level - j0);
   const unsigned long long kp = key[p];
   const int sh = kKeyLevels - level;
@@ -627,6 +627,24 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
   }
 }
 
+// One launch per level (any number of top nodes).
+__global__ void k_top_moments(int nb, int level, const unsigned long long *__restrict__ key,
+                              const int4 *__restrict__ blk, const int *__restrict__ count,
+                              const int *__restrict__ prestart, int64_t n_nodes,
+                              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
+                              float2 *__restrict__ aux, double *__restrict__ q64,
+                              WalkQuad *__restrict__ qrec, unsigned *flags,
+                              const int4 *__restrict__ fld,
+                              const unsigned long long *__restrict__ mmax, float inv_theta) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nb) return;
+  const int cnt = count[p];
+  const int lb = blk[p].x;
+  if (cnt == 0 || level < lb - cnt || level >= lb) return;
+  top_moment(p, level, key, blk, count, prestart, n_nodes, mom, rec, aux, q64, qrec, flags, fld,
+             mmax, inv_theta);
+}
+
 // Largest cell mass m = rho h^3 of each field (FP64, rounded as in k_blocks),
 // as an atomic max on its bits (a non-negative double orders like its bits).
 // One CTA per caller block; invalid levels and densities are skipped here
@@ -643,14 +661,18 @@ __global__ void __launch_bounds__(kBlockThreads)
   const double h = __dmul_rn(Lf[field], pow2d(-(lb + 3)));
   const double vol = __dmul_rn(__dmul_rn(h, h), h);
   const T *rho = density + (int64_t)b * kCellsPerBlock;
-  double mx = 0.0;
+  T mx = 0;  // the largest density, in its own precision (max is exact)
   for (int i = threadIdx.x; i < kCellsPerBlock; i += kBlockThreads) {
-    const double r = (double)rho[i];
-    if (r >= 0.0 && !isinf(r)) mx = fmax(mx, r);
+    const T r = rho[i];
+    if (r >= T(0) && !isinf(r)) mx = r > mx ? r : mx;
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0)
-    atomicMax(mmax + field, (unsigned long long)__double_as_longlong(__dmul_rn(mx, vol)));
+  for (int o = 16; o > 0; o >>= 1) {
+    const T v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx > T(0))
+    atomicMax(mmax + field,
+              (unsigned long long)__double_as_longlong(__dmul_rn((double)mx, vol)));
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -724,6 +746,20 @@ cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void
     k_mass_max<float><<<nb, kBlockThreads, 0, s>>>(nb, level, (const float *)density, fa.L,
                                                     fa.fid, fa.mmax);
   return cudaGetLastError();
+}
+
+cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top,
+                            const unsigned long long *key, const int4 *blk, const int *count,
+                            const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
+                            float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
+                            const FieldArgs &fa) {
+  if (n_top <= 0) return cudaSuccess;
+  for (int lev = max_level - 1; lev >= 0; --lev) {
+    const cudaError_t e = launch_top_moments(s, nb, lev, key, blk, count, prestart, n_nodes, mom,
+                                             rec, aux, q64, qrec, flags, fa);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,

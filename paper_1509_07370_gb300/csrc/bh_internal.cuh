@@ -195,6 +195,16 @@ cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *or
                           int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
                           double4_32a *mom, WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
                           WalkQuad *qrec, unsigned *flags);
+// Raises the dynamic shared-memory limit of the learned walk (more than 48 KB)
+// on the current device; called once per context, outside any graph capture.
+cudaError_t prepare_learned_kernels();
+// Every top level, deepest first, one launch per level; n_top = number of
+// top nodes (all fields).
+cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top,
+                            const unsigned long long *key, const int4 *blk, const int *count,
+                            const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
+                            float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
+                            const FieldArgs &fa);
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,

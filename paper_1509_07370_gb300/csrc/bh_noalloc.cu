@@ -183,9 +183,8 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   NA_CUDA(launch_mass_max(s, nb, d_level, density, density_is_fp64, fa));
   NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64, fa,
                         n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
-  for (int lev = max_level - 1; lev >= 0; --lev)
-    NA_CUDA(launch_top_moments(s, nb, lev, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_mom,
-                               d_rec, d_aux, nullptr, nullptr, d_flags, fa));
+  NA_CUDA(launch_top_tree(s, nb, max_level, (nb - 1) / 7, d_key[0], d_blk, d_count, d_prestart,
+                          n_nodes, d_mom, d_rec, d_aux, nullptr, nullptr, d_flags, fa));
   // the walk must only run on a valid tree: check the flags first
   unsigned h_flags[4] = {0, 0, 0, 0};
   NA_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));

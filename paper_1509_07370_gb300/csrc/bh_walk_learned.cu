@@ -296,16 +296,21 @@ __global__ void __launch_bounds__(kLWarps * 32, 2)
 
 }  // namespace
 
+cudaError_t prepare_learned_kernels() {
+  const int smem = (int)sizeof(LearnSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_walk_learned<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_walk_learned<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  return e;
+}
+
 cudaError_t launch_walk_learned(cudaStream_t s, bh_ctx *ctx, double G, void *out) {
   const Tree &t = ctx->tree;
   const unsigned nunits = (unsigned)t.nb * 8u;
-  const int smem = (int)sizeof(LearnSmem);
+  const int smem = (int)sizeof(LearnSmem);  // limit set by prepare_learned_kernels
   const bool kahan = ctx->opt.kahan != 0;
-  cudaError_t e = kahan ? cudaFuncSetAttribute(k_walk_learned<true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                        : cudaFuncSetAttribute(k_walk_learned<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   const unsigned grid = (nunits + kLWarps - 1) / kLWarps;
   if (kahan)
     k_walk_learned<true><<<grid, kLWarps * 32, smem, s>>>(
