@@ -260,15 +260,16 @@ constexpr int kMlpNW = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 
 // mma.sync m16n8k16 (bf16): for each (n-tile, k-tile), 32 lanes x {b0, b1};
 // lane (g = lane / 4, t = lane % 4) holds W[k0 + 2t .. k0 + 2t + 1][n0 + g] in
 // b0 and W[k0 + 2t + 8 .. k0 + 2t + 9][n0 + g] in b1, the lower k in the low
-// half.  Layer 1: K = 16 (inputs 10..15 zero), 8 n-tiles; layer 2: 8 n-tiles x
-// 4 k-tiles; layer 3: 4 k-tiles of one n-tile whose column 0 is the output.
-// The walk carries activations as 2 GELU(a), so layer-2 and layer-3 weights
-// are stored halved (exact in bf16).  Biases FP32.
+// half.  Layer 1: K = 16: inputs 0..9 the features, input 10 a constant 1
+// whose weights are b1 (so b1 is rounded to bf16 and added by the tensor
+// core), inputs 11..15 zero; 8 n-tiles.  Layer 2: 8 n-tiles x 4 k-tiles;
+// layer 3: 4 k-tiles of one n-tile whose column 0 is the output.  The walk
+// carries activations as 2 GELU(a), so layer-2 and layer-3 weights are
+// stored halved (exact in bf16).  b2, b3 FP32.
 struct MlpDev {
   uint32_t w1f[8][32][2];
   uint32_t w2f[8][4][32][2];
   uint32_t w3f[4][32][2];
-  float b1[kMlpH];
   float b2[kMlpH];
   float b3;
   float pad[3];

@@ -372,10 +372,10 @@ bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host) {
   for (int n = 0; n < kMlpH; ++n) {
     for (int k = 0; k < kMlpIn; ++k)
       frag_put(h.w1f[n >> 3][frag_lane(k, n)][frag_reg(k)], k, to_bf16(W1[k * kMlpH + n]));
+    frag_put(h.w1f[n >> 3][frag_lane(kMlpIn, n)][frag_reg(kMlpIn)], kMlpIn, to_bf16(b1[n]));
     for (int k = 0; k < kMlpH; ++k)
       frag_put(h.w2f[n >> 3][k >> 4][frag_lane(k, n)][frag_reg(k)], k,
                bf16_half(to_bf16(W2[k * kMlpH + n])));
-    h.b1[n] = b1[n];
     h.b2[n] = b2[n];
   }
   for (int k = 0; k < kMlpH; ++k)
@@ -406,10 +406,10 @@ bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host) {
   for (int n = 0; n < kMlpH; ++n) {
     for (int k = 0; k < kMlpIn; ++k)
       W1[k * kMlpH + n] = from_bf16(frag_get(h.w1f[n >> 3][frag_lane(k, n)][frag_reg(k)], k));
+    b1[n] = from_bf16(frag_get(h.w1f[n >> 3][frag_lane(kMlpIn, n)][frag_reg(kMlpIn)], kMlpIn));
     for (int k = 0; k < kMlpH; ++k)
       W2[k * kMlpH + n] =
           2.0f * from_bf16(frag_get(h.w2f[n >> 3][k >> 4][frag_lane(k, n)][frag_reg(k)], k));
-    b1[n] = h.b1[n];
     b2[n] = h.b2[n];
   }
   for (int k = 0; k < kMlpH; ++k)

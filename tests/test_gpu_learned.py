@@ -9,9 +9,9 @@ Bars:
   * the learned walk against the oracle's FP64 evaluation with the same
     bf16-rounded weights: within 2 % of the largest network contribution
     (learned walk minus monopole walk) plus 1e-5 of the potential -- the
-    tensor-core path rounds the features and the hidden activations to bf16
-    (8 significant bits, relative 2^-9 each, through two 64-wide layers) and
-    takes the GELU's tanh from the SFU's bf16 approximation, so each node's
+    tensor-core path rounds the features, b1 and the hidden activations to
+    bf16 (8 significant bits, relative 2^-9 each, through two 64-wide layers)
+    and evaluates the GELU in bf16 pairs with the SFU's tanh, so each node's
     correction carries about 1 % error; corrections of different nodes can cancel in a cell, so
     the bound scales with their size, not with a cell's net correction;
   * what the trained network gains: smaller max error against the direct sum
@@ -117,3 +117,30 @@ def test_trained_network_beats_the_plain_walk_at_the_same_theta():
     err_l = np.abs(phi_l[tg] / d - 1).max()
     err_p = np.abs(phi_p[tg] / d - 1).max()
     assert err_l < 0.5 * err_p, (err_l, err_p)
+
+
+def test_learned_walk_in_a_graph_and_a_batch():
+    """The learned walk replayed as a CUDA graph (bh_solve_graph) and inside a
+    batch of fields gives the same potentials as bh_potential per field."""
+    wts = L.init_weights(5)
+    fields = [_field(), mg.maclaurin(base_level=1, extra_levels=2, a1=0.15, e=0.6)]
+    single = []
+    for f in fields:
+        s = B.Solver(learned=True)
+        s.build(f.mesh.level, f.mesh.ijk,
+                torch.as_tensor(f.density.reshape(-1).astype(np.float32)).cuda())
+        s.set_mlp(wts)
+        single.append(s.potential(0.8).cpu().numpy())
+    nb, level, ijk, lo, ln, rho = mg.concat_fields(fields)
+    st = torch.cuda.Stream()
+    s = B.Solver(learned=True, stream=st)
+    d_rho = torch.as_tensor(rho.astype(np.float32)).cuda()
+    s.build_batch(nb, level, ijk, d_rho, lo, ln)
+    s.set_mlp(wts)
+    out = torch.empty(d_rho.numel(), device="cuda")
+    with torch.cuda.stream(st):
+        s.solve_graph(d_rho, 0.8, 1.0, out)
+        s.solve_graph(d_rho, 0.8, 1.0, out)
+    st.synchronize()
+    got = out.cpu().numpy()
+    assert np.array_equal(got, np.concatenate(single))
