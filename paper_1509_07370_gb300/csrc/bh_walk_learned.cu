@@ -26,7 +26,8 @@
 namespace bhg {
 namespace {
 
-constexpr int kLWarps = 8;      // warps per CTA (one block of 512 cells)
+constexpr int kLWarps = 8;      // warps per CTA (one block of 512 cells); 3 CTAs per SM
+                                // (80 registers, 72 KB of shared memory each)
 constexpr int kQRows = 128;     // queue capacity per warp (rows)
 constexpr int kQFlush = 64;     // evaluate once this many rows are queued
 constexpr int kXWords = 12;     // row stride of the queued features: 24 bf16 = 48 bytes
@@ -158,7 +159,7 @@ __device__ __forceinline__ void evaluate(const MlpDev &W, WarpQueue &Q, int n, i
 }
 
 template <bool KAHAN>
-__global__ void __launch_bounds__(kLWarps * 32, 2)
+__global__ void __launch_bounds__(kLWarps * 32, 3)
     k_walk_learned(unsigned nunits, const WalkRec *__restrict__ rec,
                    const WalkQuad *__restrict__ qrec, const float2 *__restrict__ aux,
                    const int4 *__restrict__ blk, const int *__restrict__ orig,
