@@ -10,7 +10,9 @@ its monopole.  Everything runs in the library's own kernels:
     optimiser steps.
 Training fields: homogeneous oblate spheroids (the Maclaurin family of the
 accuracy test) with seeded semi-axis a1 in [0.12, 0.3] and eccentricity in
-[0.3, 0.95], on meshes of 16^3 cells refined twice at the surface.
+[0.3, 0.95], on meshes of 32^3 cells refined twice at the surface; half of
+each field's targets are random cells, half lie in its densest blocks (where
+the walk's largest errors are).
 """
 from __future__ import annotations
 
@@ -26,7 +28,7 @@ def training_field(seed: int) -> mg.Workload:
     rng = np.random.Generator(np.random.PCG64(seed))
     a1 = float(rng.uniform(0.12, 0.3))
     e = float(rng.uniform(0.3, 0.95))
-    return mg.maclaurin(base_level=1, extra_levels=2, a1=a1, e=e, rho_out=1e-4)
+    return mg.maclaurin(base_level=2, extra_levels=2, a1=a1, e=e, rho_out=1e-4)
 
 
 def init_weights(seed: int = 0) -> np.ndarray:
@@ -40,13 +42,27 @@ def init_weights(seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
+def dense_cells(density: np.ndarray, nblocks: int = 8) -> np.ndarray:
+    """Cell indices of the densest blocks (by mean density)."""
+    mean = density.reshape(-1, 512).mean(axis=1)
+    top = np.argsort(-mean, kind="stable")[:nblocks]
+    return (top[:, None] * 512 + np.arange(512)[None, :]).reshape(-1)
+
+
 def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: int,
-             cap: int = 1 << 20):
-    """(features, z) of the accepted pairs of `ntargets` random cells."""
+             cap: int = 1 << 20, dense=None):
+    """(features, z) of the accepted pairs of `ntargets` cells: random ones,
+    or half random and half drawn from `dense` (cell indices) if given."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
-    tg = torch.as_tensor(rng.choice(ncells, min(ntargets, ncells), replace=False),
-                         dtype=torch.int64, device=solver.device)
+    n = min(ntargets, ncells)
+    if dense is None:
+        cells = rng.choice(ncells, n, replace=False)
+    else:
+        cells = np.unique(np.concatenate([rng.choice(ncells, n - n // 2, replace=False),
+                                          rng.choice(dense, min(n // 2, len(dense)),
+                                                     replace=False)]))
+    tg = torch.as_tensor(cells, dtype=torch.int64, device=solver.device)
     feat, eps, _ = solver.learn_pairs(theta, tg, cap)
     s = feat[:, 3]
     return feat, eps / (s * s)
@@ -63,17 +79,19 @@ def make_dataset(nfields: int = 200, theta: float = 0.8, targets_per_field: int 
         s.build(w.mesh.level, w.mesh.ijk,
                 torch.as_tensor(w.density.reshape(-1), dtype=torch.float32,
                                 device=s.device))
-        x, z = pairs_of(s, w.ncells, theta, targets_per_field, seed0 + 100000 + i)
+        x, z = pairs_of(s, w.ncells, theta, targets_per_field, seed0 + 100000 + i,
+                        dense=dense_cells(w.density))
         xs.append(x)
         zs.append(z)
         s.close()
     return torch.cat(xs), torch.cat(zs)
 
 
-def train(x, z, epochs: int = 8, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+def train(x, z, epochs: int = 16, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
           w0: np.ndarray | None = None, stream: int = 0):
-    """Adam on the mean squared error of MLP(x) against z; returns the FP32
-    weights and the per-epoch mean losses."""
+    """Adam on the mean squared error of MLP(x) against z, the learning rate
+    halved after half and after three quarters of the epochs; returns the
+    FP32 weights and the per-epoch mean losses."""
     import torch
     dev = x.device
     w = torch.as_tensor(init_weights(seed) if w0 is None else w0, device=dev).contiguous()
@@ -85,7 +103,8 @@ def train(x, z, epochs: int = 8, batch: int = 8192, lr: float = 2e-3, seed: int 
     n = z.numel()
     step = 0
     history = []
-    for _ in range(epochs):
+    for ep in range(epochs):
+        rate = lr * (0.5 if ep >= epochs // 2 else 1.0) * (0.5 if ep >= (3 * epochs) // 4 else 1.0)
         perm = torch.randperm(n, generator=gen).to(dev)
         tot = 0.0
         for b0 in range(0, n, batch):
@@ -93,7 +112,7 @@ def train(x, z, epochs: int = 8, batch: int = 8192, lr: float = 2e-3, seed: int 
             xb, zb = x[idx].contiguous(), z[idx].contiguous()
             bh.bh_mlp_grad(xb, zb, w, g, loss, stream)
             step += 1
-            bh.bh_mlp_adam(g, w, m, v, step, lr, stream)
+            bh.bh_mlp_adam(g, w, m, v, step, rate, stream)
             tot += float(loss.item()) * idx.numel()
         history.append(tot / n)
     return w.cpu().numpy(), history
