@@ -81,8 +81,13 @@ typedef struct {
   int learned;    /* 0 (default).  1: every accepted node's term M/d is
                      multiplied by (1 + s^2 y), y = MLP(pair features), with the
                      network set by bh_set_mlp and evaluated on the tensor
-                     cores (not in the paper; see bh_learn_pairs).  Needs the
-                     binary32 per-cell walk; excludes the quadrupole term. */
+                     cores by each warp as it walks (mma.sync, bf16 in, FP32
+                     accumulate).  2: the same walk and arithmetic with the
+                     rows of four warps evaluated together as 128-row tiles by
+                     tcgen05 (FP32 accumulators in tensor memory); the same
+                     results, slower on GB300 (the warps wait for each other).
+                     Not in the paper; see bh_learn_pairs.  Needs the binary32
+                     per-cell walk; excludes the quadrupole term. */
   int timing;     /* 0 (default).  1: bh_build, bh_build_batch, bh_update_density
                      and bh_potential bracket their device work with CUDA events
                      on the context's stream, for bh_stats (not while the
@@ -306,6 +311,15 @@ typedef struct {
  * Waits for the recorded events and copies 24 bytes from the device, so it
  * synchronises with the work it reports on.  BH_ERR_ARG on null pointers. */
 bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out);
+
+/* Evaluates the network set by bh_set_mlp on n rows of pair features
+ * (DEVICE FP32 x[n][10], the layout of bh_learn_pairs) into DEVICE FP32 y[n],
+ * on the tensor cores (tcgen05: bf16 operands in shared memory, FP32
+ * accumulators in tensor memory), with the same rounding as the learned walk:
+ * features, b1 and hidden activations in bf16, the GELU in bf16 pairs.  Not in
+ * the paper.  Synchronises the stream.  BH_ERR_STATE without a network;
+ * BH_ERR_DEVICE_TIMEOUT if a bounded wait for the tensor core gave up. */
+bh_status bh_mlp_eval(bh_ctx *ctx, int64_t n, const float *x, float *y);
 
 /* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
 const char *bh_last_error(const bh_ctx *ctx);

@@ -25,7 +25,7 @@ EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_update_density", "bh_sync_status", "bh_autotune", "bh_solve_graph",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
-            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_stats",
+            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats",
             "bh_last_error", "bh_destroy")
 
 
@@ -93,6 +93,7 @@ def load(build_if_needed: bool = True):
         lib.bh_set_mlp.argtypes = [P, P]
         lib.bh_get_mlp.argtypes = [P, P]
         lib.bh_stats.argtypes = [P, ctypes.POINTER(bh_stats_t)]
+        lib.bh_mlp_eval.argtypes = [P, ctypes.c_int64, P, P]
         lib.bh_last_error.argtypes = [P]
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
@@ -102,7 +103,7 @@ def load(build_if_needed: bool = True):
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
-                     "bh_set_mlp", "bh_get_mlp", "bh_stats"):
+                     "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -327,6 +328,17 @@ def bh_get_mlp(ctx) -> np.ndarray:
     return w
 
 
+def bh_mlp_eval(ctx, x, y) -> None:
+    """The context's network on DEVICE float32 features x[n, 10] -> y[n],
+    on the tensor cores (tcgen05)."""
+    import torch
+    if x.dim() != 2 or x.shape[1] != 10 or y.numel() != x.shape[0]:
+        raise ValueError("expected x[n, 10] and y[n]")
+    st = load().bh_mlp_eval(ctx, int(x.shape[0]), ctypes.c_void_p(_dev_ptr(x, torch.float32)),
+                            ctypes.c_void_p(_dev_ptr(y, torch.float32)))
+    _check(ctx, st, "bh_mlp_eval")
+
+
 def bh_stats(ctx) -> dict:
     """Tree sizes, device times of the last build / potential (timing option,
     else -1) and work totals of the last bh_walk_counts (else -1)."""
@@ -359,7 +371,7 @@ class Solver:
         o = bh_default_options()
         o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
         o.quadrupole = int(bool(quadrupole))
-        o.learned = int(bool(learned))
+        o.learned = int(learned)  # 1: mma.sync network in the walk; 2: tcgen05
         o.timing = int(bool(timing))
         self.options = o
         self.device = torch.device("cuda", device)
@@ -458,6 +470,14 @@ class Solver:
 
     def stats(self) -> dict:
         return bh_stats(self._ctx)
+
+    def mlp_eval(self, x):
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        bh_mlp_eval(self._ctx, x, y)
+        self._handoff(y)
+        return y
 
     def get_mlp(self):
         return bh_get_mlp(self._ctx)

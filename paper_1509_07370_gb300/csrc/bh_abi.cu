@@ -343,7 +343,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if ((o.precision != BH_PREC_F32 && o.precision != BH_PREC_F64) ||
       (o.criterion != BH_CRIT_PER_CELL && o.criterion != BH_CRIT_WARP_VOTE) ||
       (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1) ||
-      (o.learned != 0 && o.learned != 1) || (o.timing != 0 && o.timing != 1))
+      (o.learned < 0 || o.learned > 2) || (o.timing != 0 && o.timing != 1))
     return BH_ERR_ARG;
   // the learned walk is the binary32 per-cell walk, with the network in place
   // of the quadrupole term
@@ -361,6 +361,8 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
   if (cudaSetDevice(device) != cudaSuccess || bhg::prepare_learned_kernels() != cudaSuccess ||
+      bhg::prepare_mlp_tc_kernel() != cudaSuccess ||
+      bhg::prepare_learned_tc_kernel() != cudaSuccess ||
       cudaMalloc(&ctx->tree.d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->tree.h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
@@ -427,6 +429,8 @@ bh_status bh_sync_status(bh_ctx *ctx) {
   BH_CUDA(cudaStreamSynchronize(ctx->stream));
   if (t.h_flags[0] & bhg::kErrDensity)
     return fail(ctx, BH_ERR_ARG, "density has a negative or non-finite value");
+  if (t.h_flags[0] & bhg::kErrTimeout)
+    return fail(ctx, BH_ERR_DEVICE_TIMEOUT, "a bounded wait for the tensor core gave up");
   if (t.h_flags[0] & ~bhg::kErrDensity)
     return fail(ctx, BH_ERR_GEOMETRY, "device error flags 0x%x", t.h_flags[0]);
   return BH_OK;
@@ -481,7 +485,9 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   const bool timed = timing_mark(ctx, 2);
   if ((st = prepare(ctx, theta)) != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  if (ctx->opt.learned)
+  if (ctx->opt.learned == 2)
+    BH_CUDA(bhg::launch_walk_learned_tc(ctx->stream, ctx, G, out));
+  else if (ctx->opt.learned)
     BH_CUDA(bhg::launch_walk_learned(ctx->stream, ctx, G, out));
   else
     BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
@@ -686,9 +692,9 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
       if (cap == BH_OK && e == cudaSuccess && ctx->opt.learned && !ctx->d_mlp)
         cap = fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
       if (cap == BH_OK && e == cudaSuccess)
-        e = ctx->opt.learned
-                ? bhg::launch_walk_learned(s, ctx, G, out)
-                : bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
+        e = ctx->opt.learned == 2 ? bhg::launch_walk_learned_tc(s, ctx, G, out)
+            : ctx->opt.learned    ? bhg::launch_walk_learned(s, ctx, G, out)
+                                  : bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
                                    t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr,
                                    nullptr, t.wpc);
     }
@@ -795,7 +801,7 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
   b += t.quad_cap * (int64_t)sizeof(bhg::WalkQuad) + (t.d_q64 ? t.quad_cap * 48 : 0);
   b += t.nf_cap * (int64_t)(sizeof(int) + 2 * sizeof(double)) + (t.nf_cap ? 4 : 0);
   b += t.stage_in_bytes + t.stage_out_bytes + 4 * sizeof(unsigned);
-  if (ctx->d_mlp) b += sizeof(bhg::MlpDev);
+  if (ctx->d_mlp) b += sizeof(bhg::MlpDev) + sizeof(bhg::MlpTc) + sizeof(unsigned);
   if (ctx->d_counts) b += 3 * sizeof(unsigned long long);
   out->device_bytes = b;
   return BH_OK;
@@ -815,6 +821,8 @@ void bh_destroy(bh_ctx *ctx) {
   release(ctx->tree.d_stage_out);
   release(ctx->tree.d_flags);
   release(ctx->d_mlp);
+  release(ctx->d_mlp_tc);
+  release(ctx->d_tc_flag);
   release(ctx->d_counts);
   for (cudaEvent_t &e : ctx->ev)
     if (e) cudaEventDestroy(e);

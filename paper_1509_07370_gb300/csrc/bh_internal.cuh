@@ -53,6 +53,7 @@ enum : unsigned {
   kErrTiling = 4u,       // sorted blocks leave a gap or overlap
   kErrDensity = 8u,      // negative or non-finite density
   kErrIndex = 16u,       // a node index fell outside the allocation
+  kErrTimeout = 32u,     // a bounded wait for the tensor core gave up
 };
 
 struct __align__(32) WalkRec {
@@ -275,6 +276,32 @@ struct MlpDev {
   float pad[3];
 };
 
+// Weights of the tcgen05 evaluator (bh_mlp_eval), bf16 operands in the
+// canonical K-major layout without swizzle: element (r, k) of an operand with
+// K columns at byte tc_canon(r, k, K) (core matrices of 8 rows x 16 bytes).
+// b1: W1^T with b1 at input 10 (N = 64, K = 16); b2: W2^T halved (64 x 64);
+// b3: W3^T halved in row 0 of 16 (N = 16, K = 64).  The same bf16 values as
+// the walk's MlpDev.
+struct MlpTc {
+  uint16_t b1[64 * 16];
+  uint16_t b2[64 * 64];
+  uint16_t b3[16 * 64];
+  float bias2[kMlpH];
+  float bias3;
+  float pad[3];
+};
+__host__ __device__ constexpr int tc_canon(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// n rows of features x[n][10] -> y[n] on the tensor cores; flags[0] |= 1 if a
+// bounded wait gave up.
+cudaError_t launch_mlp_tc(cudaStream_t s, int64_t n, const float *x, const MlpTc *w, float *y,
+                          unsigned *flags);
+cudaError_t prepare_mlp_tc_kernel();
+// The learned walk with the network on tcgen05 (bh_walk_learned_tc.cu).
+cudaError_t prepare_learned_tc_kernel();
+cudaError_t launch_walk_learned_tc(cudaStream_t s, bh_ctx *ctx, double G, void *out);
+
 }  // namespace bhg
 
 // The context (shared by the C-ABI translation units).
@@ -284,6 +311,8 @@ struct bh_ctx {
   cudaStream_t stream = nullptr;
   bhg::Tree tree;
   bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
+  bhg::MlpTc *d_mlp_tc = nullptr;   // the same network for bh_mlp_eval
+  unsigned *d_tc_flag = nullptr;    // time-out flag of bh_mlp_eval
   // statistics (bh_stats): events of the timing option (build start/end,
   // potential start/end), theta of the last potential, device totals of the
   // last bh_walk_counts

@@ -381,15 +381,51 @@ bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host) {
   for (int k = 0; k < kMlpH; ++k)
     frag_put(h.w3f[k >> 4][frag_lane(k, 0)][frag_reg(k)], k, bf16_half(to_bf16(W3[k])));
   h.b3 = b3[0];
+  // the same bf16 values in the tcgen05 evaluator's canonical layout
+  MlpTc c;
+  std::memset(&c, 0, sizeof(c));
+  auto put = [](uint16_t *base, int byte_off, uint16_t v) { base[byte_off / 2] = v; };
+  for (int n = 0; n < kMlpH; ++n) {
+    for (int k = 0; k < kMlpIn; ++k) put(c.b1, tc_canon(n, k, 16), to_bf16(W1[k * kMlpH + n]));
+    put(c.b1, tc_canon(n, kMlpIn, 16), to_bf16(b1[n]));
+    for (int k = 0; k < kMlpH; ++k)
+      put(c.b2, tc_canon(n, k, 64), bf16_half(to_bf16(W2[k * kMlpH + n])));
+    c.bias2[n] = b2[n];
+  }
+  for (int k = 0; k < kMlpH; ++k) put(c.b3, tc_canon(0, k, 64), bf16_half(to_bf16(W3[k])));
+  c.bias3 = b3[0];
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
-  if (!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) {
+  if ((!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) ||
+      (!ctx->d_mlp_tc && cudaMalloc(&ctx->d_mlp_tc, sizeof(MlpTc)) != cudaSuccess) ||
+      (!ctx->d_tc_flag && cudaMalloc(&ctx->d_tc_flag, sizeof(unsigned)) != cudaSuccess)) {
     cudaGetLastError();
     return ctx_fail(ctx, BH_ERR_OOM, "bh_set_mlp: no device memory");
   }
-  if (cudaMemcpy(ctx->d_mlp, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(ctx->d_mlp, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->d_mlp_tc, &c, sizeof(c), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     return ctx_fail(ctx, BH_ERR_CUDA, "bh_set_mlp: copy failed");
   }
+  return BH_OK;
+}
+
+bh_status bh_mlp_eval(bh_ctx *ctx, int64_t n, const float *x, float *y) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->d_mlp_tc) return ctx_fail(ctx, BH_ERR_STATE, "bh_mlp_eval: call bh_set_mlp first");
+  if (n < 0 || (n > 0 && (!x || !y))) return ctx_fail(ctx, BH_ERR_ARG, "bh_mlp_eval: bad arguments");
+  if (n == 0) return BH_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
+  unsigned flag = 0;
+  if (cudaMemsetAsync(ctx->d_tc_flag, 0, sizeof(unsigned), ctx->stream) != cudaSuccess ||
+      launch_mlp_tc(ctx->stream, n, x, ctx->d_mlp_tc, y, ctx->d_tc_flag) != cudaSuccess ||
+      cudaMemcpyAsync(&flag, ctx->d_tc_flag, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(ctx, BH_ERR_CUDA, "bh_mlp_eval: %s", "launch failed");
+  }
+  if (flag) return ctx_fail(ctx, BH_ERR_DEVICE_TIMEOUT, "bh_mlp_eval: a tensor-core wait gave up");
   return BH_OK;
 }
 

@@ -144,3 +144,46 @@ def test_learned_walk_in_a_graph_and_a_batch():
     st.synchronize()
     got = out.cpu().numpy()
     assert np.array_equal(got, np.concatenate(single))
+
+
+@pytest.mark.parametrize("n", [1, 128, 1000])
+def test_tensor_core_network_matches_oracle(n):
+    """bh_mlp_eval (tcgen05, bf16 operands, FP32 accumulators in tensor
+    memory) against the oracle's FP64 forward pass with the same bf16
+    weights: within 2 % of the largest |y| (bf16 features and activations,
+    bf16 GELU), on 1 row, one full 128-row tile and a ragged 1,000 rows."""
+    rng = np.random.default_rng(n)
+    w = L.init_weights(11) + rng.normal(0, 0.05, B.MLP_NW).astype(np.float32)
+    x = rng.normal(0, 1, (n, 10)).astype(np.float32)
+    s = B.Solver(learned=True)
+    s.set_mlp(w)
+    y = s.mlp_eval(torch.as_tensor(x).cuda()).cpu().numpy()
+    wb = s.get_mlp().astype(np.float64)
+    xb = torch.as_tensor(x).to(torch.bfloat16).double().numpy()   # the features it sees
+    ref = O.mlp_forward(wb, xb)[0]
+    assert np.all(np.isfinite(y))
+    assert np.abs(y - ref).max() <= 0.02 * np.abs(ref).max() + 1e-6
+
+
+def test_tensor_core_learned_walk_matches_the_warp_level_one_and_the_oracle():
+    """The learned walk with the network on tcgen05 (learned = 2): the same
+    per-row arithmetic as the mma.sync walk up to FP32 accumulation order,
+    so within 1e-5 of it per cell; and within the oracle bar."""
+    w = _field()
+    wts = L.init_weights(4)
+    rho = torch.as_tensor(w.density.reshape(-1).astype(np.float32)).cuda()
+    phis = []
+    for mode in (1, 2):
+        s = B.Solver(learned=mode)
+        s.build(w.mesh.level, w.mesh.ijk, rho)
+        s.set_mlp(wts)
+        phis.append(s.potential(0.8).cpu().numpy())
+        s.sync_status()
+        wb = s.get_mlp().astype(np.float64)
+    assert np.all(np.abs(phis[1] / phis[0] - 1.0) <= 1e-5)
+    t = O.Tree(w.mesh.level, w.mesh.ijk, w.density.astype(np.float32).astype(np.float64))
+    tg = np.random.default_rng(6).choice(w.ncells, 600, replace=False)
+    learned = t.walk_learned(0.8, wb, targets=tg)
+    mono = t.walk(0.8, targets=tg)[0]
+    corr = np.abs(learned - mono)
+    assert np.all(np.abs(phis[1][tg] - learned) <= 0.02 * corr.max() + 1e-5 * np.abs(learned))
