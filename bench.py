@@ -621,6 +621,24 @@ def build_roofline(ncells, nnodes, quad, build_ms):
             "frac": gbs / peak, "note": "limited by FP64 arithmetic, not by HBM"}
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over all ranks (the slowest rank's time); the value
+    itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, steps, total_ms):
+    """Whole-job units per second: every rank solves its own replica, the job
+    takes as long as its slowest rank."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def measured_peak(key):
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
@@ -671,12 +689,8 @@ def main():
                                              args.warmup, flush, stream, clk)
     if world > 1:
         dist.barrier()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(float(np.sum(step_ms)), dev)
+    value = job_rate(world, n, args.steps, total_ms)
     phi_gpu = out.double().cpu().numpy()
 
     # algorithmic work of the walk (untimed): per-cell counts from the library
@@ -709,12 +723,8 @@ def main():
         psteps = max(5, args.steps // 3)
         p_step, p_build, p_walk = timed_steps(psolver, mesh, d_rho, args.plain_theta, pout,
                                               psteps, args.warmup, flush, stream)
-        p_total = float(np.sum(p_step))
-        if world > 1:
-            t = torch.tensor([p_total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            p_total = float(t.item())
-        p_value = world * n * psteps / (p_total * 1e-3)
+        p_total = max_over_ranks(float(np.sum(p_step)), dev)
+        p_value = job_rate(world, n, psteps, p_total)
         pi, pt, pc, pflops = work(psolver, args.plain_theta, False)
         phi_plain = pout.double().cpu().numpy()
         plain = {"theta": args.plain_theta, "walk": "binary32, Kahan sum, per-cell, monopole",
@@ -743,12 +753,8 @@ def main():
             t0 = time.perf_counter()
             host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
             ts.append(time.perf_counter() - t0)
-        e2e_s = float(np.sum(ts))
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n * args.steps / e2e_s, "unit": "cells/s",
+        e2e_s = max_over_ranks(float(np.sum(ts)), dev)
+        e2e = {"value": job_rate(world, n, args.steps, e2e_s * 1e3), "unit": "cells/s",
                "h2d_bytes_per_step": int(rho32.nbytes + mesh.level.nbytes + mesh.ijk.nbytes),
                "d2h_bytes_per_step": int(h_out.nbytes)}
         host_solver.close()
