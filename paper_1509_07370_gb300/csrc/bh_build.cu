@@ -303,6 +303,13 @@ __device__ __forceinline__ Moment finish(double M, double Sx, double Sy, double 
   return r;
 }
 
+// (i + 1/2) 2^-level, the centre coordinate of cube i at `level` in box units:
+// 2i + 1 < 2^22 and level <= 21, so it is formed exactly in binary32 and
+// widened (the same value as the FP64 expression, without FP64 operations).
+__device__ __forceinline__ double centre_coord(int i, int level) {
+  return (double)__fmul_rn((float)(2 * i + 1), pow2f(-(level + 1)));
+}
+
 __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m,
                                             int64_t skip) {
   WalkRec w;
@@ -453,9 +460,9 @@ __global__ void __launch_bounds__(kBlockThreads)
     if (!(r >= 0.0) || isinf(r)) bad = true;
     const int cx = i & 7, cy = (i >> 3) & 7, cz = i >> 6;
     const int m = (int)(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
-    const double ux = __dmul_rn((double)(8 * B.y + cx) + 0.5, hs);
-    const double uy = __dmul_rn((double)(8 * B.z + cy) + 0.5, hs);
-    const double uz = __dmul_rn((double)(8 * B.w + cz) + 0.5, hs);
+    const double ux = centre_coord(8 * B.y + cx, lc);
+    const double uy = centre_coord(8 * B.z + cy, lc);
+    const double uz = centre_coord(8 * B.w + cz, lc);
     const double mass = __dmul_rn(r, vol);
     const double mass_u = mass * inv_unit;
     cm[m] = mass;
@@ -474,10 +481,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   if (t < 64) {  // nodes at level lb+2: q = 8p + r, children = cells 8q..8q+7
     const int q = t;
     const int qx = (int)compact3(q), qy = (int)compact3(q >> 1), qz = (int)compact3(q >> 2);
-    const double hg = pow2d(-(lb + 2));
-    const double cx = __dmul_rn((double)(4 * B.y + qx) + 0.5, hg);
-    const double cy = __dmul_rn((double)(4 * B.z + qy) + 0.5, hg);
-    const double cz = __dmul_rn((double)(4 * B.w + qz) + 0.5, hg);
+    const double cx = centre_coord(4 * B.y + qx, lb + 2);
+    const double cy = centre_coord(4 * B.z + qy, lb + 2);
+    const double cz = centre_coord(4 * B.w + qz, lb + 2);
     double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
 #pragma unroll
     for (int o = 0; o < 8; ++o)
@@ -510,10 +516,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   __syncthreads();
   if (t < 8) {  // nodes at level lb+1
     const int c = t;
-    const double hp = pow2d(-(lb + 1));
-    const double cx = __dmul_rn((double)(2 * B.y + (c & 1)) + 0.5, hp);
-    const double cy = __dmul_rn((double)(2 * B.z + ((c >> 1) & 1)) + 0.5, hp);
-    const double cz = __dmul_rn((double)(2 * B.w + ((c >> 2) & 1)) + 0.5, hp);
+    const double cx = centre_coord(2 * B.y + (c & 1), lb + 1);
+    const double cy = centre_coord(2 * B.z + ((c >> 1) & 1), lb + 1);
+    const double cz = centre_coord(2 * B.w + ((c >> 2) & 1), lb + 1);
     double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
 #pragma unroll
     for (int o = 0; o < 8; ++o)
@@ -546,10 +551,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
   __syncthreads();
   if (t == 0) {  // the block itself
-    const double hb = pow2d(-lb);
-    const double cx = __dmul_rn((double)B.y + 0.5, hb);
-    const double cy = __dmul_rn((double)B.z + 0.5, hb);
-    const double cz = __dmul_rn((double)B.w + 0.5, hb);
+    const double cx = centre_coord(B.y, lb);
+    const double cy = centre_coord(B.z, lb);
+    const double cz = centre_coord(B.w, lb);
     double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
 #pragma unroll
     for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
@@ -586,10 +590,9 @@ __device__ __forceinline__ void top_moment(int p, int level, const unsigned long
   const int64_t id = (int64_t)prestart[p] + (level - j0);
   const unsigned long long kp = key[p];
   const int sh = kKeyLevels - level;
-  const double hl = pow2d(-level);
-  const double cx = __dmul_rn((double)(compact3(kp) >> sh) + 0.5, hl);
-  const double cy = __dmul_rn((double)(compact3(kp >> 1) >> sh) + 0.5, hl);
-  const double cz = __dmul_rn((double)(compact3(kp >> 2) >> sh) + 0.5, hl);
+  const double cx = centre_coord((int)(compact3(kp) >> sh), level);
+  const double cy = centre_coord((int)(compact3(kp >> 1) >> sh), level);
+  const double cz = centre_coord((int)(compact3(kp >> 2) >> sh), level);
   double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
   int64_t c = id + 1;
   int64_t child[8];  // found by following skip pointers, kept for the quadrupoles
