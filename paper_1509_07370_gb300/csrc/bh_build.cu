@@ -19,9 +19,10 @@
 //      (k_top_nodes);
 //   4. one CTA per block reduces its 512 cells to 64, 8 and 1 nodes in shared
 //      memory (k_blocks), and one short launch per level reduces the top
-//      nodes, deepest level first (k_top_moments).  (A single CTA walking the
-//      levels with barriers was no faster: each level's cost is the latency
-//      of its FP64 chain, not the launch.)
+//      nodes, deepest level first (k_top_moments).  (Measured alternatives
+//      that were not faster: a single CTA walking the levels with barriers;
+//      child lists found by key searches in k_top_nodes instead of following
+//      skip pointers, which cost more there than they saved here.)
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
@@ -673,9 +674,17 @@ __global__ void __launch_bounds__(kBlockThreads)
     const T v = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = v > mx ? v : mx;
   }
-  if ((threadIdx.x & 31) == 0 && mx > T(0))
-    atomicMax(mmax + field,
-              (unsigned long long)__double_as_longlong(__dmul_rn((double)mx, vol)));
+  __shared__ T warp_max[kBlockThreads / 32];
+  if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // one atomic per block, and only when it can raise the max
+    for (int w = 1; w < kBlockThreads / 32; ++w) mx = warp_max[w] > mx ? warp_max[w] : mx;
+    if (mx > T(0)) {
+      const unsigned long long bits =
+          (unsigned long long)__double_as_longlong(__dmul_rn((double)mx, vol));
+      if (bits > *(volatile unsigned long long *)(mmax + field)) atomicMax(mmax + field, bits);
+    }
+  }
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
