@@ -429,7 +429,9 @@ def batched_arm(args):
                              "value": n / (u_ms * 1e-3), "ms_per_step": u_ms,
                              "speedup": value / (n / (u_ms * 1e-3))}},
             "clocks": clk.summary(), "e2e": e2e,
-            "gpu_launches": (3 + s.tree_size()[2] - 3) * args.steps}
+            # per graph launch: largest-mass pass, k_blocks, one top-moment
+            # launch per block level above 0, opening radii, walk
+            "gpu_launches": (s.tree_size()[2] - 3 + 4) * args.steps}
     print(json.dumps(line), flush=True)
     for ps in solvers:
         ps.close()
@@ -602,7 +604,7 @@ def learned_arm(args):
                           **{k: v for k, v in res["same"].items() if k != "theta"},
                           "speedup": L_["value"] / res["same"]["value"]},
         "clocks": clocks, "e2e": e2e,
-        "gpu_launches": (6 + (maxlev - 3) + 2) * args.steps,
+        "gpu_launches": (7 + (maxlev - 3) + 1) * args.steps,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -712,7 +714,9 @@ def main():
     traffic = (captured_traffic(w.name, args.theta, "quadrupole" if quad else "monopole")
                if not args.vote else None)
     _, nn, maxlev = solver.tree_size()
-    launches_per_step = 6 + (maxlev - 3) + 2
+    # keys, sort, tiling, scan, top nodes, largest mass, blocks, one top-moment
+    # launch per block level (max block level = maxlev - 3), walk
+    launches_per_step = 7 + (maxlev - 3) + 1
 
     # the plain walk (monopole, per-cell) at the theta of equal accuracy
     plain = None
