@@ -36,6 +36,9 @@
  *     x = cell centre - R, computed here straight from that definition, and an
  *     accepted node contributes -G (M/d + (1/2) d^T Q d / d^5), d = r_t - R.
  *     The opening test is unchanged; cells carry no quadrupole.
+ *   - Periodic boundaries (App. A): the Ewald field replaces 1/d in every
+ *     term, tabulated and interpolated quadratically; see the section
+ *     "periodic boundaries" below.
  *   - Optional learned correction (not in the paper): each accepted node's
  *     term M/d is multiplied by (1 + s^2 y), y = MLP(x), where s = l/d and x
  *     holds ten features of the (target, node) pair (see pair_features); the
@@ -812,4 +815,266 @@ int or_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------ periodic boundaries -- */
+/*
+ * App. A: with periodic boundaries the contribution of a node (or a cell) of
+ * mass M to the potential of a cell becomes -G M f(r), f the Ewald field: the
+ * potential of a unit mass together with all its periodic copies.  In box
+ * units (period 1), splitting 1/r = erf(a r)/r + erfc(a r)/r and summing the
+ * smooth erf part over the copies in Fourier space (Eq. ewald), the field of
+ * a unit mass at the origin with the box's mean density subtracted (the
+ * periodic sum exists only for the density minus its mean) is
+ *   psi(r) =  sum_n erfc(a |r + n|) / |r + n|
+ *           + (1/pi) sum_{k != 0} exp(-pi^2 |k|^2 / a^2) / |k|^2 cos(2 pi k.r)
+ *           - pi / a^2
+ * with n and k integer triples whose components lie in [-N, N] (N is the
+ * paper's gpuEwaldSeriesN, App. B); the result does not depend on the split
+ * parameter a once N is large enough.  The walk uses psi(r) = 1/|r| + chi(r),
+ * chi smooth in the box around the origin; in chi the n = 0 real-space term
+ * is -erf(a |r|)/|r| (-2 a / sqrt(pi) at r = 0).
+ *
+ * Table.  The paper keeps the field on grids and interpolates it
+ * quadratically in the walk (App. A).  Here chi is tabulated on one grid over
+ * the octant [0, 1/2 + h]^3 (chi is even in every coordinate): points
+ * (i, j, k) h, h = 1/(2 ng), i, j, k = 0 .. ng + 1, stored at
+ * T[(k (ng + 2) + j) (ng + 2) + i].  At u = |displacement| (per component,
+ * minimum image, so u <= 1/2) each axis takes the grid index c nearest to
+ * u/h, clamped to [1, ng], f = u/h - c, and the three-point Lagrange weights
+ * f(f-1)/2, 1 - f^2, f(f+1)/2 of the points c-1, c, c+1; chi(u) is the sum
+ * of the 27 products of one weight per axis and the table value.
+ *
+ * Readings (the paper does not say): the mean density is subtracted; the
+ * opening test and the terms use the minimum-image displacement (each
+ * component wrapped into [-1/2, 1/2]); a cell also feels the periodic copies
+ * of its own mass, m chi(0); in the binary32 test the wrap is
+ *   dx = fl(t.x - fl(R.x));  dx > 0.5 -> fl(dx - 1),  dx < -0.5 -> fl(dx + 1)
+ * (both exact), then d2 as in the isolated test.
+ */
+#define EWALD_ALPHA 2.0
+
+/* psi(r) (chi_only = 0) or chi(r) = psi(r) - 1/|r| (chi_only = 1), FP64. */
+static double ewald_sum(const double r[3], double a, int N, int chi_only) {
+  const double pi = 3.14159265358979323846;
+  double real = 0.0, recip = 0.0;
+  for (int i = -N; i <= N; ++i)
+    for (int j = -N; j <= N; ++j)
+      for (int k = -N; k <= N; ++k) {
+        double x = r[0] + i, y = r[1] + j, z = r[2] + k;
+        double s = sqrt(x * x + y * y + z * z);
+        if (i == 0 && j == 0 && k == 0 && chi_only)
+          real += s > 0.0 ? -erf(a * s) / s : -2.0 * a / sqrt(pi);
+        else
+          real += erfc(a * s) / s;
+      }
+  for (int i = -N; i <= N; ++i)
+    for (int j = -N; j <= N; ++j)
+      for (int k = -N; k <= N; ++k) {
+        if (i == 0 && j == 0 && k == 0) continue;
+        double k2 = (double)(i * i + j * j + k * k);
+        double kr = i * r[0] + j * r[1] + k * r[2];
+        recip += exp(-pi * pi * k2 / (a * a)) / k2 * cos(2.0 * pi * kr);
+      }
+  return real + recip / pi - pi / (a * a);
+}
+
+/* psi or chi at n points r[3n] (box units), split parameter a, range N. */
+int or_ewald_sum(int64_t n, const double *r, double a, int N, int chi_only, double *out) {
+  if (n < 0 || !(a > 0.0) || N < 0) return OR_ERR_ARG;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int64_t q = 0; q < n; ++q) out[q] = ewald_sum(r + 3 * q, a, N, chi_only);
+  return OR_OK;
+}
+
+/* The table of chi (see above): (ng + 2)^3 values, a = EWALD_ALPHA. */
+int or_ewald_table(int ng, int N, double *T) {
+  if (ng < 2 || N < 1) return OR_ERR_ARG;
+  const int m = ng + 2;
+  const double h = 1.0 / (2.0 * ng);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+  for (int64_t q = 0; q < (int64_t)m * m * m; ++q) {
+    int i = (int)(q % m), j = (int)((q / m) % m), k = (int)(q / ((int64_t)m * m));
+    double r[3] = {i * h, j * h, k * h};
+    T[q] = ewald_sum(r, EWALD_ALPHA, N, 1);
+  }
+  return OR_OK;
+}
+
+/* Quadratic interpolation of the table at u (u >= 0 per component). */
+static double ewald_interp(const double *T, int ng, const double u[3]) {
+  const int m = ng + 2;
+  int c[3];
+  double w[3][3];
+  for (int a = 0; a < 3; ++a) {
+    double t = u[a] * (2.0 * ng);
+    int ci = (int)floor(t + 0.5);
+    if (ci < 1) ci = 1;
+    if (ci > ng) ci = ng;
+    double f = t - ci;
+    w[a][0] = 0.5 * f * (f - 1.0);
+    w[a][1] = 1.0 - f * f;
+    w[a][2] = 0.5 * f * (f + 1.0);
+    c[a] = ci;
+  }
+  double s = 0.0;
+  for (int kz = 0; kz < 3; ++kz)
+    for (int jy = 0; jy < 3; ++jy)
+      for (int ix = 0; ix < 3; ++ix)
+        s += w[2][kz] * w[1][jy] * w[0][ix] *
+             T[((int64_t)(c[2] - 1 + kz) * m + (c[1] - 1 + jy)) * m + (c[0] - 1 + ix)];
+  return s;
+}
+
+int or_ewald_interp(const double *T, int ng, int64_t n, const double *u, double *out) {
+  if (ng < 2 || n < 0) return OR_ERR_ARG;
+  for (int64_t q = 0; q < n; ++q) {
+    double v[3] = {fabs(u[3 * q]), fabs(u[3 * q + 1]), fabs(u[3 * q + 2])};
+    if (v[0] > 0.5 + 0.5 / ng || v[1] > 0.5 + 0.5 / ng || v[2] > 0.5 + 0.5 / ng)
+      return OR_ERR_ARG;
+    out[q] = ewald_interp(T, ng, v);
+  }
+  return OR_OK;
+}
+
+static double wrap64(double d) {
+  if (d > 0.5) return d - 1.0;
+  if (d < -0.5) return d + 1.0;
+  return d;
+}
+static float wrap32(float d) {
+  if (d > 0.5f) return d - 1.0f;
+  if (d < -0.5f) return d + 1.0f;
+  return d;
+}
+
+/* The binary32 test of Eq. 4 on the minimum-image displacement. */
+static int accept_f32_periodic(const onode *n, const float t[3], float inv_theta) {
+  float l = (float)ldexp(1.0, -n->level);
+  float s = l * inv_theta;
+  s = s + (float)n->delta;
+  float s2 = s * s;
+  float dx = wrap32(t[0] - (float)n->R[0]);
+  float dy = wrap32(t[1] - (float)n->R[1]);
+  float dz = wrap32(t[2] - (float)n->R[2]);
+  float d2 = fmaf(dx, dx, fmaf(dz, dz, dy * dy));
+  return d2 > s2;
+}
+
+/* M psi(r_t - R) with psi = 1/d + chi from the table (T) or from the sum
+ * (T == NULL, range N), minimum image; for the target's own cell (self) the
+ * copies only: M chi(0). */
+static double periodic_term(double M, const double tu[3], const double R[3], int self,
+                            const double *T, int ng, int N) {
+  double x[3] = {wrap64(tu[0] - R[0]), wrap64(tu[1] - R[1]), wrap64(tu[2] - R[2])};
+  if (self) x[0] = x[1] = x[2] = 0.0;
+  double chi;
+  if (T) {
+    double u[3] = {fabs(x[0]), fabs(x[1]), fabs(x[2])};
+    chi = ewald_interp(T, ng, u);
+  } else {
+    chi = ewald_sum(x, EWALD_ALPHA, N, 1);
+  }
+  if (self) return M * chi;
+  double d = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+  return M * (1.0 / d + chi);
+}
+
+typedef struct {
+  const otree *t;
+  int64_t self;
+  float tf[3];
+  double tu[3];
+  float inv_theta;
+  const double *T;
+  int ng;
+  neumaier sum;
+  int64_t n_int, n_test;
+} pwalk_state;
+
+static void walk_periodic(pwalk_state *w, int64_t id) {
+  const onode *n = &w->t->node[id];
+  if (n->child[0] < 0) {                      /* a leaf cell, or the target's own */
+    nm_add(&w->sum, periodic_term(n->M, w->tu, n->R, id == w->self, w->T, w->ng, 0));
+    if (id != w->self) w->n_int++;
+    return;
+  }
+  w->n_test++;
+  if (accept_f32_periodic(n, w->tf, w->inv_theta)) {
+    nm_add(&w->sum, periodic_term(n->M, w->tu, n->R, 0, w->T, w->ng, 0));
+    w->n_int++;
+    return;
+  }
+  for (int o = 0; o < 8; ++o) walk_periodic(w, n->child[o]);
+}
+
+/* Per-cell walk with periodic boundaries (App. A): minimum-image test and
+ * terms M (1/d + chi(d)) with chi interpolated from the table T (ng). */
+int or_walk_periodic(const void *p, double theta, double G, const double *T, int ng,
+                     int64_t ntargets, const int64_t *targets, double *phi, int64_t *n_int,
+                     int64_t *n_test, int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!check_theta(theta) || !isfinite(G) || !T || ng < 2) return OR_ERR_ARG;
+  int64_t ncell = (int64_t)t->nblocks * 512;
+  for (int64_t q = 0; q < ntargets; ++q)
+    if (targets[q] < 0 || targets[q] >= ncell) return OR_ERR_ARG;
+  float inv_theta = (float)(1.0 / theta);
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < ntargets; ++q) {
+    pwalk_state w;
+    memset(&w, 0, sizeof(w));
+    w.t = t;
+    w.self = t->leaf_of_cell[targets[q]];
+    w.inv_theta = inv_theta;
+    w.T = T;
+    w.ng = ng;
+    target_position(t, w.self, w.tu, w.tf);
+    walk_periodic(&w, 0);
+    phi[q] = scale * nm_value(&w.sum);
+    if (n_int) n_int[q] = w.n_int;
+    if (n_test) n_test[q] = w.n_test;
+  }
+  return OR_OK;
+}
+
+/* Direct periodic sum: Phi_t = -(G/L) (sum_{j != t} m_j psi(r_t - r_j)
+ * + m_t chi(0)), psi from the table T (ng) or, with T == NULL, from the
+ * Ewald sum itself (range N, split EWALD_ALPHA). */
+int or_direct_periodic(const void *p, double G, const double *T, int ng, int N,
+                       int64_t ntargets, const int64_t *targets, double *phi, int nthreads) {
+  const otree *t = (const otree *)p;
+  if (!isfinite(G) || (T && ng < 2) || (!T && N < 1)) return OR_ERR_ARG;
+  int64_t ncell = (int64_t)t->nblocks * 512;
+  for (int64_t q = 0; q < ntargets; ++q)
+    if (targets[q] < 0 || targets[q] >= ncell) return OR_ERR_ARG;
+  int64_t *leaf = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+  if (!leaf) return OR_ERR_OOM;
+  int64_t nl = 0;
+  for (int64_t id = 0; id < t->nnodes; ++id)
+    if (t->node[id].child[0] < 0) leaf[nl++] = id;
+  double scale = -G / t->L;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int64_t q = 0; q < ntargets; ++q) {
+    int64_t self = t->leaf_of_cell[targets[q]];
+    const double *tu = t->node[self].R;
+    neumaier s = {0.0, 0.0};
+    for (int64_t j = 0; j < nl; ++j) {
+      const onode *n = &t->node[leaf[j]];
+      nm_add(&s, periodic_term(n->M, tu, n->R, leaf[j] == self, T, ng, N));
+    }
+    phi[q] = scale * nm_value(&s);
+  }
+  free(leaf);
+  return OR_OK;
 }

@@ -75,6 +75,16 @@ def _load():
             lib.or_learn_pairs.restype = i64
             lib.or_walk_learned.argtypes = [P, dbl, dbl, P, i64, P, P, i32]
             lib.or_walk_learned.restype = i32
+            lib.or_ewald_sum.argtypes = [i64, P, dbl, i32, i32, P]
+            lib.or_ewald_sum.restype = i32
+            lib.or_ewald_table.argtypes = [i32, i32, P]
+            lib.or_ewald_table.restype = i32
+            lib.or_ewald_interp.argtypes = [P, i32, i64, P, P]
+            lib.or_ewald_interp.restype = i32
+            lib.or_walk_periodic.argtypes = [P, dbl, dbl, P, i32, i64, P, P, P, P, i32]
+            lib.or_walk_periodic.restype = i32
+            lib.or_direct_periodic.argtypes = [P, dbl, P, i32, i32, i64, P, P, i32]
+            lib.or_direct_periodic.restype = i32
             _lib = lib
     return _lib
 
@@ -225,6 +235,38 @@ class Tree:
             raise OracleError(st, "or_walk_learned")
         return phi
 
+    def walk_periodic(self, theta: float, G: float = 1.0, targets=None, threads: int = 0,
+                      ng: int = 64, nseries: int = 3):
+        """Per-cell walk with periodic boundaries (App. A): minimum-image
+        opening test, terms M (1/d + chi) with chi interpolated from the
+        Ewald table (ng, nseries).  Returns (phi, n_int, n_test)."""
+        T = ewald_table(ng, nseries)
+        t = self._targets(targets)
+        phi = np.empty(t.shape[0])
+        ni = np.empty(t.shape[0], np.int64)
+        nt = np.empty(t.shape[0], np.int64)
+        st = _load().or_walk_periodic(self._h, float(theta), float(G), _ptr(T), int(ng),
+                                      t.shape[0], _ptr(t), _ptr(phi), _ptr(ni), _ptr(nt),
+                                      int(threads))
+        if st != OR_OK:
+            raise OracleError(st, "or_walk_periodic")
+        return phi, ni, nt
+
+    def direct_periodic(self, G: float = 1.0, targets=None, threads: int = 0,
+                        ng: int | None = 64, nseries: int = 3) -> np.ndarray:
+        """Direct periodic potential: every other cell's mass times the Ewald
+        field psi, plus the copies of the cell's own mass.  psi from the table
+        (ng) or, with ng=None, from the Ewald sum itself (range nseries)."""
+        t = self._targets(targets)
+        phi = np.empty(t.shape[0])
+        T = ewald_table(ng, nseries) if ng else None
+        st = _load().or_direct_periodic(self._h, float(G), None if T is None else _ptr(T),
+                                        int(ng or 0), int(nseries), t.shape[0], _ptr(t),
+                                        _ptr(phi), int(threads))
+        if st != OR_OK:
+            raise OracleError(st, "or_direct_periodic")
+        return phi
+
     def direct(self, G: float = 1.0, targets=None, threads: int = 0) -> np.ndarray:
         """Direct O(N^2) potential (Eq. 2 without the 1/2) at the given cells."""
         t = self._targets(targets)
@@ -249,6 +291,52 @@ def direct_points(pos, m, G=1.0, targets=None) -> np.ndarray:
     if st != OR_OK:
         raise OracleError(st, "or_direct_points")
     return phi
+
+
+# ------------------------------------------------ periodic boundaries --
+EWALD_ALPHA = 2.0
+_tables: dict = {}
+
+
+def ewald_sum(r, alpha: float = EWALD_ALPHA, nseries: int = 3, chi: bool = False):
+    """Ewald field psi(r) of a unit mass in the unit-period box, mean density
+    subtracted (chi=True: psi - 1/|r|), at points r[..., 3], FP64."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    shape = r.shape[:-1]
+    r = r.reshape(-1, 3)
+    out = np.empty(r.shape[0])
+    st = _load().or_ewald_sum(r.shape[0], _ptr(r), float(alpha), int(nseries), int(bool(chi)),
+                              _ptr(out))
+    if st != OR_OK:
+        raise OracleError(st, "or_ewald_sum")
+    return out.reshape(shape)
+
+
+def ewald_table(ng: int = 64, nseries: int = 3) -> np.ndarray:
+    """chi on the (ng+2)^3 grid of the octant [0, 1/2 + h]^3, h = 1/(2 ng),
+    x fastest (cached per (ng, nseries))."""
+    key = (int(ng), int(nseries))
+    if key not in _tables:
+        T = np.empty((ng + 2) ** 3)
+        st = _load().or_ewald_table(int(ng), int(nseries), _ptr(T))
+        if st != OR_OK:
+            raise OracleError(st, "or_ewald_table")
+        _tables[key] = T
+    return _tables[key]
+
+
+def ewald_interp(u, ng: int = 64, nseries: int = 3) -> np.ndarray:
+    """chi at displacements u[..., 3] (|u_i| <= 1/2) by the table's quadratic
+    interpolation."""
+    T = ewald_table(ng, nseries)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    shape = u.shape[:-1]
+    u = u.reshape(-1, 3)
+    out = np.empty(u.shape[0])
+    st = _load().or_ewald_interp(_ptr(T), int(ng), u.shape[0], _ptr(u), _ptr(out))
+    if st != OR_OK:
+        raise OracleError(st, "or_ewald_interp")
+    return out.reshape(shape)
 
 
 def local_morton_order() -> np.ndarray:
