@@ -43,6 +43,14 @@ FLOP_PER_INTERACTION = 8        # 3 sub, 1 mul + 2 fma for d^2, 1 mul m*rsqrt, 1
 FLOP_PER_QUAD_INTERACTION = 20  # the above, with 9 ops for d^T Q d / 2 and 3 more for
                                 # rinv (M + q rinv^4) in place of the m*rsqrt product
 FLOP_PER_TEST = 7
+# periodic boundaries (App. A): the minimum-image wrap adds 3 ops per component
+# (the y and z ones shared by the x-neighbour pair: 6 per target); chi from the
+# table costs 3 axes x 11 ops (index, fraction, three weights; y and z shared
+# by the pair) + 39 for the weighted 27-point sum = 61 per target, plus 1 add
+FLOP_PER_TEST_PERIODIC = FLOP_PER_TEST + 6
+FLOP_PER_INTERACTION_PERIODIC = FLOP_PER_INTERACTION + 61 + 1
+FLOP_PER_CELL_WRAP = 6
+FLOP_PER_SELF_IMAGE = 61 + 1
 
 
 def parse():
@@ -60,6 +68,10 @@ def parse():
                     help="plain monopole nodes (default: with the quadrupole term)")
     ap.add_argument("--vote", action="store_true",
                     help="the paper's warp vote instead of the per-cell test")
+    ap.add_argument("--periodic", action="store_true",
+                    help="periodic boundaries (Ewald field, App. A); monopole nodes")
+    ap.add_argument("--ewald-grid", type=int, default=64,
+                    help="Ewald table points per half box (periodic)")
     ap.add_argument("--plain-theta", type=float, default=None,
                     help="theta of the plain monopole walk timed for vs_plain "
                          "(default 0.25; 0.4 for --workload learned)")
@@ -166,7 +178,8 @@ def captured_traffic(workload_name, theta, mode):
 
 
 # ------------------------------------------------------------ CPU oracle --
-def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None):
+def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, periodic=False,
+               ewald_grid=64):
     """Times the CPU oracle (tree + FP64 moments in full, walk on a sample of
     targets) and extrapolates to cells/s for the whole field."""
     from oracle import oracle as O
@@ -175,35 +188,65 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None):
     tree = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
     if quad:
         tree.quadrupoles()
+    if periodic:
+        O.ewald_table(ewald_grid)
     t_build = time.perf_counter() - t0
+
+    def walk(targets, threads=0):
+        if periodic:
+            return tree.walk_periodic(theta, targets=targets, threads=threads, ng=ewald_grid)
+        return tree.walk(theta, targets=targets, quad=quad, threads=threads)
+
     rng = np.random.default_rng(1234)
     n = w.ncells
     probe = rng.choice(n, min(n, 2000), replace=False)
-    tree.walk(theta, targets=probe[:64], quad=quad)      # start the OpenMP threads
+    walk(probe[:64])                                     # start the OpenMP threads
     t0 = time.perf_counter()
-    tree.walk(theta, targets=probe, quad=quad)
+    walk(probe)
     per = (time.perf_counter() - t0) / len(probe)
     k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
     tg = np.sort(rng.choice(n, k, replace=False))
     t0 = time.perf_counter()
-    ref, ni, nt = tree.walk(theta, targets=tg, quad=quad)
+    ref, ni, nt = walk(tg)
     t_walk = time.perf_counter() - t0
     t_step = t_build + t_walk * (n / k)
     t0 = time.perf_counter()
-    tree.walk(theta, targets=probe, quad=quad, threads=1)
+    walk(probe, threads=1)
     per1 = (time.perf_counter() - t0) / len(probe)
+    kind = "periodic (Ewald table), monopole" if periodic else (
+        "quadrupole" if quad else "monopole")
     out = {"value": n / t_step, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
            "value_1core": n / (t_build + per1 * n),
            "sample": f"tree+FP64 moments of all {n} cells; per-cell walk of {k} random cells "
-                     f"(seed 1234, {'quadrupole' if quad else 'monopole'}, theta {theta}) "
+                     f"(seed 1234, {kind}, theta {theta}) "
                      f"extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s; "
                      f"value_1core: the walk of {len(probe)} cells on one thread"}
-    if phi_gpu is not None:
+    if phi_gpu is not None and periodic:
+        # the periodic field has zero mean and changes sign: errors relative
+        # to its largest magnitude; a smaller direct sample (each direct
+        # periodic term interpolates the table)
+        dt = direct_targets(w, rng, nrandom=200, ndense=1)
+        t0 = time.perf_counter()
+        d = tree.direct_periodic(targets=dt, ng=ewald_grid)
+        t_direct = time.perf_counter() - t0
+        wd = walk(dt)[0]
+        out["accuracy"] = {
+            "max_err_over_max_abs_vs_oracle_walk":
+                float(np.max(np.abs(phi_gpu[tg] - ref)) / np.max(np.abs(ref))),
+            "max_err_over_max_abs_vs_direct":
+                float(np.max(np.abs(phi_gpu[dt] - d)) / np.max(np.abs(d))),
+            "oracle_walk_max_err_over_max_abs_vs_direct":
+                float(np.max(np.abs(wd - d)) / np.max(np.abs(d))),
+            "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
+            "direct_sample": "200 random cells (seed 1234) + every cell of the densest block; "
+                             "direct periodic sum with the same Ewald table",
+            "direct_cells_per_s": len(dt) / t_direct}
+    elif phi_gpu is not None:
         dt = direct_targets(w, rng)
         t0 = time.perf_counter()
         d = tree.direct(targets=dt)
         t_direct = time.perf_counter() - t0
-        wd = tree.walk(theta, targets=dt, quad=quad)[0]
+        wd = walk(dt)[0]
         out["accuracy"] = {
             "max_rel_vs_oracle_walk": float(np.max(np.abs(phi_gpu[tg] / ref - 1.0))),
             "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[dt] / d - 1.0))),
@@ -676,11 +719,17 @@ def main():
     w = workload(args.workload)
     n = w.ncells
     mesh = w.mesh
-    quad = not args.monopole
+    periodic = args.periodic
+    quad = not args.monopole and not periodic
+    if periodic and args.vote:
+        raise SystemExit("--periodic runs the per-cell walk (no --vote)")
     crit = bh.BH_CRIT_WARP_VOTE if args.vote else bh.BH_CRIT_PER_CELL
     rho32 = np.ascontiguousarray(w.density.reshape(-1), dtype=np.float32)
     stream = torch.cuda.Stream(dev)
-    solver = bh.Solver(criterion=crit, quadrupole=quad, device=local, stream=stream)
+    solver = bh.Solver(criterion=crit, quadrupole=quad, periodic=periodic, device=local,
+                       stream=stream)
+    if periodic and args.ewald_grid != 64:
+        solver.set_ewald(args.ewald_grid, 3)
     d_rho = torch.as_tensor(rho32, device=dev)
     out = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
@@ -704,6 +753,9 @@ def main():
         n_cell = int(nc.sum(dtype=torch.int64).item())
         per_node = FLOP_PER_QUAD_INTERACTION if with_quad else FLOP_PER_INTERACTION
         flops = FLOP_PER_INTERACTION * n_cell + per_node * (n_int - n_cell) + FLOP_PER_TEST * n_test
+        if s.options.periodic:
+            flops = (FLOP_PER_INTERACTION_PERIODIC * n_int + FLOP_PER_CELL_WRAP * n_cell
+                     + FLOP_PER_TEST_PERIODIC * n_test + FLOP_PER_SELF_IMAGE * n)
         return n_int, n_test, n_cell, flops
 
     n_int, n_test, n_cell, flops = work(solver, args.theta, quad)
@@ -713,7 +765,7 @@ def main():
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
     traffic = (captured_traffic(w.name, args.theta, "quadrupole" if quad else "monopole")
-               if not args.vote else None)
+               if not (args.vote or periodic) else None)
     _, nn, maxlev = solver.tree_size()
     # keys, sort, tiling, scan, top nodes, largest mass, blocks, one top-moment
     # launch per block level (max block level = maxlev - 3), walk
@@ -722,7 +774,7 @@ def main():
     # the plain walk (monopole, per-cell) at the theta of equal accuracy
     plain = None
     phi_plain = None
-    if not args.no_plain:
+    if not args.no_plain and not periodic:
         psolver = bh.Solver(device=local, stream=stream)
         pout = torch.empty(n, dtype=torch.float32, device=dev)
         psteps = max(5, args.steps // 3)
@@ -748,7 +800,10 @@ def main():
         pinned = (torch.from_numpy(rho32).pin_memory(),
                   torch.empty(n, dtype=torch.float32).pin_memory())
         h_rho, h_out = pinned[0].numpy(), pinned[1].numpy()
-        host_solver = bh.Solver(criterion=crit, quadrupole=quad, device=local, stream=stream)
+        host_solver = bh.Solver(criterion=crit, quadrupole=quad, periodic=periodic,
+                                device=local, stream=stream)
+        if periodic and args.ewald_grid != 64:
+            host_solver.set_ewald(args.ewald_grid, 3)
         for _ in range(max(1, args.warmup)):
             host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
         ts = []
@@ -767,7 +822,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_leg(w, args.theta, args.cpu_seconds, phi_gpu, quad=quad,
-                         plain=(phi_plain, args.plain_theta) if phi_plain is not None else None)
+                         plain=(phi_plain, args.plain_theta) if phi_plain is not None else None,
+                         periodic=periodic, ewald_grid=args.ewald_grid)
 
     if rank == 0:
         line = {
@@ -778,6 +834,8 @@ def main():
             "config": {"workload": w.name, "cells": n, "nodes": nn, "theta": args.theta,
                        "walk": "binary32, Kahan sum, "
                                + ("warp vote (paper)" if args.vote else "per-cell opening test")
+                               + (f", periodic boundaries (Ewald table {args.ewald_grid}, "
+                                  "series 3)" if periodic else "")
                                + (", quadrupole nodes" if quad else ", monopole nodes"),
                        "moments": "f64", "density_input": "f32",
                        "l2": "flushed between steps (256 MiB write)",

@@ -92,7 +92,19 @@ typedef struct {
                      and bh_potential bracket their device work with CUDA events
                      on the context's stream, for bh_stats (not while the
                      stream is being captured into a graph). */
-  int reserved[2];
+  int periodic;   /* 0 (default): isolated boundaries (Eq. 2).  1: periodic
+                     boundaries (App. A): every node's or cell's term M/d
+                     becomes M psi(d), psi the Ewald field of a unit mass and
+                     all its periodic copies with the mean density
+                     subtracted, psi = 1/d + chi(d), chi interpolated from a
+                     table (see bh_set_ewald); the opening test and the terms
+                     use the minimum-image displacement (each box-unit
+                     component wrapped into [-1/2, 1/2]:
+                     dx > 0.5 -> fl(dx - 1), dx < -0.5 -> fl(dx + 1)), and
+                     every cell also gets its own mass times chi(0), the
+                     field of its periodic copies.  Needs the binary32
+                     per-cell walk without the quadrupole or learned options. */
+  int reserved[1];
 } bh_options;
 
 /* Fills *opt with the defaults: F32 walk, per-cell test, Kahan summation,
@@ -320,6 +332,33 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out);
  * the paper.  Synchronises the stream.  BH_ERR_STATE without a network;
  * BH_ERR_DEVICE_TIMEOUT if a bounded wait for the tensor core gave up. */
 bh_status bh_mlp_eval(bh_ctx *ctx, int64_t n, const float *x, float *y);
+
+/* ---- periodic boundaries (App. A) ----------------------------------------
+ * The Ewald field of a unit mass in the box (box units, period 1), mean
+ * density subtracted, split as 1/r = erf(a r)/r + erfc(a r)/r with a = 2:
+ *   psi(r) = sum_n erfc(a|r+n|)/|r+n|
+ *          + (1/pi) sum_{k!=0} exp(-pi^2 |k|^2/a^2)/|k|^2 cos(2 pi k.r) - pi/a^2
+ * (n, k integer triples with components in [-n_series, n_series], the
+ * paper's gpuEwaldSeriesN), and chi(r) = psi(r) - 1/|r|, smooth around the
+ * origin.  The table holds chi at the points (i, j, k) h, h = 1/(2 n_grid),
+ * i, j, k = 0 .. n_grid + 1 (the octant [0, 1/2 + h]^3; chi is even in each
+ * coordinate).  At u = |minimum-image displacement| the walk interpolates
+ * quadratically: per axis c = floor(u/h + 1/2) clamped to [1, n_grid],
+ * f = u/h - c, weights f(f-1)/2, 1 - f^2, f(f+1)/2 for the points c-1, c,
+ * c+1; chi(u) = sum of the 27 weight products times the table values. */
+
+/* Computes the table on the device (FP64 sums, stored as binary32) for the
+ * periodic walk of this context; a context created with the periodic
+ * option starts with n_grid = 64, n_series = 3 (interpolation error about
+ * 3e-6 of chi(0), series converged to 1e-13).  n_grid in [2, 512],
+ * n_series in [1, 8], else BH_ERR_ARG.  Enqueued on the context's stream. */
+bh_status bh_set_ewald(bh_ctx *ctx, int n_grid, int n_series);
+
+/* chi at n box-unit displacements (DEVICE FP32 r[n][3], each component in
+ * [-1/2, 1/2]) into DEVICE FP32 chi[n], by the walk's interpolation of the
+ * table.  BH_ERR_STATE without a table (context not periodic and no
+ * bh_set_ewald call); enqueued on the context's stream. */
+bh_status bh_ewald_eval(bh_ctx *ctx, int64_t n, const float *r, float *chi);
 
 /* Reason for the last failure on ctx ("" if none).  Valid until the next call. */
 const char *bh_last_error(const bh_ctx *ctx);

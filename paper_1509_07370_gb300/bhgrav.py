@@ -26,14 +26,14 @@ EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
             "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats",
-            "bh_last_error", "bh_destroy")
+            "bh_set_ewald", "bh_ewald_eval", "bh_last_error", "bh_destroy")
 
 
 class bh_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("criterion", ctypes.c_int),
                 ("kahan", ctypes.c_int), ("quadrupole", ctypes.c_int),
                 ("learned", ctypes.c_int), ("timing", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("periodic", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class bh_stats_t(ctypes.Structure):
@@ -94,6 +94,8 @@ def load(build_if_needed: bool = True):
         lib.bh_get_mlp.argtypes = [P, P]
         lib.bh_stats.argtypes = [P, ctypes.POINTER(bh_stats_t)]
         lib.bh_mlp_eval.argtypes = [P, ctypes.c_int64, P, P]
+        lib.bh_set_ewald.argtypes = [P, I, I]
+        lib.bh_ewald_eval.argtypes = [P, ctypes.c_int64, P, P]
         lib.bh_last_error.argtypes = [P]
         lib.bh_last_error.restype = ctypes.c_char_p
         lib.bh_destroy.argtypes = [P]
@@ -103,7 +105,8 @@ def load(build_if_needed: bool = True):
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
-                     "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats"):
+                     "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats", "bh_set_ewald",
+                     "bh_ewald_eval"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -347,6 +350,21 @@ def bh_stats(ctx) -> dict:
     return {name: getattr(out, name) for name, _ in bh_stats_t._fields_}
 
 
+def bh_set_ewald(ctx, n_grid: int, n_series: int) -> None:
+    _check(ctx, load().bh_set_ewald(ctx, int(n_grid), int(n_series)), "bh_set_ewald")
+
+
+def bh_ewald_eval(ctx, r, chi) -> None:
+    """chi (smooth part of the Ewald field) at DEVICE float32 displacements
+    r[n, 3] (box units, |component| <= 1/2) -> chi[n], by the table."""
+    import torch
+    if r.dim() != 2 or r.shape[1] != 3 or chi.numel() != r.shape[0]:
+        raise ValueError("expected r[n, 3] and chi[n]")
+    st = load().bh_ewald_eval(ctx, int(r.shape[0]), ctypes.c_void_p(_dev_ptr(r, torch.float32)),
+                              ctypes.c_void_p(_dev_ptr(chi, torch.float32)))
+    _check(ctx, st, "bh_ewald_eval")
+
+
 def bh_last_error(ctx) -> str:
     return load().bh_last_error(ctx).decode()
 
@@ -366,13 +384,15 @@ class Solver:
     """
 
     def __init__(self, precision=BH_PREC_F32, criterion=BH_CRIT_PER_CELL, kahan=True,
-                 quadrupole=False, learned=False, timing=False, device=0, stream=None):
+                 quadrupole=False, learned=False, timing=False, periodic=False, device=0,
+                 stream=None):
         import torch
         o = bh_default_options()
         o.precision, o.criterion, o.kahan = int(precision), int(criterion), int(bool(kahan))
         o.quadrupole = int(bool(quadrupole))
         o.learned = int(learned)  # 1: mma.sync network in the walk; 2: tcgen05
         o.timing = int(bool(timing))
+        o.periodic = int(bool(periodic))
         self.options = o
         self.device = torch.device("cuda", device)
         if stream is None:
@@ -467,6 +487,18 @@ class Solver:
 
     def set_mlp(self, w):
         bh_set_mlp(self._ctx, w)
+
+    def set_ewald(self, n_grid: int = 64, n_series: int = 3):
+        """Recompute the periodic walk's Ewald table (grid, series range)."""
+        bh_set_ewald(self._ctx, n_grid, n_series)
+
+    def ewald_eval(self, r):
+        """chi at DEVICE float32 displacements r[n, 3] by the table."""
+        import torch
+        chi = torch.empty(r.shape[0], dtype=torch.float32, device=self.device)
+        bh_ewald_eval(self._ctx, r, chi)
+        self._handoff(chi)
+        return chi
 
     def stats(self) -> dict:
         return bh_stats(self._ctx)

@@ -334,6 +334,56 @@ void bh_default_options(bh_options *opt) {
   opt->kahan = 1;
 }
 
+// Default Ewald table of a periodic context: interpolation error about 3e-6
+// of chi(0), series converged to 1e-13.
+constexpr int kEwaldGrid = 64, kEwaldSeries = 3;
+
+// Computes the Ewald table (n, N) on the context's stream and makes it the
+// context's table; synchronises once (to free the FP64 scratch).
+static bh_status set_ewald(bh_ctx *ctx, int n, int N) {
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  const int64_t m = n + 2;
+  double *scratch = nullptr;
+  float *tab = nullptr;
+  if (cudaMalloc(&scratch, m * m * m * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&tab, (int64_t)n * n * n * 32 * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    release(scratch);
+    release(tab);
+    return fail(ctx, BH_ERR_OOM, "Ewald table: device allocation failed");
+  }
+  cudaError_t e = bhg::launch_ewald_table(ctx->stream, n, N, scratch, tab);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  release(scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release(tab);
+    return fail(ctx, BH_ERR_CUDA, "Ewald table: %s", cudaGetErrorString(e));
+  }
+  drop_graph(ctx->tree);  // a captured walk holds the old table
+  release(ctx->d_ewald);
+  ctx->d_ewald = tab;
+  ctx->ewald_n = n;
+  ctx->ewald_series = N;
+  return BH_OK;
+}
+
+// The walk of the context's options on stream s: the potential into out, or
+// with n_int / n_test (and optional n_leaf) the per-cell counts.
+static cudaError_t enqueue_walk(bh_ctx *ctx, cudaStream_t s, double G, void *out,
+                                int32_t *n_int, int32_t *n_test, int32_t *n_leaf, int wpc) {
+  bhg::Tree &t = ctx->tree;
+  if (ctx->opt.periodic)
+    return bhg::launch_walk_periodic(s, ctx->opt, t.nb, t.d_rec, t.d_blk, t.d_orig,
+                                     field_args(t), ctx->d_ewald, ctx->ewald_n, G, out, n_int,
+                                     n_test, n_leaf, wpc);
+  if (!n_int && ctx->opt.learned == 2) return bhg::launch_walk_learned_tc(s, ctx, G, out);
+  if (!n_int && ctx->opt.learned) return bhg::launch_walk_learned(s, ctx, G, out);
+  return bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
+                          t.d_orig, field_args(t), G, out, n_int, n_test, n_leaf, wpc);
+}
+
 bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_stream) {
   if (!out) return BH_ERR_ARG;
   *out = nullptr;
@@ -343,7 +393,12 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if ((o.precision != BH_PREC_F32 && o.precision != BH_PREC_F64) ||
       (o.criterion != BH_CRIT_PER_CELL && o.criterion != BH_CRIT_WARP_VOTE) ||
       (o.kahan != 0 && o.kahan != 1) || (o.quadrupole != 0 && o.quadrupole != 1) ||
-      (o.learned < 0 || o.learned > 2) || (o.timing != 0 && o.timing != 1))
+      (o.learned < 0 || o.learned > 2) || (o.timing != 0 && o.timing != 1) ||
+      (o.periodic != 0 && o.periodic != 1))
+    return BH_ERR_ARG;
+  // periodic boundaries: the binary32 per-cell walk with monopole terms
+  if (o.periodic && (o.precision != BH_PREC_F32 || o.criterion != BH_CRIT_PER_CELL ||
+                     o.quadrupole || o.learned))
     return BH_ERR_ARG;
   // the learned walk is the binary32 per-cell walk, with the network in place
   // of the quadrupole term
@@ -370,6 +425,13 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
     if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
     delete ctx;
     return BH_ERR_CUDA;
+  }
+  if (o.periodic) {
+    const bh_status st = set_ewald(ctx, kEwaldGrid, kEwaldSeries);
+    if (st != BH_OK) {
+      bh_destroy(ctx);
+      return st;
+    }
   }
   *out = ctx;
   return BH_OK;
@@ -484,15 +546,7 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   if (st != BH_OK) return st;
   const bool timed = timing_mark(ctx, 2);
   if ((st = prepare(ctx, theta)) != BH_OK) return st;
-  bhg::Tree &t = ctx->tree;
-  if (ctx->opt.learned == 2)
-    BH_CUDA(bhg::launch_walk_learned_tc(ctx->stream, ctx, G, out));
-  else if (ctx->opt.learned)
-    BH_CUDA(bhg::launch_walk_learned(ctx->stream, ctx, G, out));
-  else
-    BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
-                             t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr,
-                             nullptr, t.wpc));
+  BH_CUDA(enqueue_walk(ctx, ctx->stream, G, out, nullptr, nullptr, nullptr, ctx->tree.wpc));
   ctx->potential_timed = timed && timing_mark(ctx, 3);
   ctx->last_theta = theta;
   return BH_OK;
@@ -507,9 +561,7 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
-                           t.d_blk, t.d_orig, field_args(t), 0.0, nullptr, n_int, n_test, n_cell,
-                           t.wpc));
+  BH_CUDA(enqueue_walk(ctx, ctx->stream, 0.0, nullptr, n_int, n_test, n_cell, t.wpc));
   // totals for bh_stats
   ctx->counts_valid = false;
   if (!ctx->d_counts) BH_CUDA(cudaMalloc(&ctx->d_counts, 3 * sizeof(unsigned long long)));
@@ -619,7 +671,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
   const bool tunable = ctx->opt.precision == BH_PREC_F32 &&
-                       ctx->opt.criterion == BH_CRIT_PER_CELL;
+                       ctx->opt.criterion == BH_CRIT_PER_CELL && !ctx->opt.learned;
   if (tunable) {
     const int64_t out_bytes = (int64_t)t.nb * bhg::kCellsPerBlock * sizeof(float);
     if (t.stage_out_bytes < out_bytes) {
@@ -638,9 +690,8 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
       float tmin = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         BH_CUDA(cudaEventRecord(e0, ctx->stream));
-        BH_CUDA(bhg::launch_walk(ctx->stream, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec,
-                                 t.d_q64, t.d_blk, t.d_orig, field_args(t), 1.0, t.d_stage_out,
-                                 nullptr, nullptr, nullptr, w));
+        BH_CUDA(enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
+                             w));
         BH_CUDA(cudaEventRecord(e1, ctx->stream));
         BH_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -692,11 +743,7 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
       if (cap == BH_OK && e == cudaSuccess && ctx->opt.learned && !ctx->d_mlp)
         cap = fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
       if (cap == BH_OK && e == cudaSuccess)
-        e = ctx->opt.learned == 2 ? bhg::launch_walk_learned_tc(s, ctx, G, out)
-            : ctx->opt.learned    ? bhg::launch_walk_learned(s, ctx, G, out)
-                                  : bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64,
-                                   t.d_blk, t.d_orig, field_args(t), G, out, nullptr, nullptr,
-                                   nullptr, t.wpc);
+        e = enqueue_walk(ctx, s, G, out, nullptr, nullptr, nullptr, t.wpc);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);
@@ -803,7 +850,28 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
   b += t.stage_in_bytes + t.stage_out_bytes + 4 * sizeof(unsigned);
   if (ctx->d_mlp) b += sizeof(bhg::MlpDev) + sizeof(bhg::MlpTc) + sizeof(unsigned);
   if (ctx->d_counts) b += 3 * sizeof(unsigned long long);
+  if (ctx->d_ewald) b += (int64_t)ctx->ewald_n * ctx->ewald_n * ctx->ewald_n * 128;
   out->device_bytes = b;
+  return BH_OK;
+}
+
+bh_status bh_set_ewald(bh_ctx *ctx, int n_grid, int n_series) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (n_grid < 2 || n_grid > 256 || n_series < 1 || n_series > 8)
+    return fail(ctx, BH_ERR_ARG, "bh_set_ewald: n_grid in [2, 256], n_series in [1, 8]");
+  return set_ewald(ctx, n_grid, n_series);
+}
+
+bh_status bh_ewald_eval(bh_ctx *ctx, int64_t n, const float *r, float *chi) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!ctx->d_ewald) return fail(ctx, BH_ERR_STATE, "bh_ewald_eval: no Ewald table");
+  if (n < 0 || (n > 0 && (!r || !chi)))
+    return fail(ctx, BH_ERR_ARG, "bh_ewald_eval: bad size or null buffer");
+  bh_status st = use_device(ctx);
+  if (st != BH_OK) return st;
+  BH_CUDA(bhg::launch_ewald_eval(ctx->stream, n, r, ctx->d_ewald, ctx->ewald_n, chi));
   return BH_OK;
 }
 
@@ -824,6 +892,7 @@ void bh_destroy(bh_ctx *ctx) {
   release(ctx->d_mlp_tc);
   release(ctx->d_tc_flag);
   release(ctx->d_counts);
+  release(ctx->d_ewald);
   for (cudaEvent_t &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
