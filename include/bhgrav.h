@@ -347,11 +347,15 @@ bh_status bh_mlp_eval(bh_ctx *ctx, int64_t n, const float *x, float *y);
  * f = u/h - c, weights f(f-1)/2, 1 - f^2, f(f+1)/2 for the points c-1, c,
  * c+1; chi(u) = sum of the 27 weight products times the table values. */
 
-/* Computes the table on the device (FP64 sums, stored as binary32) for the
- * periodic walk of this context; a context created with the periodic
- * option starts with n_grid = 64, n_series = 3 (interpolation error about
- * 3e-6 of chi(0), series converged to 1e-13).  n_grid in [2, 512],
- * n_series in [1, 8], else BH_ERR_ARG.  Enqueued on the context's stream. */
+/* Computes the table on the device (FP64 sums) for the periodic walk of
+ * this context and keeps it as n_grid^3 entries of 64 bytes: per grid
+ * centre the 27 coefficients of its quadratic interpolant, the value and
+ * first-order ones in binary32, the 23 smaller ones in binary16 (they change
+ * chi by less than 3e-7).  A context created with the periodic option starts
+ * with n_grid = 64, n_series = 3 (16 MB; interpolation error about 3e-6,
+ * series converged to 1e-13).  n_grid in [2, 256], n_series in [1, 8], else
+ * BH_ERR_ARG; BH_ERR_OOM if the table does not fit.  Synchronises the
+ * context's stream. */
 bh_status bh_set_ewald(bh_ctx *ctx, int n_grid, int n_series);
 
 /* chi at n box-unit displacements (DEVICE FP32 r[n][3], each component in

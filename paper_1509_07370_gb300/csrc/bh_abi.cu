@@ -345,9 +345,9 @@ static bh_status set_ewald(bh_ctx *ctx, int n, int N) {
   if (st != BH_OK) return st;
   const int64_t m = n + 2;
   double *scratch = nullptr;
-  float *tab = nullptr;
+  unsigned char *tab = nullptr;
   if (cudaMalloc(&scratch, m * m * m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&tab, (int64_t)n * n * n * 32 * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&tab, (int64_t)n * n * n * 64) != cudaSuccess) {
     cudaGetLastError();
     release(scratch);
     release(tab);
@@ -850,7 +850,7 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
   b += t.stage_in_bytes + t.stage_out_bytes + 4 * sizeof(unsigned);
   if (ctx->d_mlp) b += sizeof(bhg::MlpDev) + sizeof(bhg::MlpTc) + sizeof(unsigned);
   if (ctx->d_counts) b += 3 * sizeof(unsigned long long);
-  if (ctx->d_ewald) b += (int64_t)ctx->ewald_n * ctx->ewald_n * ctx->ewald_n * 128;
+  if (ctx->d_ewald) b += (int64_t)ctx->ewald_n * ctx->ewald_n * ctx->ewald_n * 64;
   out->device_bytes = b;
   return BH_OK;
 }

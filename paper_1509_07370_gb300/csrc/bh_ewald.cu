@@ -51,8 +51,9 @@ __global__ void k_ewald_points(int n, int N, double *__restrict__ chi) {
 // Coefficients of the quadratic interpolant around each centre (layout in
 // bh_ewald.cuh): the 27 point values, transformed along x, then y, then z by
 // [v(-1), v(0), v(1)] -> [v(0), (v(1) - v(-1))/2, (v(1) - 2 v(0) + v(-1))/2],
-// in FP64, rounded once to binary32.
-__global__ void k_ewald_pack(int n, const double *__restrict__ chi, float *__restrict__ tab) {
+// in FP64, rounded once to binary32 or binary16 (layout in bh_ewald.cuh).
+__global__ void k_ewald_pack(int n, const double *__restrict__ chi,
+                             unsigned char *__restrict__ tab) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)n * n * n) return;
   const int m = n + 2;
@@ -74,15 +75,25 @@ __global__ void k_ewald_pack(int n, const double *__restrict__ chi, float *__res
     for (int a = 0; a < 3; ++a) q(v[c][0][a], v[c][1][a], v[c][2][a]);  // along y
   for (int b = 0; b < 3; ++b)
     for (int a = 0; a < 3; ++a) q(v[0][b][a], v[1][b][a], v[2][b][a]);  // along z
-  float *out = tab + kEwaldEntryFloats * e;
+  unsigned char *out = tab + (int64_t)kEwaldEntryBytes * e;
+  float *f32 = reinterpret_cast<float *>(out);
+  __half *f16 = reinterpret_cast<__half *>(out + 16);
+  f32[0] = (float)v[0][0][0];
+  f32[1] = (float)v[0][0][1];
+  f32[2] = (float)v[0][1][0];
+  f32[3] = (float)v[1][0][0];
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 3; ++j)
-      for (int i = 0; i < 3; ++i) out[9 * k + 3 * j + i] = (float)v[k][j][i];
-  for (int i = 27; i < kEwaldEntryFloats; ++i) out[i] = 0.0f;
+      for (int i = 0; i < 3; ++i) {
+        const int slot = ewald_half_slot(k, j, i);
+        if (slot >= 0) f16[slot] = __double2half(v[k][j][i]);
+      }
+  f16[23] = __ushort_as_half((unsigned short)0);
 }
 
 __global__ void k_ewald_eval(int64_t npts, const float *__restrict__ r,
-                             const float *__restrict__ tab, int n, float *__restrict__ out) {
+                             const unsigned char *__restrict__ tab, int n,
+                             float *__restrict__ out) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= npts) return;
   out[q] = ewald_chi(tab, n, (float)(2 * n), fabsf(r[3 * q]), fabsf(r[3 * q + 1]),
@@ -91,7 +102,8 @@ __global__ void k_ewald_eval(int64_t npts, const float *__restrict__ r,
 
 }  // namespace
 
-cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch, float *tab) {
+cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch,
+                               unsigned char *tab) {
   const int m = n + 2;
   const int64_t npts = (int64_t)m * m * m, nent = (int64_t)n * n * n;
   k_ewald_points<<<(unsigned)((npts + 127) / 128), 128, 0, s>>>(n, N, scratch);
@@ -99,8 +111,8 @@ cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_ewald_eval(cudaStream_t s, int64_t npts, const float *r, const float *tab,
-                              int n, float *out) {
+cudaError_t launch_ewald_eval(cudaStream_t s, int64_t npts, const float *r,
+                              const unsigned char *tab, int n, float *out) {
   if (npts <= 0) return cudaSuccess;
   k_ewald_eval<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(npts, r, tab, n, out);
   return cudaGetLastError();

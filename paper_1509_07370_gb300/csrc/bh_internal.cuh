@@ -304,16 +304,18 @@ cudaError_t launch_walk_learned_tc(cudaStream_t s, bh_ctx *ctx, double G, void *
 
 // ---- periodic boundaries (bh_ewald.cu, bh_walk_periodic.cu) ----------------
 // The Ewald table of grid n and series range N (layout in bh_ewald.cuh):
-// FP64 values at the (n+2)^3 points into scratch, then n^3 entries of 32
-// floats (the interpolants' coefficients) into tab.
-cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch, float *tab);
+// FP64 values at the (n+2)^3 points into scratch, then n^3 entries of 64
+// bytes (the interpolants' coefficients) into tab.
+cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch,
+                               unsigned char *tab);
 // chi at npts displacements r[npts][3] by the walk's interpolation.
-cudaError_t launch_ewald_eval(cudaStream_t s, int64_t npts, const float *r, const float *tab,
-                              int n, float *out);
+cudaError_t launch_ewald_eval(cudaStream_t s, int64_t npts, const float *r,
+                              const unsigned char *tab, int n, float *out);
 // The binary32 per-cell walk with periodic boundaries; counts as launch_walk.
 cudaError_t launch_walk_periodic(cudaStream_t s, const bh_options &opt, int nb,
                                  const WalkRec *rec, const int4 *blk, const int *orig,
-                                 const FieldArgs &fa, const float *tab, int n, double G,
+                                 const FieldArgs &fa, const unsigned char *tab, int n,
+                                 double G,
                                  void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
                                  int wpc);
 
@@ -328,7 +330,7 @@ struct bh_ctx {
   bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
   bhg::MlpTc *d_mlp_tc = nullptr;   // the same network for bh_mlp_eval
   unsigned *d_tc_flag = nullptr;    // time-out flag of bh_mlp_eval
-  float *d_ewald = nullptr;         // periodic boundaries: the Ewald table
+  unsigned char *d_ewald = nullptr; // periodic boundaries: the Ewald table
   int ewald_n = 0, ewald_series = 0;
   // statistics (bh_stats): events of the timing option (build start/end,
   // potential start/end), theta of the last potential, device totals of the

@@ -10,7 +10,7 @@
 //    the term;
 //  * an accepted node or another cell adds M psi(d) = M (1/d + chi(d)), chi
 //    the smooth part of the Ewald field interpolated quadratically from the
-//    table (bh_ewald.cuh): one 128-byte entry of interpolant coefficients
+//    table (bh_ewald.cuh): one 64-byte entry of interpolant coefficients
 //    per target and 26 FMAs, the y and z indices shared by the x-neighbour
 //    pair;
 //  * the target's own cell adds its mass times chi(0): the field of its
@@ -52,9 +52,9 @@ __device__ __forceinline__ void dist2_min_image(u64 tx2, float ty, float tz, u64
 // that takes nothing loads nothing, and target b reuses a's entry when both
 // fall on the same centre (the y and z parts of the index and fy, fz are
 // shared by the x-neighbour pair).
-__device__ __forceinline__ u64 chi_pair(const float *__restrict__ tab, int n, float s, u64 dx2,
+__device__ __forceinline__ u64 chi_pair(const unsigned char *__restrict__ tab, int n, float s, u64 dx2,
                                         float dy, float dz, bool ua, bool ub) {
-  float dxa, dxb, fxa, fxb, fy, fz, C[32];
+  float dxa, dxb, fxa, fxb, fy, fz, C[27];
   upk(dx2, dxa, dxb);
   const int ca = ewald_axis(fabsf(dxa), s, n, fxa);
   const int cb = ewald_axis(fabsf(dxb), s, n, fxb);
@@ -85,7 +85,7 @@ template <bool KAHAN, bool COUNTS>
 __device__ __forceinline__ void walk_octant_periodic(
     unsigned u, int lane, const WalkRec *__restrict__ rec, const int4 *__restrict__ blk,
     const int *__restrict__ orig, const int4 *__restrict__ fld, const double *__restrict__ invL,
-    const unsigned long long *__restrict__ mmax, const float *__restrict__ tab, int n, double G,
+    const unsigned long long *__restrict__ mmax, const unsigned char *__restrict__ tab, int n, double G,
     float *__restrict__ out, int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
     int32_t *__restrict__ n_leaf) {
   const unsigned p = u >> 3;                          // sorted block
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kPMaxThreads)
     k_walk_periodic(unsigned nunits, const WalkRec *__restrict__ rec,
                     const int4 *__restrict__ blk, const int *__restrict__ orig,
                     const int4 *__restrict__ fld, const double *__restrict__ invL,
-                    const unsigned long long *__restrict__ mmax, const float *__restrict__ tab,
+                    const unsigned long long *__restrict__ mmax, const unsigned char *__restrict__ tab,
                     int n, double G, float *__restrict__ out, int32_t *__restrict__ n_int,
                     int32_t *__restrict__ n_test, int32_t *__restrict__ n_leaf) {
   const int lane = threadIdx.x & 31;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kPMaxThreads)
 
 template <bool KAHAN, bool COUNTS>
 cudaError_t go_periodic(cudaStream_t s, int nb, const WalkRec *rec, const int4 *blk,
-                        const int *orig, const FieldArgs &fa, const float *tab, int n, double G,
+                        const int *orig, const FieldArgs &fa, const unsigned char *tab, int n, double G,
                         void *out, int32_t *ni, int32_t *nt, int32_t *nl, int wpc) {
   const unsigned nunits = (unsigned)nb * 8u;
   const int w = wpc > 0 ? wpc : kPWarpsPerCta;
@@ -223,7 +223,7 @@ cudaError_t go_periodic(cudaStream_t s, int nb, const WalkRec *rec, const int4 *
 
 cudaError_t launch_walk_periodic(cudaStream_t s, const bh_options &opt, int nb,
                                  const WalkRec *rec, const int4 *blk, const int *orig,
-                                 const FieldArgs &fa, const float *tab, int n, double G,
+                                 const FieldArgs &fa, const unsigned char *tab, int n, double G,
                                  void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
                                  int wpc) {
   if (n_int)
