@@ -225,7 +225,7 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
         # the periodic field has zero mean and changes sign: errors relative
         # to its largest magnitude; a smaller direct sample (each direct
         # periodic term interpolates the table)
-        dt = direct_targets(w, rng, nrandom=200, ndense=1)
+        dt = direct_targets(w, np.random.default_rng(4321), nrandom=200, ndense=1)
         t0 = time.perf_counter()
         d = tree.direct_periodic(targets=dt, ng=ewald_grid)
         t_direct = time.perf_counter() - t0
@@ -238,11 +238,11 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
             "oracle_walk_max_err_over_max_abs_vs_direct":
                 float(np.max(np.abs(wd - d)) / np.max(np.abs(d))),
             "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
-            "direct_sample": "200 random cells (seed 1234) + every cell of the densest block; "
+            "direct_sample": "200 random cells (seed 4321) + every cell of the densest block; "
                              "direct periodic sum with the same Ewald table",
             "direct_cells_per_s": len(dt) / t_direct}
     elif phi_gpu is not None:
-        dt = direct_targets(w, rng)
+        dt = direct_targets(w, np.random.default_rng(4321))
         t0 = time.perf_counter()
         d = tree.direct(targets=dt)
         t_direct = time.perf_counter() - t0
@@ -252,7 +252,7 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
             "max_rel_vs_direct": float(np.max(np.abs(phi_gpu[dt] / d - 1.0))),
             "oracle_walk_max_rel_vs_direct": float(np.max(np.abs(wd / d - 1.0))),
             "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
-            "direct_sample": "2,000 random cells (seed 1234) + every cell of the 8 densest "
+            "direct_sample": "2,000 random cells (seed 4321) + every cell of the 8 densest "
                              "blocks",
             "direct_cells_per_s": len(dt) / t_direct}
         if plain is not None:
@@ -504,7 +504,7 @@ def learned_oracle_leg(w, theta, wts, plain_theta, phi, cpu_seconds):
     t0 = time.perf_counter()
     ref = tree.walk_learned(theta, wts, targets=tg)
     t_walk = time.perf_counter() - t0
-    dt = direct_targets(w, rng)
+    dt = direct_targets(w, np.random.default_rng(4321))
     d = tree.direct(targets=dt)
 
     def rel(a):
@@ -516,7 +516,8 @@ def learned_oracle_leg(w, theta, wts, plain_theta, phi, cpu_seconds):
            "learned_max_rel_vs_oracle_learned": float(np.max(np.abs(phi["learned"][tg] / ref - 1))),
            "theta": theta, "plain_theta": plain_theta,
            "cells_compared": int(k), "cells_vs_direct": int(len(dt)),
-           "direct_sample": "2,000 random cells + every cell of the 8 densest blocks"}
+           "direct_sample": "2,000 random cells (seed 4321) + every cell of the 8 densest "
+                            "blocks"}
     return {"value": n / (t_build + t_walk * n / k), "unit": "cells/s",
             "cores": O.max_threads(), "kind": "oracle",
             "sample": f"tree+FP64 moments+quadrupoles of all {n} cells; learned walk (FP64 MLP) "
