@@ -57,7 +57,19 @@ def test_bad_options_rejected_before_device_use():
     o = B.bh_default_options()
     o.criterion = -1
     assert lib.bh_create(ctypes.byref(h), ctypes.byref(o), 0, None) == B.BH_ERR_ARG
+    # periodic boundaries: the binary32 per-cell monopole walk only
+    for field, value in (("quadrupole", 1), ("learned", 1), ("precision", B.BH_PREC_F64),
+                         ("criterion", B.BH_CRIT_WARP_VOTE)):
+        o = B.bh_default_options()
+        o.periodic = 1
+        setattr(o, field, value)
+        assert lib.bh_create(ctypes.byref(h), ctypes.byref(o), 0, None) == B.BH_ERR_ARG
+    o = B.bh_default_options()
+    o.periodic = 2
+    assert lib.bh_create(ctypes.byref(h), ctypes.byref(o), 0, None) == B.BH_ERR_ARG
     assert not h.value
+    assert lib.bh_set_ewald(None, 64, 3) == B.BH_ERR_ARG
+    assert lib.bh_ewald_eval(None, 0, None, None) == B.BH_ERR_ARG
 
 
 def test_library_is_built_for_sm103a():
