@@ -151,16 +151,22 @@ class ClockSampler:
 
 # ----------------------------------------------------- captured traffic --
 def captured_traffic(workload_name, theta, mode):
-    """DRAM bytes per walk launch from the committed ncu summary, if that
-    capture is of this workload and of the walk source as it is now."""
+    """DRAM bytes per walk launch from the committed ncu summary of this walk,
+    if that capture is of this workload and of the walk source as it is now."""
     import hashlib
     import re
+    profile, files = {
+        "quadrupole": ("walk_pair_quadrupole_theta0.7_maclaurin_2M.md",
+                       ("bh_walk.cu", "bh_walk_common.cuh")),
+        "periodic64": ("walk_periodic_theta0.7_maclaurin_2M.md",
+                       ("bh_walk_periodic.cu", "bh_ewald.cuh")),
+    }.get(mode, (None, None))
+    if profile is None:
+        return None
     try:
-        txt = open(os.path.join(ROOT, "profiles",
-                                "walk_pair_quadrupole_theta0.7_maclaurin_2M.md")).read()
+        txt = open(os.path.join(ROOT, "profiles", profile)).read()
         csrc = os.path.join(ROOT, "paper_1509_07370_gb300", "csrc")
-        src = b"".join(open(os.path.join(csrc, f), "rb").read()
-                       for f in ("bh_walk.cu", "bh_walk_common.cuh"))
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in files)
     except OSError:
         return None
     sha = re.search(r"source_sha256: ([0-9a-f]{64})", txt)
@@ -765,8 +771,9 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
-    traffic = (captured_traffic(w.name, args.theta, "quadrupole" if quad else "monopole")
-               if not (args.vote or periodic) else None)
+    mode = (f"periodic{args.ewald_grid}" if periodic
+            else "quadrupole" if quad else "monopole")
+    traffic = captured_traffic(w.name, args.theta, mode) if not args.vote else None
     _, nn, maxlev = solver.tree_size()
     # keys, sort, tiling, scan, top nodes, largest mass, blocks, one top-moment
     # launch per block level (max block level = maxlev - 3), walk
