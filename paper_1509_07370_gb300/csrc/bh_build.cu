@@ -278,6 +278,7 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
 // octant order, every operation rounded once.  c = geometric centre.
 struct Moment {
   double x, y, z, m, delta;
+  double ox, oy, oz;  // R - geometric centre
 };
 __device__ __forceinline__ void accumulate(double &M, double &Sx, double &Sy, double &Sz,
                                            double m, double x, double y, double z) {
@@ -301,14 +302,20 @@ __device__ __forceinline__ Moment finish(double M, double Sx, double Sy, double 
   }
   const double ox = __dsub_rn(r.x, cx), oy = __dsub_rn(r.y, cy), oz = __dsub_rn(r.z, cz);
   r.delta = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ox, ox), __dmul_rn(oy, oy)), __dmul_rn(oz, oz)));
+  r.ox = ox;
+  r.oy = oy;
+  r.oz = oz;
   return r;
 }
 
 // (i + 1/2) 2^-level, the centre coordinate of cube i at `level` in box units:
 // 2i + 1 < 2^22 and level <= 21, so it is formed exactly in binary32 and
 // widened (the same value as the FP64 expression, without FP64 operations).
+__device__ __forceinline__ float centre_coord_f(int i, int level) {
+  return __fmul_rn((float)(2 * i + 1), pow2f(-(level + 1)));
+}
 __device__ __forceinline__ double centre_coord(int i, int level) {
-  return (double)__fmul_rn((float)(2 * i + 1), pow2f(-(level + 1)));
+  return (double)centre_coord_f(i, level);
 }
 
 __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m,
@@ -326,10 +333,11 @@ __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double
 // inv_unit = 2^-e of the field's binary32 mass unit (the record's mass).
 // inv_theta > 0: also the squared opening radius s2 = fl(fl(l fl(1/theta)) +
 // delta)^2 from the same binary32 l and delta as k_prepare_s2 (identical).
-__device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int level,
-                                               const Moment &r, double4_32a *mom, WalkRec *rec,
-                                               float2 *aux, uint8_t *lvl, double inv_unit,
-                                               float inv_theta) {
+// Returns the record's binary32 mass (in the field's unit).
+__device__ __forceinline__ float store_internal(int64_t id, int64_t skip, int level,
+                                                const Moment &r, double4_32a *mom, WalkRec *rec,
+                                                float2 *aux, uint8_t *lvl, double inv_unit,
+                                                float inv_theta) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
   WalkRec w = make_rec(r.x, r.y, r.z, r.m * inv_unit, skip);
   const float l = pow2f(-level), delta = __double2float_rn(r.delta);
@@ -340,6 +348,7 @@ __device__ __forceinline__ void store_internal(int64_t id, int64_t skip, int lev
   rec[id] = w;
   aux[id] = make_float2(l, delta);
   if (lvl) lvl[id] = (uint8_t)level;
+  return w.m;
 }
 
 // Quadrupole about the parent's centre of mass (parallel-axis rule): the
@@ -362,10 +371,30 @@ __device__ __forceinline__ void add_shifted(double Q[6], const double *Qc, doubl
 // small correction rounded to binary32 anyway, and GB300 runs FP64 far slower
 // than FP32.  fm is the child's mass in the field's binary32 mass unit; the
 // shift s is formed in FP64 (a difference of nearby centres of mass) and
-// then rounded.
+// then rounded (top nodes), or inside a block from binary32 offsets (below).
 __device__ __forceinline__ void add_shifted_f(float Q[6], const float *Qc, float fm, double sx,
                                               double sy, double sz) {
   const float x = __double2float_rn(sx), y = __double2float_rn(sy), z = __double2float_rn(sz);
+  const float s2 = x * x + y * y + z * z;
+  Q[0] += fm * (3.0f * x * x - s2);
+  Q[1] += fm * (3.0f * y * y - s2);
+  Q[2] += fm * (3.0f * z * z - s2);
+  Q[3] += fm * (3.0f * x * y);
+  Q[4] += fm * (3.0f * x * z);
+  Q[5] += fm * (3.0f * y * z);
+  if (Qc)
+    for (int a = 0; a < 6; ++a) Q[a] += Qc[a];
+}
+
+// The same with the shift given in binary32.  Inside a block it is formed as
+// s = (c_child - c_parent) + (o_child - o_parent), o = R - c the binary32
+// offsets of the centres of mass from the geometric centres c: c_child -
+// c_parent is +-l/4 (exact) and every term is of the node's size, so s
+// carries an absolute error of a few 2^-24 l -- the quadrupole, a sum of
+// m s s^T terms against M l^2, keeps about 2^-22 relative accuracy -- and
+// needs no FP64 operation (GB300 issues FP64 at a small fraction of FP32).
+__device__ __forceinline__ void add_shifted_ff(float Q[6], const float *Qc, float fm, float x,
+                                               float y, float z) {
   const float s2 = x * x + y * y + z * z;
   Q[0] += fm * (3.0f * x * x - s2);
   Q[1] += fm * (3.0f * y * y - s2);
@@ -435,6 +464,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   __shared__ double pm[8], px[8], py[8], pz[8];             // level lb+1 nodes
   __shared__ double gq[64][6], pq[8][6];                    // their quadrupoles (FP64)
   __shared__ float gqf[64][6], pqf[8][6];                   // (binary32)
+  __shared__ float go[64][3], po[8][3], gmu[64], pmu[8];    // binary32 offsets R - c, masses
   const bool quad64 = q64 != nullptr;                       // FP64 quadrupoles
   const bool quad32 = !quad64 && qrec != nullptr;           // binary32 quadrupoles
   const int p = blockIdx.x;
@@ -457,23 +487,32 @@ __global__ void __launch_bounds__(kBlockThreads)
   const T *rho = density + (int64_t)orig[p] * kCellsPerBlock;
   bool bad = false;
   for (int i = t; i < kCellsPerBlock; i += kBlockThreads) {
-    const double r = (double)rho[i];
-    if (!(r >= 0.0) || isinf(r)) bad = true;
+    const T rv = rho[i];
+    if (!(rv >= T(0)) || isinf(rv)) bad = true;  // checked in the input's precision
+    const double r = (double)rv;
     const int cx = i & 7, cy = (i >> 3) & 7, cz = i >> 6;
     const int m = (int)(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
-    const double ux = centre_coord(8 * B.y + cx, lc);
-    const double uy = centre_coord(8 * B.z + cy, lc);
-    const double uz = centre_coord(8 * B.w + cz, lc);
+    const float fx = centre_coord_f(8 * B.y + cx, lc);
+    const float fy = centre_coord_f(8 * B.z + cy, lc);
+    const float fz = centre_coord_f(8 * B.w + cz, lc);
+    const double ux = fx, uy = fy, uz = fz;
     const double mass = __dmul_rn(r, vol);
-    const double mass_u = mass * inv_unit;
+    const float mu = __double2float_rn(mass * inv_unit);
     cm[m] = mass;
-    cmu[m] = __double2float_rn(mass_u);
+    cmu[m] = mu;
     cxs[m] = ux;
     cys[m] = uy;
     czs[m] = uz;
     const int64_t id = root + cell_offset(m);
     mom[id] = make_double4_32a(ux, uy, uz, mass);
-    rec[id] = make_rec(ux, uy, uz, mass_u, id + 1);
+    WalkRec w;  // make_rec without the conversions: the centre is a binary32 value
+    w.px = w.px2 = fx;
+    w.py = fy;
+    w.pz = fz;
+    w.m = w.m2 = mu;
+    w.s2 = 0.0f;
+    w.skip = (unsigned)(id + 1);
+    rec[id] = w;
     aux[id] = make_float2(0.0f, 0.0f);
     lvl[id] = (uint8_t)lc;
   }
@@ -495,7 +534,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     gy[q] = r.y;
     gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+    gmu[q] = store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -505,12 +544,20 @@ __global__ void __launch_bounds__(kBlockThreads)
       for (int a = 0; a < 6; ++a) gq[q][a] = Q[a];
       store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
+      // children: cells at c +- h/2 (h = 2^-(lb+3)) with o = 0
+      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
+                  oz = __double2float_rn(r.oz);
+      const float hc = pow2f(-(lb + 4));
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
-        const int k = 8 * q + o;
-        add_shifted_f(Q, nullptr, cmu[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
+        const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
+        add_shifted_ff(Q, nullptr, cmu[8 * q + o], __fsub_rn(dx, ox), __fsub_rn(dy, oy),
+                       __fsub_rn(dz, oz));
       }
       for (int a = 0; a < 6; ++a) gqf[q][a] = Q[a];
+      go[q][0] = ox;
+      go[q][1] = oy;
+      go[q][2] = oz;
       store_quad_f(id, Q, qrec);
     }
   }
@@ -530,7 +577,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     py[c] = r.y;
     pz[c] = r.z;
     const int64_t id = root + 1 + 73 * c;
-    store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+    pmu[c] = store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -540,13 +587,21 @@ __global__ void __launch_bounds__(kBlockThreads)
       for (int a = 0; a < 6; ++a) pq[c][a] = Q[a];
       store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
+      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
+                  oz = __double2float_rn(r.oz);
+      const float hc = pow2f(-(lb + 3));  // child centre - centre: +-2^-(lb+3)
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
         const int k = 8 * c + o;
-        add_shifted_f(Q, gqf[k], __double2float_rn(gm[k] * inv_unit), gx[k] - r.x, gy[k] - r.y,
-                      gz[k] - r.z);
+        const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
+        add_shifted_ff(Q, gqf[k], gmu[k], __fsub_rn(__fadd_rn(dx, go[k][0]), ox),
+                       __fsub_rn(__fadd_rn(dy, go[k][1]), oy),
+                       __fsub_rn(__fadd_rn(dz, go[k][2]), oz));
       }
       for (int a = 0; a < 6; ++a) pqf[c][a] = Q[a];
+      po[c][0] = ox;
+      po[c][1] = oy;
+      po[c][2] = oz;
       store_quad_f(id, Q, qrec);
     }
   }
@@ -565,10 +620,16 @@ __global__ void __launch_bounds__(kBlockThreads)
       for (int o = 0; o < 8; ++o) add_shifted(Q, pq[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
       store_quad(root, Q, q64, qrec, inv_unit);
     } else if (quad32) {
+      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
+                  oz = __double2float_rn(r.oz);
+      const float hc = pow2f(-(lb + 2));
       float Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int o = 0; o < 8; ++o)
-        add_shifted_f(Q, pqf[o], __double2float_rn(pm[o] * inv_unit), px[o] - r.x, py[o] - r.y,
-                      pz[o] - r.z);
+      for (int o = 0; o < 8; ++o) {
+        const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
+        add_shifted_ff(Q, pqf[o], pmu[o], __fsub_rn(__fadd_rn(dx, po[o][0]), ox),
+                       __fsub_rn(__fadd_rn(dy, po[o][1]), oy),
+                       __fsub_rn(__fadd_rn(dz, po[o][2]), oz));
+      }
       store_quad_f(root, Q, qrec);
     }
   }
