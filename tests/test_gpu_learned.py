@@ -80,9 +80,14 @@ def test_adam_step_lowers_the_loss():
 
 
 def test_learned_walk_matches_oracle():
+    """A fixed (Glorot-initialised, seed 3) network, so that the comparison is
+    reproducible: training on the GPU is not bit-reproducible (its pair list
+    and gradient sums use atomics), and with trained networks, whose net
+    corrections are small and cancel between nodes, the largest
+    difference measured 0.8 to 1.2 times this bar across four trainings.
+    Trained networks are checked by what they gain (below)."""
     w = _field()
-    x, z = L.pairs_of(_gpu(w), w.ncells, 0.8, 256, seed=11)
-    wts, _ = L.train(x, z, epochs=3, batch=2048, seed=3)
+    wts = L.init_weights(3)
     s = _gpu(w, learned=True)
     s.set_mlp(wts)
     phi = s.potential(0.8).cpu().numpy()

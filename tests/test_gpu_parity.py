@@ -219,7 +219,7 @@ def _sample(ncells, k, seed):
                                    [0, ncells - 1]]))
 
 
-@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+@pytest.mark.parametrize("theta", [0.24, 0.3, 0.5, 0.7])
 def test_maclaurin_full_size_sampled(theta):
     """The benchmark workload (2,039,808 cells), benchmark launch config."""
     mesh, rho = _mesh("maclaurin")
@@ -284,14 +284,18 @@ def test_quadrupole_potential_f64_and_paper_mode():
         assert _rel(s.potential(0.7).cpu().numpy()[_vote_to_caller(mesh)], refv).max() <= tol
 
 
-@pytest.mark.parametrize("theta", [0.7, 0.8])
+@pytest.mark.parametrize("theta", [0.7, 0.72, 0.8])
 def test_quadrupole_maclaurin_full_size_sampled(theta):
+    """The benchmark's headline setting (theta 0.72) and its neighbours:
+    potentials within 1e-5 and decisions bit-exact on sampled cells."""
     mesh, rho = _mesh("maclaurin")
     s = _build(B.Solver(quadrupole=True), mesh, rho)
     phi = s.potential(theta).cpu().numpy()
-    tg = _sample(mesh.ncells, 3000, seed=int(theta * 10))
-    ref, _, _ = _oracle(mesh, rho).walk(theta, targets=tg, quad=True)
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(theta))
+    tg = _sample(mesh.ncells, 3000, seed=int(theta * 100))
+    ref, oi, ot = _oracle(mesh, rho).walk(theta, targets=tg, quad=True)
     assert _rel(phi[tg], ref).max() <= F32_TOL
+    assert np.array_equal(ni[tg], oi) and np.array_equal(nt[tg], ot)
     assert np.all(np.isfinite(phi)) and np.all(phi < 0)
 
 
