@@ -276,7 +276,7 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
 
 
 def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=False,
-                    limit=4_200_000):
+                    ewald_grid=64, limit=4_200_000):
     """Max error of each potential in `phis` over EVERY cell against the
     exhaustive sum the library computes at theta = 2^-maxlev (maxlev = the
     deepest cell level): the smallest internal node has side 2^-(maxlev-1),
@@ -292,6 +292,8 @@ def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=Fals
         return None
     theta = 2.0 ** -maxlev
     ref = bh.Solver(periodic=periodic, device=device.index, stream=stream)
+    if periodic and ewald_grid != 64:
+        ref.set_ewald(ewald_grid, 3)
     ref.build(mesh.level, mesh.ijk, d_rho)
     ni, _ = ref.walk_counts(theta)
     if int(ni.min().item()) != n - 1 or int(ni.max().item()) != n - 1:
@@ -662,6 +664,10 @@ def learned_arm(args):
     sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
     alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * sm_mhz * 1e6
     bf16_peak = measured_peak("bf16_tflops") * 1e12
+    all_cells = all_cells_error(
+        bh, mesh, d_rho, maxlev,
+        {"learned_max_rel_vs_direct": phi["learned"], "plain_max_rel_vs_direct": phi["plain"],
+         "plain_same_theta_max_rel_vs_direct": phi["same"]}, dev, stream)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = learned_oracle_leg(w, args.theta, wts_dev, args.plain_theta, phi, args.cpu_seconds)
@@ -700,6 +706,7 @@ def learned_arm(args):
         "vs_same_theta": {"theta": args.theta, "walk": "the plain walk, no network",
                           **{k: v for k, v in res["same"].items() if k != "theta"},
                           "speedup": L_["value"] / res["same"]["value"]},
+        "accuracy_all_cells": all_cells,
         "clocks": clocks, "e2e": e2e,
         "gpu_launches": (7 + (maxlev - 3) + 1) * args.steps,
         "cpu_baseline": cpu,
@@ -881,7 +888,7 @@ def main():
             bh, mesh, d_rho, maxlev,
             {("max_err_over_max_abs_vs_direct" if periodic else "max_rel_vs_direct"): phi_gpu,
              "plain_max_rel_vs_direct": phi_plain},
-            dev, stream, periodic=periodic)
+            dev, stream, periodic=periodic, ewald_grid=args.ewald_grid)
         if all_cells is not None and phi_plain is not None:
             all_cells["plain_theta"] = args.plain_theta
 
