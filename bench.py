@@ -509,6 +509,36 @@ def batched_arm(args):
                 ts.append(time.perf_counter() - t0)
     e2e = {"value": n / float(np.mean(ts)), "unit": "cells/s",
            "h2d_bytes_per_step": int(h_rho.numel() * 4), "d2h_bytes_per_step": int(n * 4)}
+    # the dominant kernel (the walk of all fields) alone, and its work
+    with torch.cuda.stream(stream):
+        wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(5)]
+        for a, b in wev:
+            flush.zero_()
+            a.record(stream)
+            s.potential(theta, 1.0, out=out)
+            b.record(stream)
+        stream.synchronize()
+    walk_ms = float(np.mean([a.elapsed_time(b) for a, b in wev]))
+    ni, nt = s.walk_counts(theta)
+    n_int = int(ni.sum(dtype=torch.int64).item())
+    n_test = int(nt.sum(dtype=torch.int64).item())
+    flops = FLOP_PER_INTERACTION * n_int + FLOP_PER_TEST * n_test
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] if clocks else 1440.0
+    peak = FP32_LANES_PER_SM * torch.cuda.get_device_properties(dev).multi_processor_count \
+        * sm_mhz * 1e6
+    roofline = {"bound": "alu", "kernel": "bh_potential walk of all 64 fields (one launch)",
+                "walk_ms": walk_ms, "achieved": flops / (walk_ms * 1e-3) / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / (walk_ms * 1e-3) / peak,
+                "traffic": None, "ops": "8 per interaction, 7 per test (monopole)",
+                "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n}
+    cpu = None
+    if not args.no_cpu_baseline:  # the oracle on the largest field of the batch
+        big = int(np.argmax([w.ncells for w in ws]))
+        cpu = oracle_leg(ws[big], theta, args.cpu_seconds,
+                         phi[offs[big]:offs[big] + ws[big].ncells].astype(np.float64))
+        cpu["sample"] = f"field {big} of the batch ({ws[big].ncells} cells): " + cpu["sample"]
     line = {"metric": "cell potentials/sec", "value": value, "unit": "cells/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -526,7 +556,7 @@ def batched_arm(args):
                              "how": "field after field: bh_update_density + bh_potential",
                              "value": n / (u_ms * 1e-3), "ms_per_step": u_ms,
                              "speedup": value / (n / (u_ms * 1e-3))}},
-            "clocks": clk.summary(), "e2e": e2e,
+            "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             # per graph launch: largest-mass pass, k_blocks, one top-moment
             # launch per block level above 0, opening radii, walk
             "gpu_launches": (s.tree_size()[2] - 3 + 4) * args.steps}
