@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--train-fields", type=int, default=200,
                     help="--workload learned: seeded training fields")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--all-cells-limit", type=int, default=4_200_000,
+                    help="largest field (cells) whose potentials are compared with the "
+                         "exhaustive direct sum over every cell (N^2 work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -697,7 +700,8 @@ def learned_arm(args):
     all_cells = all_cells_error(
         bh, mesh, d_rho, maxlev,
         {"learned_max_rel_vs_direct": phi["learned"], "plain_max_rel_vs_direct": phi["plain"],
-         "plain_same_theta_max_rel_vs_direct": phi["same"]}, dev, stream)
+         "plain_same_theta_max_rel_vs_direct": phi["same"]}, dev, stream,
+        limit=args.all_cells_limit)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = learned_oracle_leg(w, args.theta, wts_dev, args.plain_theta, phi, args.cpu_seconds)
@@ -918,7 +922,8 @@ def main():
             bh, mesh, d_rho, maxlev,
             {("max_err_over_max_abs_vs_direct" if periodic else "max_rel_vs_direct"): phi_gpu,
              "plain_max_rel_vs_direct": phi_plain},
-            dev, stream, periodic=periodic, ewald_grid=args.ewald_grid)
+            dev, stream, periodic=periodic, ewald_grid=args.ewald_grid,
+            limit=args.all_cells_limit)
         if all_cells is not None and phi_plain is not None:
             all_cells["plain_theta"] = args.plain_theta
 
