@@ -148,3 +148,20 @@ def test_full_size_sampled_against_oracle():
     assert np.array_equal(ni[tg], nio) and np.array_equal(nt[tg], nto)
     assert np.abs(phi[tg] - po).max() <= 1e-5 * np.abs(po).max()
     assert np.all(np.isfinite(phi))
+
+
+def test_zero_field_and_one_block():
+    """Edge cases: an all-zero density gives exactly zero (every term carries
+    its mass), and a mesh of one block (the whole box one 8^3 block, every
+    displacement wrapped) matches the oracle."""
+    m = mg.uniform_mesh(0)
+    s = _solver(m, np.zeros((1, 8, 8, 8)))
+    assert np.all(s.potential(0.5).cpu().numpy() == 0.0)
+    rho = mg.random_density(m, seed=77)
+    s = _solver(m, rho)
+    for theta in (0.2, 0.5, 1.0):
+        phi = s.potential(theta).cpu().numpy()
+        po, nio, _ = _oracle(m, rho).walk_periodic(theta)
+        ni, _ = s.walk_counts(theta)
+        assert np.array_equal(ni.cpu().numpy(), nio)
+        assert np.abs(phi - po).max() <= 1e-5 * np.abs(po).max()
