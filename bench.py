@@ -948,7 +948,11 @@ def main():
                        "moments": "f64", "density_input": "f32",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms))},
+            "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms)),
+                          "step_median": float(np.median(step_ms)),
+                          "potential_median": float(np.median(walk_ms)),
+                          "potential_p10_p90": [float(np.percentile(walk_ms, 10)),
+                                                float(np.percentile(walk_ms, 90))]},
             "walk_only_value": n / walk_s,
             "build_roofline": build_roofline(n, nn, quad, float(np.mean(build_ms))),
             "walk_work": {"interactions": n_int, "cell_interactions": n_cell, "tests": n_test,
