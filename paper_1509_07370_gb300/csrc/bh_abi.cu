@@ -1,7 +1,9 @@
 // C-ABI of libbhgrav: argument checking, buffer ownership, the order of the
-// build and walk launches, and the batched (CUDA graph) solve.  The method's
-// arithmetic lives in bh_build.cu and bh_walk.cu; this file only holds the
-// small export kernels.
+// build and walk launches, the choice of walk for the context's options, the
+// Ewald table's lifetime and the batched (CUDA graph) solve.  The method's
+// arithmetic lives in the other translation units (bh_build.cu, bh_walk.cu,
+// bh_walk_periodic.cu with bh_ewald.cu, bh_walk_learned*.cu with bh_learn.cu
+// and bh_mlp_tc.cu); this file only holds the small export kernels.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
