@@ -7,12 +7,46 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "bh_internal.cuh"
 
+namespace bhg {
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+  static std::mutex mu;
+  static std::string armed;  // the variable's value the count belongs to
+  static long long made = 0;
+  const char *env = std::getenv("BHGRAV_FAIL_ALLOC_AFTER");
+  if (env && *env) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (armed != env) {
+      armed = env;
+      made = 0;
+    }
+    if (made >= std::atoll(env)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    ++made;
+  }
+  return cudaMalloc(p, bytes);
+}
+}  // namespace bhg
+
 namespace {
+
+// A named NVTX range around each entry point's host work (header-only NVTX:
+// a no-op unless a profiler is attached), so that timelines show the calls.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 bh_status fail(bh_ctx *c, bh_status st, const char *fmt, ...) {
   if (c) {
@@ -71,19 +105,19 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   if (t.nb_cap >= nb) return BH_OK;
   free_blocks(t);
   const size_t n = (size_t)nb;
-  BH_CUDA(cudaMalloc(&t.d_level, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_ijk, 3 * n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_key[0], n * sizeof(unsigned long long)));
-  BH_CUDA(cudaMalloc(&t.d_key[1], n * sizeof(unsigned long long)));
-  BH_CUDA(cudaMalloc(&t.d_idx[0], n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_idx[1], n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_count, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_prestart, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_blk, n * sizeof(int4)));
-  BH_CUDA(cudaMalloc(&t.d_orig, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_fid, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_pos, n * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_fld, n * sizeof(int4)));
+  BH_CUDA(bhg::dev_malloc(&t.d_level, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_ijk, 3 * n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_key[0], n * sizeof(unsigned long long)));
+  BH_CUDA(bhg::dev_malloc(&t.d_key[1], n * sizeof(unsigned long long)));
+  BH_CUDA(bhg::dev_malloc(&t.d_idx[0], n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_idx[1], n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_count, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_prestart, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_blk, n * sizeof(int4)));
+  BH_CUDA(bhg::dev_malloc(&t.d_orig, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_fid, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_pos, n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_fld, n * sizeof(int4)));
   t.nb_cap = nb;
   return BH_OK;
 }
@@ -95,15 +129,15 @@ bh_status ensure_nodes(bh_ctx *ctx, int64_t n_nodes) {
   if (t.node_cap >= n_nodes && (!quad || t.quad_cap >= n_nodes)) return BH_OK;
   free_nodes(t);
   if (quad) {
-    if (quad64) BH_CUDA(cudaMalloc(&t.d_q64, (size_t)n_nodes * 6 * sizeof(double)));
-    BH_CUDA(cudaMalloc(&t.d_qrec, (size_t)n_nodes * sizeof(bhg::WalkQuad)));
+    if (quad64) BH_CUDA(bhg::dev_malloc(&t.d_q64, (size_t)n_nodes * 6 * sizeof(double)));
+    BH_CUDA(bhg::dev_malloc(&t.d_qrec, (size_t)n_nodes * sizeof(bhg::WalkQuad)));
     t.quad_cap = n_nodes;
   }
   const size_t n = (size_t)n_nodes;
-  BH_CUDA(cudaMalloc(&t.d_mom, n * sizeof(double4_32a)));
-  BH_CUDA(cudaMalloc(&t.d_rec, n * sizeof(bhg::WalkRec)));
-  BH_CUDA(cudaMalloc(&t.d_aux, n * sizeof(float2)));
-  BH_CUDA(cudaMalloc(&t.d_lvl, n * sizeof(uint8_t)));
+  BH_CUDA(bhg::dev_malloc(&t.d_mom, n * sizeof(double4_32a)));
+  BH_CUDA(bhg::dev_malloc(&t.d_rec, n * sizeof(bhg::WalkRec)));
+  BH_CUDA(bhg::dev_malloc(&t.d_aux, n * sizeof(float2)));
+  BH_CUDA(bhg::dev_malloc(&t.d_lvl, n * sizeof(uint8_t)));
   t.node_cap = n_nodes;
   return BH_OK;
 }
@@ -134,10 +168,10 @@ bh_status ensure_fields(bh_ctx *ctx, int nfields) {
   bhg::Tree &t = ctx->tree;
   if (t.nf_cap >= nfields) return BH_OK;
   free_fields(t);
-  BH_CUDA(cudaMalloc(&t.d_fstart, (size_t)(nfields + 1) * sizeof(int)));
-  BH_CUDA(cudaMalloc(&t.d_invL, (size_t)nfields * sizeof(double)));
-  BH_CUDA(cudaMalloc(&t.d_L, (size_t)nfields * sizeof(double)));
-  BH_CUDA(cudaMalloc(&t.d_mmax, (size_t)nfields * sizeof(unsigned long long)));
+  BH_CUDA(bhg::dev_malloc(&t.d_fstart, (size_t)(nfields + 1) * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_invL, (size_t)nfields * sizeof(double)));
+  BH_CUDA(bhg::dev_malloc(&t.d_L, (size_t)nfields * sizeof(double)));
+  BH_CUDA(bhg::dev_malloc(&t.d_mmax, (size_t)nfields * sizeof(unsigned long long)));
   t.nf_cap = nfields;
   return BH_OK;
 }
@@ -348,8 +382,8 @@ static bh_status set_ewald(bh_ctx *ctx, int n, int N) {
   const int64_t m = n + 2;
   double *scratch = nullptr;
   unsigned char *tab = nullptr;
-  if (cudaMalloc(&scratch, m * m * m * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&tab, (int64_t)n * n * n * 64) != cudaSuccess) {
+  if (bhg::dev_malloc(&scratch, m * m * m * sizeof(double)) != cudaSuccess ||
+      bhg::dev_malloc(&tab, (int64_t)n * n * n * 64) != cudaSuccess) {
     cudaGetLastError();
     release(scratch);
     release(tab);
@@ -420,7 +454,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if (cudaSetDevice(device) != cudaSuccess || bhg::prepare_learned_kernels() != cudaSuccess ||
       bhg::prepare_mlp_tc_kernel() != cudaSuccess ||
       bhg::prepare_learned_tc_kernel() != cudaSuccess ||
-      cudaMalloc(&ctx->tree.d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
+      bhg::dev_malloc(&ctx->tree.d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->tree.h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->tree.d_flags) cudaFree(ctx->tree.d_flags);
@@ -442,6 +476,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
 bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
                    const double *box_lo, double box_len, const void *density,
                    int density_is_fp64) {
+  const Range range_("bh_build");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (nblocks <= 0) {
@@ -456,6 +491,7 @@ bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t
 bh_status bh_build_batch(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
                          const int32_t *ijk, const double *box_lo, const double *box_len,
                          const void *density, int density_is_fp64) {
+  const Range range_("bh_build_batch");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   return build_fields(ctx, nfields, nblocks, level, ijk, box_lo, box_len, density,
@@ -463,6 +499,7 @@ bh_status bh_build_batch(bh_ctx *ctx, int nfields, const int32_t *nblocks, const
 }
 
 bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp64) {
+  const Range range_("bh_update_density");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
@@ -536,6 +573,7 @@ static bh_status prepare(bh_ctx *ctx, double theta) {
 }
 
 bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
+  const Range range_("bh_potential");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
@@ -556,6 +594,7 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
 
 bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_test,
                          int32_t *n_cell) {
+  const Range range_("bh_walk_counts");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (!ctx->tree.built) return fail(ctx, BH_ERR_STATE, "no tree: call bh_build first");
@@ -566,7 +605,7 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   BH_CUDA(enqueue_walk(ctx, ctx->stream, 0.0, nullptr, n_int, n_test, n_cell, t.wpc));
   // totals for bh_stats
   ctx->counts_valid = false;
-  if (!ctx->d_counts) BH_CUDA(cudaMalloc(&ctx->d_counts, 3 * sizeof(unsigned long long)));
+  if (!ctx->d_counts) BH_CUDA(bhg::dev_malloc(&ctx->d_counts, 3 * sizeof(unsigned long long)));
   BH_CUDA(cudaMemsetAsync(ctx->d_counts, 0, 3 * sizeof(unsigned long long), ctx->stream));
   const int64_t ncell = (int64_t)t.nb * bhg::kCellsPerBlock;
   k_sum_counts<<<4 * 152, 256, 0, ctx->stream>>>(ncell, n_int, n_test, n_cell, ctx->d_counts);
@@ -679,7 +718,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
     if (t.stage_out_bytes < out_bytes) {
       release(t.d_stage_out);
       t.stage_out_bytes = 0;
-      BH_CUDA(cudaMalloc(&t.d_stage_out, out_bytes));
+      BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
       t.stage_out_bytes = out_bytes;
     }
     cudaEvent_t e0, e1;
@@ -716,6 +755,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
 
 bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, double theta,
                          double G, void *out) {
+  const Range range_("bh_solve_graph");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   bhg::Tree &t = ctx->tree;
@@ -772,6 +812,7 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
 bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
                         const double *box_lo, double box_len, const void *density_host,
                         int density_is_fp64, double theta, double G, void *out_host) {
+  const Range range_("bh_solve_host");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (nblocks <= 0 || !density_host || !out_host)
@@ -785,13 +826,13 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
   if (t.stage_in_bytes < in_bytes) {
     release(t.d_stage_in);
     t.stage_in_bytes = 0;
-    BH_CUDA(cudaMalloc(&t.d_stage_in, in_bytes));
+    BH_CUDA(bhg::dev_malloc(&t.d_stage_in, in_bytes));
     t.stage_in_bytes = in_bytes;
   }
   if (t.stage_out_bytes < out_bytes) {
     release(t.d_stage_out);
     t.stage_out_bytes = 0;
-    BH_CUDA(cudaMalloc(&t.d_stage_out, out_bytes));
+    BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
     t.stage_out_bytes = out_bytes;
   }
   BH_CUDA(cudaMemcpyAsync(t.d_stage_in, density_host, in_bytes, cudaMemcpyHostToDevice,
@@ -858,6 +899,7 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
 }
 
 bh_status bh_set_ewald(bh_ctx *ctx, int n_grid, int n_series) {
+  const Range range_("bh_set_ewald");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (n_grid < 2 || n_grid > 256 || n_series < 1 || n_series > 8)

@@ -302,6 +302,18 @@ cudaError_t prepare_mlp_tc_kernel();
 cudaError_t prepare_learned_tc_kernel();
 cudaError_t launch_walk_learned_tc(cudaStream_t s, bh_ctx *ctx, double G, void *out);
 
+// ---- device allocations (bh_abi.cu) ------------------------------------------
+// Every device buffer the library owns is allocated through here.  Fault
+// injection for tests of the out-of-memory paths: with the environment
+// variable BHGRAV_FAIL_ALLOC_AFTER=n, the allocations after the first n made
+// since the variable took that value fail with cudaErrorMemoryAllocation --
+// nothing is allocated and no device fault is involved.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
+
 // ---- periodic boundaries (bh_ewald.cu, bh_walk_periodic.cu) ----------------
 // The Ewald table of grid n and series range N (layout in bh_ewald.cuh):
 // FP64 values at the (n+2)^3 points into scratch, then n^3 entries of 64

@@ -305,8 +305,8 @@ bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int6
   int64_t *d_pairs = nullptr;
   unsigned long long *d_count = nullptr;
   const int64_t pcap = cap > 0 ? cap : 1;
-  cudaError_t e = cudaMalloc(&d_pairs, (size_t)pcap * 2 * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(unsigned long long));
+  cudaError_t e = bhg::dev_malloc(&d_pairs, (size_t)pcap * 2 * sizeof(int64_t));
+  if (e == cudaSuccess) e = bhg::dev_malloc(&d_count, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess && ntargets > 0) {
     k_pairs_list<<<(unsigned)((ntargets + 127) / 128), 128, 0, s>>>(
@@ -395,9 +395,9 @@ bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host) {
   for (int k = 0; k < kMlpH; ++k) put(c.b3, tc_canon(0, k, 64), bf16_half(to_bf16(W3[k])));
   c.bias3 = b3[0];
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
-  if ((!ctx->d_mlp && cudaMalloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) ||
-      (!ctx->d_mlp_tc && cudaMalloc(&ctx->d_mlp_tc, sizeof(MlpTc)) != cudaSuccess) ||
-      (!ctx->d_tc_flag && cudaMalloc(&ctx->d_tc_flag, sizeof(unsigned)) != cudaSuccess)) {
+  if ((!ctx->d_mlp && bhg::dev_malloc(&ctx->d_mlp, sizeof(MlpDev)) != cudaSuccess) ||
+      (!ctx->d_mlp_tc && bhg::dev_malloc(&ctx->d_mlp_tc, sizeof(MlpTc)) != cudaSuccess) ||
+      (!ctx->d_tc_flag && bhg::dev_malloc(&ctx->d_tc_flag, sizeof(unsigned)) != cudaSuccess)) {
     cudaGetLastError();
     return ctx_fail(ctx, BH_ERR_OOM, "bh_set_mlp: no device memory");
   }

@@ -308,6 +308,29 @@ def test_quadrupole_export_needs_the_option():
 
 
 # --------------------------------------------------------------- errors ---
+@pytest.mark.parametrize("n", [0, 3, 9, 14])
+def test_out_of_memory_reported_and_recoverable(monkeypatch, n):
+    """Fault injection on the host: with BHGRAV_FAIL_ALLOC_AFTER=n the
+    library's device allocations after the first n fail as out of memory
+    (nothing is allocated; no device fault).  bh_build reports BH_ERR_OOM
+    with a reason and keeps no tree (bh_potential: BH_ERR_STATE); once the
+    variable is cleared the same context builds and gives the potentials of
+    a fresh one, bit for bit."""
+    mesh, rho = _mesh("refined_corner")
+    s = _solver()
+    monkeypatch.setenv("BHGRAV_FAIL_ALLOC_AFTER", str(n))
+    with pytest.raises(B.BHError) as e:
+        _build(s, mesh, rho)
+    assert e.value.status == B.BH_ERR_OOM and "out of memory" in str(e.value).lower()
+    with pytest.raises(B.BHError) as e:
+        s.potential(0.5)
+    assert e.value.status == B.BH_ERR_STATE
+    monkeypatch.delenv("BHGRAV_FAIL_ALLOC_AFTER")
+    got = _build(s, mesh, rho).potential(0.5).cpu().numpy()
+    want = _build(_solver(), mesh, rho).potential(0.5).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
 def test_errors_reported():
     mesh, rho = _mesh("eight_blocks")
     s = _solver()
