@@ -86,6 +86,7 @@ void free_blocks(bhg::Tree &t) {
   release(t.d_fid);
   release(t.d_fld);
   release(t.d_pos);
+  release(t.d_child);
   t.nb_cap = 0;
 }
 
@@ -118,6 +119,8 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   BH_CUDA(bhg::dev_malloc(&t.d_fid, n * sizeof(int)));
   BH_CUDA(bhg::dev_malloc(&t.d_pos, n * sizeof(int)));
   BH_CUDA(bhg::dev_malloc(&t.d_fld, n * sizeof(int4)));
+  // top nodes: (nb_f - 1)/7 per field, so fewer than nb/4 of them in all
+  BH_CUDA(bhg::dev_malloc(&t.d_child, 2 * n * sizeof(int)));
   t.nb_cap = nb;
   return BH_OK;
 }
@@ -207,7 +210,7 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64)
   const int64_t n_top = t.n_nodes - (int64_t)bhg::kNodesPerBlock * t.nb;
   BH_CUDA(bhg::launch_top_tree(s, t.nb, t.max_block_level, n_top, t.d_key[0], t.d_blk, t.d_count,
                                t.d_prestart, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec,
-                               t.d_flags, fa));
+                               t.d_flags, fa, t.d_child, t.nb_cap / 4));
   return BH_OK;
 }
 
@@ -335,7 +338,8 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
                                      t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, t.d_pos));
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
   BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
-                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig));
+                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig,
+                                max_level, t.d_child, t.nb_cap / 4));
   if ((st = enqueue_moments(ctx, density, density_is_fp64)) != BH_OK) return st;
   ctx->build_timed = timed && timing_mark(ctx, 1);
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -16,13 +16,16 @@
 //      in pre-order;
 //   3. an exclusive scan gives every block the pre-order index of its first
 //      node (k_prestart_scan), from which top nodes get their skip pointers
-//      (k_top_nodes);
+//      (k_top_nodes) and their child lists (k_top_children: one binary
+//      search per top node and octant, all in parallel);
 //   4. one CTA per block reduces its 512 cells to 64, 8 and 1 nodes in shared
 //      memory (k_blocks), and one short launch per level reduces the top
-//      nodes, deepest level first (k_top_moments).  (Measured alternatives
-//      that were not faster: a single CTA walking the levels with barriers;
-//      child lists found by key searches in k_top_nodes instead of following
-//      skip pointers, which cost more there than they saved here.)
+//      nodes, deepest level first (k_top_moments), reading each node's
+//      children from its list.  (Measured: following skip pointers from the
+//      first child instead took 13 us more per build -- a chain of 8
+//      dependent loads per node and level; so did searching the children
+//      one after another in one thread; a single CTA walking the levels with
+//      barriers was not faster.)
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
@@ -272,6 +275,59 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
     aux[id] = make_float2(pow2f(-k), 0.0f);
     lvl[id] = (uint8_t)k;
   }
+}
+
+// Child lists of the top nodes, for the moment pass: entry 8 slot + o holds
+// the pre-order index of child o of the top node with compact index
+// slot = prestart[p] - 585 p + r (the r-th top node that starts at block p,
+// level k = j0 + r; prestart[p] - 585 p counts the top nodes before p).
+// Child o's cube starts at key kp + o 8^(21-k-1), so its first block q is
+// found by one binary search, and the child is q's top node of level k + 1
+// or, if q is a block of level k + 1, q's root.  One thread per (top node,
+// octant), all independent: the moment pass then reads its children
+// directly instead of chasing skip pointers one after another.
+__global__ void k_top_children(int nb, const unsigned long long *__restrict__ key,
+                               const int4 *__restrict__ blk, const int *__restrict__ count,
+                               const int *__restrict__ prestart, int64_t n_nodes,
+                               const int *__restrict__ fstart, const int *__restrict__ fid,
+                               const int *__restrict__ orig, int *__restrict__ child,
+                               int64_t child_slots, unsigned *flags) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)nb * 8) return;
+  const int p = (int)(tid >> 3), o = (int)(tid & 7);
+  const int r = blockIdx.y;
+  const int cnt = count[p];
+  if (r >= cnt) return;
+  const int lb = blk[p].x, k = lb - cnt + r;
+  const int fend = fstart[fid[orig[p]] + 1];
+  const int64_t slot = (int64_t)prestart[p] - (int64_t)kNodesPerBlock * p + r;
+  if (k < 0 || k >= kKeyLevels || slot < 0 || slot >= child_slots) {
+    atomicOr(flags, kErrIndex);
+    return;
+  }
+  const unsigned long long start = key[p] + (unsigned long long)o * key_span(k + 1);
+  int q = p;
+  if (o > 0) {
+    int a = p + 1, e = fend;
+    while (a < e) {
+      const int m = (a + e) >> 1;
+      if (key[m] < start) a = m + 1; else e = m;
+    }
+    q = a;
+  }
+  if (q >= fend || key[q] != start) {  // a complete tiling starts every cube with a block
+    atomicOr(flags, kErrIndex);
+    return;
+  }
+  const int lq = blk[q].x, cq = count[q];
+  int64_t idx = -1;
+  if (k + 1 < lq && k + 1 >= lq - cq) idx = (int64_t)prestart[q] + (k + 1 - (lq - cq));
+  else if (k + 1 == lq) idx = (int64_t)prestart[q] + cq;
+  if (idx <= 0 || idx >= n_nodes) {
+    atomicOr(flags, kErrIndex);
+    return;
+  }
+  child[8 * slot + o] = (int)idx;
 }
 
 // Moments of one internal node from its 8 children (Eq. 5), children in
@@ -637,15 +693,15 @@ __global__ void __launch_bounds__(kBlockThreads)
 
 // The top node of sorted block p at `level` (the block starts cnt = count[p]
 // top nodes, levels lb - cnt .. lb - 1): its children are top nodes one level
-// down or block roots, found by following skip pointers from the first child
-// (the next node).
+// down or block roots, read from its child list (k_top_children).
 __device__ __forceinline__ void top_moment(int p, int level, const unsigned long long *key,
                                            const int4 *blk, const int *count,
                                            const int *prestart, int64_t n_nodes,
                                            double4_32a *mom, WalkRec *rec, float2 *aux,
                                            double *q64, WalkQuad *qrec, unsigned *flags,
                                            const int4 *fld, const unsigned long long *mmax,
-                                           float inv_theta) {
+                                           float inv_theta, const int *__restrict__ child_list,
+                                           int64_t child_slots) {
   const int cnt = count[p];
   const int lb = blk[p].x;
   const int j0 = lb - cnt;
@@ -656,17 +712,23 @@ __device__ __forceinline__ void top_moment(int p, int level, const unsigned long
   const double cy = centre_coord((int)(compact3(kp >> 1) >> sh), level);
   const double cz = centre_coord((int)(compact3(kp >> 2) >> sh), level);
   double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-  int64_t c = id + 1;
-  int64_t child[8];  // found by following skip pointers, kept for the quadrupoles
+  const int64_t slot = id - (int64_t)kNodesPerBlock * p;
+  if (slot < 0 || slot >= child_slots) {
+    atomicOr(flags, kErrIndex);
+    return;
+  }
+  int64_t child[8];  // from the child list, kept for the quadrupoles
   for (int o = 0; o < 8; ++o) {
+    const int64_t c = child_list[8 * slot + o];
     if (c <= 0 || c >= n_nodes) {
       atomicOr(flags, kErrIndex);
       return;
     }
     child[o] = c;
-    const double4_32a ch = mom[c];
+  }
+  for (int o = 0; o < 8; ++o) {
+    const double4_32a ch = mom[child[o]];
     accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
-    c = rec[c].skip;
   }
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
   const int64_t skip = rec[id].skip;
@@ -700,14 +762,15 @@ __global__ void k_top_moments(int nb, int level, const unsigned long long *__res
                               float2 *__restrict__ aux, double *__restrict__ q64,
                               WalkQuad *__restrict__ qrec, unsigned *flags,
                               const int4 *__restrict__ fld,
-                              const unsigned long long *__restrict__ mmax, float inv_theta) {
+                              const unsigned long long *__restrict__ mmax, float inv_theta,
+                              const int *__restrict__ child_list, int64_t child_slots) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int cnt = count[p];
   const int lb = blk[p].x;
   if (cnt == 0 || level < lb - cnt || level >= lb) return;
   top_moment(p, level, key, blk, count, prestart, n_nodes, mom, rec, aux, q64, qrec, flags, fld,
-             mmax, inv_theta);
+             mmax, inv_theta, child_list, child_slots);
 }
 
 // Largest cell mass m = rho h^3 of each field (FP64, rounded as in k_blocks),
@@ -785,10 +848,16 @@ cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
-                             unsigned *flags, const FieldArgs &fa, const int *orig) {
+                             unsigned *flags, const FieldArgs &fa, const int *orig,
+                             int max_level, int *child, int64_t child_slots) {
   k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec,
                                                  aux, lvl, flags, fa.nfields, fa.fstart, fa.fid,
                                                  orig, fa.fld);
+  if (max_level > 0) {  // a block starts at most max_level top nodes
+    const dim3 grid((unsigned)grid_for((int64_t)nb * 8, 256), (unsigned)max_level);
+    k_top_children<<<grid, 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, fa.fstart,
+                                         fa.fid, orig, child, child_slots, flags);
+  }
   return cudaGetLastError();
 }
 
@@ -825,11 +894,11 @@ cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top
                             const unsigned long long *key, const int4 *blk, const int *count,
                             const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
                             float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
-                            const FieldArgs &fa) {
+                            const FieldArgs &fa, const int *child, int64_t child_slots) {
   if (n_top <= 0) return cudaSuccess;
   for (int lev = max_level - 1; lev >= 0; --lev) {
     const cudaError_t e = launch_top_moments(s, nb, lev, key, blk, count, prestart, n_nodes, mom,
-                                             rec, aux, q64, qrec, flags, fa);
+                                             rec, aux, q64, qrec, flags, fa, child, child_slots);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -838,11 +907,12 @@ cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags,
-                               const FieldArgs &fa) {
+                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa,
+                               const int *child, int64_t child_slots) {
   k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
                                                    n_nodes, mom, rec, aux, q64, qrec, flags,
-                                                   fa.fld, fa.mmax, fa.inv_theta);
+                                                   fa.fld, fa.mmax, fa.inv_theta, child,
+                                                   child_slots);
   return cudaGetLastError();
 }
 

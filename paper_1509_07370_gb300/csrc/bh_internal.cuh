@@ -87,6 +87,7 @@ struct Tree {
   int4 *d_blk = nullptr;
   int *d_orig = nullptr;
   int *d_pos = nullptr;         // sorted position of each caller block
+  int *d_child = nullptr;       // child lists of the top nodes: 8 per top node (2 nb_cap ints)
   unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total
   unsigned *h_flags = nullptr;  // pinned mirror of d_flags
   // fields
@@ -183,10 +184,14 @@ cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long lo
                                   const FieldArgs &fa, int *pos = nullptr);
 cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
                                  unsigned *flags);
+// Skip pointers of the top nodes, and their child lists: child[8 slot + o]
+// (child_slots = capacity in top nodes) for the moment pass; max_level =
+// the largest block level.
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
-                             unsigned *flags, const FieldArgs &fa, const int *orig);
+                             unsigned *flags, const FieldArgs &fa, const int *orig,
+                             int max_level, int *child, int64_t child_slots);
 // Largest cell mass of every field (atomic max on fa.mmax, which the caller
 // zeroes first); caller block order.
 cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
@@ -205,11 +210,12 @@ cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top
                             const unsigned long long *key, const int4 *blk, const int *count,
                             const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
                             float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
-                            const FieldArgs &fa);
+                            const FieldArgs &fa, const int *child, int64_t child_slots);
 cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
                                const int4 *blk, const int *count, const int *prestart,
                                int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa);
+                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa,
+                               const int *child, int64_t child_slots);
 
 // ---- walk kernels (bh_walk.cu) ---------------------------------------------
 cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,
