@@ -24,8 +24,11 @@
 //      children from its list.  (Measured: following skip pointers from the
 //      first child instead took 13 us more per build -- a chain of 8
 //      dependent loads per node and level; so did searching the children
-//      one after another in one thread; a single CTA walking the levels with
-//      barriers was not faster.)
+//      one after another in one thread.  Not faster either: a single CTA
+//      walking the levels with barriers, and a cluster of 8 CTAs doing so
+//      with cluster barriers (0.330-0.345 ms per build instead of 0.310):
+//      spread over the whole GPU a level's FP64 work finishes sooner than
+//      the launches it saves.)
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
