@@ -742,7 +742,7 @@ def learned_arm(args):
                           "speedup": L_["value"] / res["same"]["value"]},
         "accuracy_all_cells": all_cells,
         "clocks": clocks, "e2e": e2e,
-        "gpu_launches": (7 + (maxlev - 3) + 1) * args.steps,
+        "gpu_launches": (8 + (maxlev - 3) + 1) * args.steps,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -864,9 +864,10 @@ def main():
             else "quadrupole" if quad else "monopole")
     traffic = captured_traffic(w.name, args.theta, mode) if not args.vote else None
     _, nn, maxlev = solver.tree_size()
-    # keys, sort, tiling, scan, top nodes, largest mass, blocks, one top-moment
-    # launch per block level (max block level = maxlev - 3), walk
-    launches_per_step = 7 + (maxlev - 3) + 1
+    # keys, sort, tiling, scan, top nodes, top-node child lists, largest mass,
+    # blocks, one top-moment launch per block level (max block level =
+    # maxlev - 3), walk
+    launches_per_step = 8 + (maxlev - 3) + 1
 
     # the plain walk (monopole, per-cell) at the theta of equal accuracy
     plain = None
