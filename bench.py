@@ -961,6 +961,9 @@ def main():
             "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",
                          "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": traffic,
+                         "frac_with_kahan": (flops + 3 * n_int) / walk_s / peak,
+                         "mufu_bound_ms": n_int / (16 * props.multi_processor_count
+                                                   * sm_mhz * 1e6) * 1e3,
                          "traffic_unit": "bytes per walk launch (ncu dram read+write)",
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz "
