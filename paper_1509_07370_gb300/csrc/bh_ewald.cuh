@@ -64,47 +64,38 @@ __device__ __forceinline__ float half_hi(uint32_t w) {
   return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
 }
 
-// The 64-byte entry of centre (cx, cy, cz), as two 32-byte loads, widened to
-// the 27 binary32 coefficients C[9k + 3j + i].
+// The 64-byte entry of centre (cx, cy, cz), as two 32-byte loads (raw words).
 __device__ __forceinline__ void ewald_load(const unsigned char *tab, int n, int cx, int cy, int cz,
-                                           float C[27]) {
+                                           uint32_t w[16]) {
   const unsigned char *e = tab + (size_t)kEwaldEntryBytes *
                                      (unsigned)(((cz - 1) * n + (cy - 1)) * n + (cx - 1));
-  uint32_t w[16];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
     asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(w[8 * q]), "=r"(w[8 * q + 1]), "=r"(w[8 * q + 2]), "=r"(w[8 * q + 3]),
           "=r"(w[8 * q + 4]), "=r"(w[8 * q + 5]), "=r"(w[8 * q + 6]), "=r"(w[8 * q + 7])
         : "l"(e + 32 * q));
-  float H[24];
-#pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    H[2 * q] = half_lo(w[4 + q]);
-    H[2 * q + 1] = half_hi(w[4 + q]);
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int slot = ewald_half_slot(k, j, i);
-        C[9 * k + 3 * j + i] = slot >= 0 ? H[slot] : 0.0f;
-      }
-  C[0] = __uint_as_float(w[0]);
-  C[1] = __uint_as_float(w[1]);
-  C[3] = __uint_as_float(w[2]);
-  C[9] = __uint_as_float(w[3]);
 }
 
-// The interpolant at (fx, fy, fz) from its coefficients, in Horner form:
-// x first (9 quadratics), then y (3), then z.
-__device__ __forceinline__ float ewald_poly(const float C[27], float fx, float fy, float fz) {
+// Coefficient K(k, j, i) of an entry, widened to binary32 where it is used.
+__device__ __forceinline__ float ewald_coef(const uint32_t w[16], int k, int j, int i) {
+  const int f = 9 * k + 3 * j + i;
+  if (f == 0) return __uint_as_float(w[0]);
+  if (f == 1) return __uint_as_float(w[1]);
+  if (f == 3) return __uint_as_float(w[2]);
+  if (f == 9) return __uint_as_float(w[3]);
+  const int slot = ewald_half_slot(k, j, i);
+  return (slot & 1) ? half_hi(w[4 + (slot >> 1)]) : half_lo(w[4 + (slot >> 1)]);
+}
+
+// The interpolant at (fx, fy, fz) from an entry, in Horner form: x first (9
+// quadratics), then y (3), then z.
+__device__ __forceinline__ float ewald_poly(const uint32_t w[16], float fx, float fy, float fz) {
   float px[9];
 #pragma unroll
   for (int r = 0; r < 9; ++r)
-    px[r] = __fmaf_rn(fx, __fmaf_rn(fx, C[3 * r + 2], C[3 * r + 1]), C[3 * r]);
+    px[r] = __fmaf_rn(fx, __fmaf_rn(fx, ewald_coef(w, r / 3, r % 3, 2), ewald_coef(w, r / 3, r % 3, 1)),
+                      ewald_coef(w, r / 3, r % 3, 0));
   float py[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -115,12 +106,13 @@ __device__ __forceinline__ float ewald_poly(const float C[27], float fx, float f
 // chi at |displacement| (ax, ay, az), each >= 0.
 __device__ __forceinline__ float ewald_chi(const unsigned char *tab, int n, float s, float ax,
                                            float ay, float az) {
-  float fx, fy, fz, C[27];
+  float fx, fy, fz;
+  uint32_t w[16];
   const int cx = ewald_axis(ax, s, n, fx);
   const int cy = ewald_axis(ay, s, n, fy);
   const int cz = ewald_axis(az, s, n, fz);
-  ewald_load(tab, n, cx, cy, cz, C);
-  return ewald_poly(C, fx, fy, fz);
+  ewald_load(tab, n, cx, cy, cz, w);
+  return ewald_poly(w, fx, fy, fz);
 }
 
 }  // namespace

@@ -54,7 +54,8 @@ __device__ __forceinline__ void dist2_min_image(u64 tx2, float ty, float tz, u64
 // shared by the x-neighbour pair).
 __device__ __forceinline__ u64 chi_pair(const unsigned char *__restrict__ tab, int n, float s, u64 dx2,
                                         float dy, float dz, bool ua, bool ub) {
-  float dxa, dxb, fxa, fxb, fy, fz, C[27];
+  float dxa, dxb, fxa, fxb, fy, fz;
+  uint32_t C[16];
   upk(dx2, dxa, dxb);
   const int ca = ewald_axis(fabsf(dxa), s, n, fxa);
   const int cb = ewald_axis(fabsf(dxb), s, n, fxb);
