@@ -66,3 +66,16 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
     a.theta = 0.7
     assert bench.reference_arm(a) is None
     assert capsys.readouterr().out == ""
+
+
+def test_committed_walk_profiles_match_the_sources():
+    """The ncu summaries the benchmark takes its DRAM traffic from are of the
+    walk sources as they are now (their recorded hash), for the benchmark's
+    workloads; any other workload or mode gets no traffic figure."""
+    import bench
+    w = "maclaurin_e0.9_L2+3"
+    assert bench.captured_traffic(w, 0.72, "quadrupole") is not None
+    assert bench.captured_traffic(w, 0.7, "periodic64") is not None
+    assert bench.captured_traffic(w, 0.7, "quadrupole") is None
+    assert bench.captured_traffic(w, 0.72, "monopole") is None
+    assert bench.captured_traffic("cloud_core", 0.72, "quadrupole") is None
