@@ -165,3 +165,21 @@ def test_zero_field_and_one_block():
         ni, _ = s.walk_counts(theta)
         assert np.array_equal(ni.cpu().numpy(), nio)
         assert np.abs(phi - po).max() <= 1e-5 * np.abs(po).max()
+
+
+def test_physical_box_and_G():
+    """A box of side 2.5 at (1, -2, 0.5) and G = 3: the walk works in box
+    units and scales by -G/L like the oracle (which takes the same box)."""
+    m = mg.refined_mesh(1, 2, lambda lev, ijk: np.all(ijk == 1, axis=1), name="corner11")
+    rho = mg.random_density(m, seed=21)
+    lo, L = (1.0, -2.0, 0.5), 2.5
+    s = B.Solver(periodic=True)
+    s.build(m.level, m.ijk, torch.as_tensor(np.asarray(rho, np.float32).reshape(-1)).cuda(), lo, L)
+    phi = s.potential(0.6, G=3.0).cpu().numpy()
+    t = O.Tree(m.level, m.ijk, np.asarray(rho, np.float32).astype(np.float64), lo, L)
+    po = t.walk_periodic(0.6, G=3.0)[0]
+    assert np.abs(phi - po).max() <= 1e-5 * np.abs(po).max()
+    # and the unit box scales: Phi_L = Phi_1 * L^2 (masses ~ L^3, distances ~ L)
+    s1 = _solver(m, rho)
+    phi1 = s1.potential(0.6, G=3.0).cpu().numpy()
+    assert np.abs(phi - phi1 * L * L).max() <= 1e-5 * np.abs(phi).max()
