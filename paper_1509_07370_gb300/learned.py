@@ -10,9 +10,11 @@ its monopole.  Everything runs in the library's own kernels:
     optimiser steps.
 Training fields: homogeneous oblate spheroids (the Maclaurin family of the
 accuracy test) with seeded semi-axis a1 in [0.12, 0.3] and eccentricity in
-[0.3, 0.95], on meshes of 32^3 cells refined twice at the surface; half of
-each field's targets are random cells, half lie in its densest blocks (where
-the walk's largest errors are).
+[0.3, 0.95], on meshes of 32^3 cells refined twice at the surface.  Each
+field's targets: random cells, cells of its densest blocks, and the cells
+where the plain walk at the training theta errs most against the exhaustive
+direct sum (computed by the library itself at a theta below which no node is
+accepted) -- the pairs that decide the largest errors.
 """
 from __future__ import annotations
 
@@ -49,10 +51,26 @@ def dense_cells(density: np.ndarray, nblocks: int = 8) -> np.ndarray:
     return (top[:, None] * 512 + np.arange(512)[None, :]).reshape(-1)
 
 
+def worst_cells(w: mg.Workload, density, theta: float, k: int, device: int = 0) -> np.ndarray:
+    """The k cells where the plain monopole walk at theta has the largest
+    relative error against the exhaustive direct sum, which the library
+    computes at theta = 2^-(deepest cell level): there the smallest internal
+    node has l/theta = 2, more than any box-unit distance, so no node is
+    accepted and every cell meets every other cell singly."""
+    plain = bh.Solver(device=device)
+    plain.build(w.mesh.level, w.mesh.ijk, density, w.mesh.box_lo, w.mesh.box_len)
+    _, _, maxlev = plain.tree_size()
+    direct = plain.potential(2.0 ** -maxlev).double()
+    err = (plain.potential(theta).double() / direct - 1.0).abs()
+    plain.close()
+    return np.sort(err.argsort(descending=True)[:k].cpu().numpy())
+
+
 def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: int,
-             cap: int = 1 << 20, dense=None):
+             cap: int = 1 << 20, dense=None, extra=None):
     """(features, z) of the accepted pairs of `ntargets` cells: random ones,
-    or half random and half drawn from `dense` (cell indices) if given."""
+    or half random and half drawn from `dense` (cell indices) if given; plus
+    the cells in `extra`, if given."""
     import torch
     rng = np.random.Generator(np.random.PCG64(seed))
     n = min(ntargets, ncells)
@@ -62,6 +80,8 @@ def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: 
         cells = np.unique(np.concatenate([rng.choice(ncells, n - n // 2, replace=False),
                                           rng.choice(dense, min(n // 2, len(dense)),
                                                      replace=False)]))
+    if extra is not None:
+        cells = np.unique(np.concatenate([cells, np.asarray(extra, dtype=cells.dtype)]))
     tg = torch.as_tensor(cells, dtype=torch.int64, device=solver.device)
     feat, eps, _ = solver.learn_pairs(theta, tg, cap)
     s = feat[:, 3]
@@ -69,18 +89,21 @@ def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: 
 
 
 def make_dataset(nfields: int = 200, theta: float = 0.8, targets_per_field: int = 64,
-                 seed0: int = 9000, device: int = 0):
-    """Method-generated training pairs from `nfields` seeded fields."""
+                 seed0: int = 9000, device: int = 0, worst_per_field: int = 32):
+    """Method-generated training pairs from `nfields` seeded fields: per
+    field, `targets_per_field` random and dense-block cells plus the
+    `worst_per_field` cells where the plain walk errs most."""
     import torch
     xs, zs = [], []
     for i in range(nfields):
         w = training_field(seed0 + i)
         s = bh.Solver(quadrupole=True, device=device)
-        s.build(w.mesh.level, w.mesh.ijk,
-                torch.as_tensor(w.density.reshape(-1), dtype=torch.float32,
-                                device=s.device))
+        rho = torch.as_tensor(w.density.reshape(-1), dtype=torch.float32, device=s.device)
+        s.build(w.mesh.level, w.mesh.ijk, rho)
+        worst = (worst_cells(w, rho, theta, worst_per_field, device)
+                 if worst_per_field > 0 else None)
         x, z = pairs_of(s, w.ncells, theta, targets_per_field, seed0 + 100000 + i,
-                        dense=dense_cells(w.density))
+                        dense=dense_cells(w.density), extra=worst)
         xs.append(x)
         zs.append(z)
         s.close()
