@@ -890,7 +890,9 @@ bh_status bh_stats(const bh_ctx *ctx, bh_stats_t *out) {
     out->tests = (int64_t)c[1];
     out->cell_interactions = ctx->counts_have_cells ? (int64_t)c[2] : -1;
   }
-  int64_t b = t.nb_cap * (int64_t)(4 + 12 + 8 + 8 + 4 + 4 + 4 + 4 + 16 + 4 + 4 + 4 + 16);
+  // per block: level, ijk, 2 keys, 2 indices, count, prestart, blk, orig, fid,
+  // pos, fld, and 8 bytes of top-node child lists
+  int64_t b = t.nb_cap * (int64_t)(4 + 12 + 8 + 8 + 4 + 4 + 4 + 4 + 16 + 4 + 4 + 4 + 16 + 8);
   b += t.node_cap * (int64_t)(sizeof(double4_32a) + sizeof(bhg::WalkRec) + sizeof(float2) + 1);
   b += t.quad_cap * (int64_t)sizeof(bhg::WalkQuad) + (t.d_q64 ? t.quad_cap * 48 : 0);
   b += t.nf_cap * (int64_t)(sizeof(int) + 2 * sizeof(double)) + (t.nf_cap ? 4 : 0);
