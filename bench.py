@@ -105,18 +105,85 @@ def workload(name):
 
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
+    """SM clock and clock-event (throttle) reasons during the timed region.
+
+    Polls NVML (the driver's libnvidia-ml, through ctypes) from a thread
+    every `period_s` (default 2 ms); if NVML cannot be loaded, falls back to
+    `nvidia-smi --query-gpu ... -lms 100`.  Only reads; changes nothing."""
+
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clocks-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
+        self.period = period_s
         self.proc = None
-        fd, self.path = tempfile.mkstemp(prefix=f"bh_clocks_{index}_", suffix=".csv")
-        os.close(fd)
+        self.thread = None
+        self.samples = []           # (sm_mhz, reason bits)
+        self.max_mhz = None
+        self.path = None
+
+    def _nvml(self):
+        import ctypes
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                lib = None
+        if lib is None or lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        found = False
+        try:  # the CUDA device by its PCI address (NVML numbers every GPU of the host)
+            import torch
+            pr = torch.cuda.get_device_properties(self.index)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            found = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        except (ImportError, AttributeError, RuntimeError):
+            found = False
+        if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index),
+                                                           ctypes.byref(h)) != 0:
+            return None
+        try:
+            reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _poll(self, lib, h, reasons):
+        import ctypes
+        clk = ctypes.c_uint()
+        bits = ctypes.c_ulonglong()
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM = 1
+            self.max_mhz = float(mx.value)
+        while not self.stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0:
+                r = reasons(h, ctypes.byref(bits))
+                self.samples.append((float(clk.value), int(bits.value) if r == 0 else 0))
+            time.sleep(self.period)
 
     def __enter__(self):
+        import threading
+        nv = None
         try:
+            nv = self._nvml()
+        except (OSError, AttributeError):
+            nv = None
+        if nv is not None:
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=nv, daemon=True)
+            self.thread.start()
+            return self
+        try:
+            fd, self.path = tempfile.mkstemp(prefix=f"bh_clocks_{self.index}_", suffix=".csv")
+            os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
@@ -127,6 +194,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self.thread is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -136,7 +206,17 @@ class ClockSampler:
             self.f.close()
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        if self.thread is not None:
+            if not self.samples:
+                return None
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({n for _, b in self.samples for bit, n in self.REASONS.items()
+                              if b & bit})
+            return {"sm_mhz": float(np.median(sm)),
+                    "sm_max_mhz": self.max_mhz if self.max_mhz else float(max(sm)),
+                    "samples": len(sm), "period_ms": 1e3 * self.period, "source": "nvml",
+                    "reasons": reasons}
+        if self.proc is None or not self.path or not os.path.exists(self.path):
             return None
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -155,7 +235,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "period_ms": 100.0, "source": "nvidia-smi",
+                "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------- captured traffic --
@@ -167,8 +248,10 @@ def captured_traffic(workload_name, theta, mode):
     profile, files = {
         "quadrupole": ("walk_pair_quadrupole_theta0.72_maclaurin_2M.md",
                        ("bh_walk.cu", "bh_walk_common.cuh")),
+        "monopole": ("walk_pair_monopole_theta0.24_maclaurin_2M.md",
+                     ("bh_walk.cu", "bh_walk_common.cuh")),
         "periodic64": ("walk_periodic_theta0.7_maclaurin_2M.md",
-                       ("bh_walk_periodic.cu", "bh_ewald.cuh")),
+                       ("bh_walk_periodic.cu", "bh_ewald.cuh", "bh_walk_common.cuh")),
     }.get(mode, (None, None))
     if profile is None:
         return None
@@ -215,27 +298,50 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
     rng = np.random.default_rng(1234)
     n = w.ncells
     probe = rng.choice(n, min(n, 2000), replace=False)
-    walk(probe[:64])                                     # start the OpenMP threads
-    t0 = time.perf_counter()
-    walk(probe)
-    per = (time.perf_counter() - t0) / len(probe)
-    k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
-    tg = np.sort(rng.choice(n, k, replace=False))
-    t0 = time.perf_counter()
-    ref, ni, nt = walk(tg)
-    t_walk = time.perf_counter() - t0
-    t_step = t_build + t_walk * (n / k)
-    t0 = time.perf_counter()
-    walk(probe, threads=1)
-    per1 = (time.perf_counter() - t0) / len(probe)
+    per = walk_time_per_cell(walk, rng, n)
     kind = "periodic (Ewald table), monopole" if periodic else (
         "quadrupole" if quad else "monopole")
-    out = {"value": n / t_step, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
+    if t_build + per * n <= 1.5 * cpu_seconds:
+        # whole steps (tree build + walk of every cell), repeated to ~cpu_seconds
+        tg = np.arange(n)
+        steps, t_total, t_walk = 0, 0.0, 0.0
+        while steps == 0 or t_total < cpu_seconds:
+            t0 = time.perf_counter()
+            tr = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+            t1 = time.perf_counter()        # (the oracle's walk reduces the quadrupoles)
+            if periodic:
+                ref, ni, nt = tr.walk_periodic(theta, targets=tg, ng=ewald_grid)
+            else:
+                ref, ni, nt = tr.walk(theta, targets=tg, quad=quad)
+            t2 = time.perf_counter()
+            t_walk += t2 - t1
+            t_total += t2 - t0
+            steps += 1
+            del tr
+        k = n
+        value = n * steps / t_total
+        sample = (f"{steps} whole steps: tree + FP64 moments{' + quadrupoles' if quad else ''}"
+                  f" and the per-cell walk of all {n} cells ({kind}, theta {theta}), "
+                  f"{t_total:.2f} s in all ({t_walk:.2f} s in the walk call"
+                  f"{', quadrupoles included' if quad else ''}); no extrapolation")
+    else:
+        # a whole step would take too long: the walk of a random sample, scaled
+        k = int(min(n, max(len(probe), cpu_seconds / max(per, 1e-9))))
+        tg = np.sort(rng.choice(n, k, replace=False))
+        t0 = time.perf_counter()
+        ref, ni, nt = walk(tg)
+        t_walk = time.perf_counter() - t0
+        value = n / (t_build + t_walk * (n / k))
+        sample = (f"tree + FP64 moments of all {n} cells ({t_build:.2f} s) and the per-cell walk "
+                  f"of {k} random cells (seed 1234, {kind}, theta {theta}, {t_walk:.2f} s), "
+                  f"the walk time scaled by {n}/{k}: a whole step would exceed "
+                  f"{1.5 * cpu_seconds:.0f} s")
+    per1 = walk_time_per_cell(lambda tg: walk(tg, threads=1), rng, n)
+    out = {"value": value, "unit": "cells/s", "cores": O.max_threads(), "kind": "oracle",
            "value_1core": n / (t_build + per1 * n),
-           "sample": f"tree+FP64 moments of all {n} cells; per-cell walk of {k} random cells "
-                     f"(seed 1234, {kind}, theta {theta}) "
-                     f"extrapolated to {n}; build {t_build:.2f}s, walk {t_walk:.2f}s; "
-                     f"value_1core: the walk of {len(probe)} cells on one thread"}
+           "sample": sample + "; value_1core: the per-cell walk time on one thread (timed on "
+                              "2,000 and 22,000 random cells) times every cell, plus the "
+                              "tree build"}
     if phi_gpu is not None and periodic:
         # the periodic field has zero mean and changes sign: errors relative
         # to its largest magnitude; a smaller direct sample (each direct
@@ -276,6 +382,25 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
                 np.max(np.abs(phi_plain[dt] / d - 1.0)))
             out["accuracy"]["plain_theta"] = plain_theta
     return out
+
+
+def walk_time_per_cell(walk, rng, n):
+    """Per-cell time of the oracle's walk on the host cores: the difference of
+    two timed calls on 2,000 and 22,000 random cells, over the 20,000 cells
+    between them (each call also pays fixed costs: thread start-up, and for
+    the quadrupole walk one reduction of every node's quadrupole)."""
+    a = rng.choice(n, min(n, 2000), replace=False)
+    b = rng.choice(n, min(n, 22000), replace=False)
+    walk(a[:64])                                         # start the OpenMP threads
+    t0 = time.perf_counter()
+    walk(a)
+    ta = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    walk(b)
+    tb = time.perf_counter() - t0
+    if len(b) > len(a) and tb > ta:
+        return (tb - ta) / (len(b) - len(a))
+    return tb / len(b)
 
 
 def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=False,
@@ -332,7 +457,14 @@ def direct_targets(w, rng, nrandom=2000, ndense=8):
 
 
 def reference_arm(args):
-    """The reference arm: the CPU oracle, on the host cores, same workload."""
+    """The reference arm: the CPU oracle, on the host cores, same workload and
+    metric.  A step is what the GPU step computes -- the tree with FP64
+    moments (and quadrupoles) and the per-cell walk of every cell -- timed
+    whole, so ms_per_step is time spent.  If whole steps would take the run
+    past about two and a half minutes, fewer steps are timed (`steps` says
+    how many); only if a single step is longer than half of that does a step
+    walk a random sample of the cells, and the rate is then the cells walked
+    over the time spent."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -342,39 +474,46 @@ def reference_arm(args):
     n = w.ncells
     rng = np.random.default_rng(99)
     quad = not args.monopole
-    tree = O.Tree(w.mesh.level, w.mesh.ijk, rho)
-    probe = rng.choice(n, 500, replace=False)
+    budget = 150.0
     t0 = time.perf_counter()
-    tree.walk(args.theta, targets=probe, quad=quad)
-    per = (time.perf_counter() - t0) / 500
-    budget = 150.0 / max(1, args.steps + args.warmup)       # whole run within minutes
-    k = int(min(n, max(500, budget / max(per, 1e-9))))
+    tree = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+    if quad:
+        tree.quadrupoles()
+    t_build = time.perf_counter() - t0
+    per = walk_time_per_cell(lambda tg: tree.walk(args.theta, targets=tg, quad=quad), rng, n)
+    del tree
+    est = t_build + per * n                                # one whole step
+    warmup = min(args.warmup, 1)
+    if est <= budget / 2:
+        k = n
+        steps = max(1, min(args.steps, int(budget / est) - warmup))
+    else:
+        steps, warmup = 1, 0
+        k = int(max(1000, min(n, (budget / 2 - t_build) / max(per, 1e-9))))
     times = []
-    for s in range(args.warmup + args.steps):
-        tg = rng.choice(n, k, replace=False)
+    for s in range(warmup + steps):
+        tg = np.arange(n) if k == n else np.sort(rng.choice(n, k, replace=False))
         t0 = time.perf_counter()
-        tr = O.Tree(w.mesh.level, w.mesh.ijk, rho)
-        if quad:
-            tr.quadrupoles()
-        tb = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        tr.walk(args.theta, targets=tg, quad=quad)
-        tw = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(tb + tw * n / k)
+        tr = O.Tree(w.mesh.level, w.mesh.ijk, rho, w.mesh.box_lo, w.mesh.box_len)
+        tr.walk(args.theta, targets=tg, quad=quad)          # reduces the quadrupoles too
+        if s >= warmup:
+            times.append(time.perf_counter() - t0)
+        del tr
     t = float(np.sum(times))
-    value = n * args.steps / t
+    value = k * steps / t
+    what = (f"per step: tree + FP64 moments{' + quadrupoles' if quad else ''} of all {n} cells "
+            + ("and the walk of every cell (a whole step)" if k == n else
+               f"and the walk of {k} random cells (a whole step would take about {est:.0f} s)")
+            + f"; {steps} steps timed after {warmup} untimed")
     line = {"impl": "reference", "metric": "cell potentials/sec", "value": value,
-            "unit": "cells/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "unit": "cells/s", "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * t / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "cells": n, "theta": args.theta,
                        "walk": "FP64, per-cell opening test"
                                + (", quadrupole nodes" if quad else ", monopole nodes")},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": O.max_threads(),
-                             "kind": "oracle",
-                             "sample": f"per step: full tree build + walk of {k} random cells "
-                                       f"extrapolated to {n}"},
+                             "kind": "oracle", "sample": what},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -433,7 +572,7 @@ def batched_arm(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s = bh.Solver(device=dev.index, stream=stream)
     s.build_batch(nb, level, ijk, d_rho, lo, ln)
-    wpc = s.autotune(theta)
+    wpc, npairs = s.autotune(theta)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.solve_graph(d_rho, theta, 1.0, out)
@@ -551,7 +690,8 @@ def batched_arm(args):
                        "field_cells": sorted({w.ncells for w in ws}), "theta": theta,
                        "walk": "binary32, Kahan sum, per-cell opening test, monopole nodes",
                        "step": "one CUDA-graph launch: moments + walk of all fields",
-                       "tuned_warps_per_cta": wpc, "l2": "flushed between steps"},
+                       "tuned_warps_per_cta": wpc, "tuned_target_pairs_per_lane": npairs,
+                       "l2": "flushed between steps"},
             "vs_plain": {"how": "the same fields one after the other: bh_build + bh_potential",
                          "value": p_value, "ms_per_step": p_ms, "speedup": value / p_value,
                          "identical_potentials": bool(same),
@@ -889,6 +1029,7 @@ def main():
                                "potential": float(np.mean(p_walk))},
                  "interactions_per_cell": pi / n, "tests_per_cell": pt / n,
                  "roofline_frac": pflops / (float(np.mean(p_walk)) * 1e-3) / peak,
+                 "traffic": captured_traffic(w.name, args.plain_theta, "monopole"),
                  "speedup": value / p_value}
         psolver.close()
 
@@ -965,6 +1106,10 @@ def main():
                          "mufu_bound_ms": n_int / (16 * props.multi_processor_count
                                                    * sm_mhz * 1e6) * 1e3,
                          "traffic_unit": "bytes per walk launch (ncu dram read+write)",
+                         "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of "
+                                            "the ncu capture summarised in profiles/ for this "
+                                            "walk source (its sha256 checked) and workload; "
+                                            "null when the source or workload differs"),
                          "peak_basis": f"{FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{props.multi_processor_count} SMs x {sm_mhz:.0f} MHz "
                                        "(median SM clock measured during the timed region)"},

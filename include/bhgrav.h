@@ -176,10 +176,14 @@ bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp6
 bh_status bh_sync_status(bh_ctx *ctx);
 
 /* Times the binary32 per-cell walk of the current tree at this theta for
- * CTAs of 2, 4, 8 and 16 warps (one warp per 64-cell octant) and keeps the
- * fastest for later walks; *warps_per_cta (may be NULL) receives it (0 for
- * walk modes with a fixed launch shape).  Allocates a scratch output once. */
-bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta);
+ * every launch shape it offers -- CTAs of 2, 4, 8 and 16 warps, and warps
+ * that walk for 64 targets (a 4x4x4 octant of a block, one pair of
+ * x-neighbours per lane) or 128 targets (a 8x4x4 slab, two pairs per lane;
+ * not for the periodic walk) -- and keeps the fastest for later walks.  All
+ * shapes give bit-identical potentials.  shape (may be NULL) receives two
+ * ints: {warps per CTA, target pairs per lane} ({0, 0} for walk modes with a
+ * fixed launch shape).  Allocates a scratch output once. */
+bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape);
 
 /* bh_update_density + bh_potential as ONE CUDA graph launch: the first call
  * (or a call with a different density/out pointer, density type, theta or G)

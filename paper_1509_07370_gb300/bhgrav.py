@@ -189,10 +189,11 @@ def bh_sync_status(ctx) -> None:
     _check(ctx, load().bh_sync_status(ctx), "bh_sync_status")
 
 
-def bh_autotune(ctx, theta: float) -> int:
-    w = ctypes.c_int()
-    _check(ctx, load().bh_autotune(ctx, float(theta), ctypes.byref(w)), "bh_autotune")
-    return w.value
+def bh_autotune(ctx, theta: float) -> tuple:
+    """Returns the chosen (warps per CTA, target pairs per lane)."""
+    sh = (ctypes.c_int * 2)()
+    _check(ctx, load().bh_autotune(ctx, float(theta), sh), "bh_autotune")
+    return int(sh[0]), int(sh[1])
 
 
 def bh_solve_graph(ctx, density, theta: float, G: float, out) -> None:
@@ -432,7 +433,8 @@ class Solver:
     def sync_status(self):
         bh_sync_status(self._ctx)
 
-    def autotune(self, theta: float) -> int:
+    def autotune(self, theta: float) -> tuple:
+        """Tunes the walk's launch shape: (warps per CTA, target pairs per lane)."""
         return bh_autotune(self._ctx, theta)
 
     def solve_graph(self, density, theta: float, G: float = 1.0, out=None):

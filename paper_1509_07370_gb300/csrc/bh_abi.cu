@@ -412,16 +412,17 @@ static bh_status set_ewald(bh_ctx *ctx, int n, int N) {
 // The walk of the context's options on stream s: the potential into out, or
 // with n_int / n_test (and optional n_leaf) the per-cell counts.
 static cudaError_t enqueue_walk(bh_ctx *ctx, cudaStream_t s, double G, void *out,
-                                int32_t *n_int, int32_t *n_test, int32_t *n_leaf, int wpc) {
+                                int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
+                                bhg::WalkShape shape) {
   bhg::Tree &t = ctx->tree;
   if (ctx->opt.periodic)
     return bhg::launch_walk_periodic(s, ctx->opt, t.nb, t.d_rec, t.d_blk, t.d_orig,
                                      field_args(t), ctx->d_ewald, ctx->ewald_n, G, out, n_int,
-                                     n_test, n_leaf, wpc);
+                                     n_test, n_leaf, shape.warps);
   if (!n_int && ctx->opt.learned == 2) return bhg::launch_walk_learned_tc(s, ctx, G, out);
   if (!n_int && ctx->opt.learned) return bhg::launch_walk_learned(s, ctx, G, out);
   return bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
-                          t.d_orig, field_args(t), G, out, n_int, n_test, n_leaf, wpc);
+                          t.d_orig, field_args(t), G, out, n_int, n_test, n_leaf, shape);
 }
 
 bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_stream) {
@@ -590,7 +591,7 @@ bh_status bh_potential(bh_ctx *ctx, double theta, double G, void *out) {
   if (st != BH_OK) return st;
   const bool timed = timing_mark(ctx, 2);
   if ((st = prepare(ctx, theta)) != BH_OK) return st;
-  BH_CUDA(enqueue_walk(ctx, ctx->stream, G, out, nullptr, nullptr, nullptr, ctx->tree.wpc));
+  BH_CUDA(enqueue_walk(ctx, ctx->stream, G, out, nullptr, nullptr, nullptr, ctx->tree.shape));
   ctx->potential_timed = timed && timing_mark(ctx, 3);
   ctx->last_theta = theta;
   return BH_OK;
@@ -606,7 +607,7 @@ bh_status bh_walk_counts(bh_ctx *ctx, double theta, int32_t *n_int, int32_t *n_t
   bh_status st = prepare(ctx, theta);
   if (st != BH_OK) return st;
   bhg::Tree &t = ctx->tree;
-  BH_CUDA(enqueue_walk(ctx, ctx->stream, 0.0, nullptr, n_int, n_test, n_cell, t.wpc));
+  BH_CUDA(enqueue_walk(ctx, ctx->stream, 0.0, nullptr, n_int, n_test, n_cell, t.shape));
   // totals for bh_stats
   ctx->counts_valid = false;
   if (!ctx->d_counts) BH_CUDA(bhg::dev_malloc(&ctx->d_counts, 3 * sizeof(unsigned long long)));
@@ -709,7 +710,7 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
   return BH_OK;
 }
 
-bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
+bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   bh_status st = prepare(ctx, theta);
@@ -717,6 +718,8 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
   bhg::Tree &t = ctx->tree;
   const bool tunable = ctx->opt.precision == BH_PREC_F32 &&
                        ctx->opt.criterion == BH_CRIT_PER_CELL && !ctx->opt.learned;
+  // the periodic walk has one target pair per lane; only its CTA width is tuned
+  const int npairs = ctx->opt.periodic ? 1 : 2;
   if (tunable) {
     const int64_t out_bytes = (int64_t)t.nb * bhg::kCellsPerBlock * sizeof(float);
     if (t.stage_out_bytes < out_bytes) {
@@ -730,30 +733,40 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *warps_per_cta) {
     BH_CUDA(cudaEventCreate(&e1));
     const int cand[4] = {2, 4, 8, 16};
     float best = 1e30f;
-    int best_w = 8;
-    for (int w : cand) {
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
-        BH_CUDA(cudaEventRecord(e0, ctx->stream));
-        BH_CUDA(enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
-                             w));
-        BH_CUDA(cudaEventRecord(e1, ctx->stream));
-        BH_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        tmin = ms < tmin ? ms : tmin;
-      }
-      if (tmin < best) {
-        best = tmin;
-        best_w = w;
+    bhg::WalkShape best_s;
+    best_s.warps = 8;
+    best_s.pairs = 1;
+    for (int np = 1; np <= npairs; ++np) {
+      for (int w : cand) {
+        bhg::WalkShape sh;
+        sh.warps = w;
+        sh.pairs = np;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          BH_CUDA(cudaEventRecord(e0, ctx->stream));
+          BH_CUDA(enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
+                               sh));
+          BH_CUDA(cudaEventRecord(e1, ctx->stream));
+          BH_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          tmin = ms < tmin ? ms : tmin;
+        }
+        if (tmin < best) {
+          best = tmin;
+          best_s = sh;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    t.wpc = best_w;
+    t.shape = best_s;
     drop_graph(t);
   }
-  if (warps_per_cta) *warps_per_cta = tunable ? t.wpc : 0;
+  if (shape) {
+    shape[0] = tunable ? t.shape.warps : 0;
+    shape[1] = tunable ? t.shape.pairs : 0;
+  }
   return BH_OK;
 }
 
@@ -777,7 +790,7 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
                     t.graph_fp64 == density_is_fp64 && t.graph_theta == theta && t.graph_G == G;
   if (!same) {
     drop_graph(t);
-    if (t.wpc == 0 && (st = bh_autotune(ctx, theta, nullptr)) != BH_OK) return st;
+    if (t.shape.warps == 0 && (st = bh_autotune(ctx, theta, nullptr)) != BH_OK) return st;
     cudaStream_t s = ctx->stream;
     BH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     bh_status cap = BH_OK;
@@ -789,7 +802,7 @@ bh_status bh_solve_graph(bh_ctx *ctx, const void *density, int density_is_fp64, 
       if (cap == BH_OK && e == cudaSuccess && ctx->opt.learned && !ctx->d_mlp)
         cap = fail(ctx, BH_ERR_STATE, "learned walk: call bh_set_mlp first");
       if (cap == BH_OK && e == cudaSuccess)
-        e = enqueue_walk(ctx, s, G, out, nullptr, nullptr, nullptr, t.wpc);
+        e = enqueue_walk(ctx, s, G, out, nullptr, nullptr, nullptr, t.shape);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s, &g);

@@ -380,12 +380,13 @@ __device__ __forceinline__ double centre_coord(int i, int level) {
 __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m,
                                             int64_t skip) {
   WalkRec w;
-  w.px = w.px2 = __double2float_rn(x);
+  w.px = __double2float_rn(x);
   w.py = __double2float_rn(y);
   w.pz = __double2float_rn(z);
-  w.m = w.m2 = __double2float_rn(m);
+  w.m = __double2float_rn(m);
   w.s2 = 0.0f;
   w.skip = (unsigned)skip;
+  w.pad[0] = w.pad[1] = 0.0f;
   return w;
 }
 
@@ -467,13 +468,13 @@ __device__ __forceinline__ void add_shifted_ff(float Q[6], const float *Qc, floa
 
 __device__ __forceinline__ void store_quad_f(int64_t id, const float Q[6], WalkQuad *qrec) {
   WalkQuad w;
-  w.hxx = w.hxx2 = 0.5f * Q[0];
+  w.hxx = 0.5f * Q[0];
   w.hyy = 0.5f * Q[1];
   w.hzz = 0.5f * Q[2];
   w.qxy = Q[3];
   w.qxz = Q[4];
   w.qyz = Q[5];
-  w.pad = 0.0f;
+  w.pad[0] = w.pad[1] = 0.0f;
   qrec[id] = w;
 }
 
@@ -487,21 +488,21 @@ __device__ __forceinline__ void load_quad_f(const WalkQuad &w, float Q[6]) {
   Q[5] = w.qyz;
 }
 
-// FP64 quadrupole (physical) and its binary32 walk record {Qxx/2 (twice),
-// Qyy/2, Qzz/2, Qxy, Qxz, Qyz, 0} in the field's mass unit (inv_unit = 2^-e):
+// FP64 quadrupole (physical) and its binary32 walk record {Qxx/2, Qyy/2,
+// Qzz/2, Qxy, Qxz, Qyz} in the field's mass unit (inv_unit = 2^-e):
 // the halves fold the 1/2 of the quadrupole term.
 __device__ __forceinline__ void store_quad(int64_t id, const double Q[6], double *q64,
                                            WalkQuad *qrec, double inv_unit) {
   for (int a = 0; a < 6; ++a) q64[6 * id + a] = Q[a];
   const double u = inv_unit;
   WalkQuad w;
-  w.hxx = w.hxx2 = __double2float_rn(0.5 * Q[0] * u);
+  w.hxx = __double2float_rn(0.5 * Q[0] * u);
   w.hyy = __double2float_rn(0.5 * Q[1] * u);
   w.hzz = __double2float_rn(0.5 * Q[2] * u);
   w.qxy = __double2float_rn(Q[3] * u);
   w.qxz = __double2float_rn(Q[4] * u);
   w.qyz = __double2float_rn(Q[5] * u);
-  w.pad = 0.0f;
+  w.pad[0] = w.pad[1] = 0.0f;
   qrec[id] = w;
 }
 
@@ -565,12 +566,13 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int64_t id = root + cell_offset(m);
     mom[id] = make_double4_32a(ux, uy, uz, mass);
     WalkRec w;  // make_rec without the conversions: the centre is a binary32 value
-    w.px = w.px2 = fx;
+    w.px = fx;
     w.py = fy;
     w.pz = fz;
-    w.m = w.m2 = mu;
+    w.m = mu;
     w.s2 = 0.0f;
     w.skip = (unsigned)(id + 1);
+    w.pad[0] = w.pad[1] = 0.0f;
     rec[id] = w;
     aux[id] = make_float2(0.0f, 0.0f);
     lvl[id] = (uint8_t)lc;

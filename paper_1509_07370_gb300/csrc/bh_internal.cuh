@@ -4,14 +4,14 @@
 // depth-first visit of the octree in octant order o = ox + 2 oy + 4 oz, so a
 // node's first child sits right after it and its subtree is contiguous):
 //   mom  double4 {Rx, Ry, Rz, M}  FP64 centre of mass (box units) and mass
-//   rec  WalkRec (32 bytes)       what the walk reads, in one 256-bit load:
-//                                 the centre of mass and mass rounded to
-//                                 binary32, the mass in its field's binary32
-//                                 mass unit (below) (Px and M stored twice so that they
-//                                 form ready-made pairs for packed f32x2
-//                                 arithmetic), the squared opening radius s2
-//                                 for the current theta (0 for cells), and the
-//                                 index of the first node after the subtree
+//   rec  WalkRec (32 bytes)       what the walk reads, 24 bytes in a 128-bit
+//                                 and a 64-bit load: the centre of mass and
+//                                 mass rounded to binary32, the mass in its
+//                                 field's binary32 mass unit (below), the
+//                                 squared opening radius s2 for the current
+//                                 theta (0 for cells), and the index of the
+//                                 first node after the subtree; 8 bytes of
+//                                 padding keep records 32-byte aligned
 //   aux  float2  {l, delta}       node side and |R - centre| in binary32
 //                                 (both 0 for cells)
 //   lvl  uint8                    node level
@@ -56,27 +56,37 @@ enum : unsigned {
   kErrTimeout = 32u,     // a bounded wait for the tensor core gave up
 };
 
+// Every warp lane needs every field of the record it walks through, so each
+// load is delivered to all 32 lanes: only the six fields the walk uses are
+// read (24 bytes; the L1 returns a warp's data 128 bytes per cycle).
 struct __align__(32) WalkRec {
-  float px, px2;   // Px twice
-  float py, pz;
-  float m, m2;     // M twice
-  float s2;        // (l/theta + delta)^2 in binary32; 0 for cells
-  unsigned skip;   // first node after this node's subtree
+  float px, py, pz;  // centre of mass, box units
+  float m;           // mass in the field's binary32 unit
+  float s2;          // (l/theta + delta)^2 in binary32; 0 for cells
+  unsigned skip;     // first node after this node's subtree
+  float pad[2];
 };
 static_assert(sizeof(WalkRec) == 32, "walk record must be 32 bytes");
 
 // Quadrupole walk record (quadrupole or learned option), box units and the
-// field's binary32 mass unit: half the diagonal of Q (Qxx/2 twice, for packed
-// pairs), and the off-diagonal terms, so that
+// field's binary32 mass unit: half the diagonal of Q and the off-diagonal
+// terms (read as 24 bytes, like WalkRec), so that
 //   d^T Q d / 2 = dx (Qxx/2 dx + Qxy dy + Qxz dz) + dy (Qyy/2 dy + Qyz dz)
 //                 + Qzz/2 dz^2.
 struct __align__(32) WalkQuad {
-  float hxx, hxx2;
-  float hyy, hzz;
-  float qxy, qxz;
-  float qyz, pad;
+  float hxx, hyy, hzz, qxy;
+  float qxz, qyz;
+  float pad[2];
 };
 static_assert(sizeof(WalkQuad) == 32, "quadrupole record must be 32 bytes");
+
+// Launch shape of the per-cell binary32 walk: warps per CTA and x-neighbour
+// target pairs per lane (a warp's group of targets: 1 pair = a 4x4x4 octant,
+// 2 pairs = a 8x4x4 slab); 0 = the default.
+struct WalkShape {
+  int warps = 0;
+  int pairs = 0;
+};
 
 struct Tree {
   // block arrays (capacity nb_cap)
@@ -108,7 +118,7 @@ struct Tree {
   void *graph_out = nullptr;
   int graph_fp64 = -1;
   double graph_theta = 0.0, graph_G = 0.0;
-  int wpc = 0;                  // tuned warps per CTA of the walk (0 = default)
+  WalkShape shape;              // tuned launch shape of the walk (0 = defaults)
   int64_t nb_cap = 0;
   // node arrays (capacity node_cap)
   double4_32a *d_mom = nullptr;
@@ -222,13 +232,13 @@ cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux
                               float inv_theta);
 // out: float* (F32) or double* (F64); counts: optional per-cell n_int/n_test.
 // Potential scale of field f: -G * invL[f] (times the field's mass unit for
-// the binary32 walk).  wpc = warps per CTA of the
-// per-cell binary32 walk (0 = default), a tunable launch shape.
+// the binary32 walk).  shape = the launch shape of the per-cell binary32
+// walk (warps per CTA, target pairs per lane; 0 = defaults), tunable.
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
                         const double4_32a *mom, const WalkQuad *qrec, const double *q64,
                         const int4 *blk, const int *orig, const FieldArgs &fa, double G,
                         void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf = nullptr,
-                        int wpc = 0);
+                        WalkShape shape = WalkShape());
 
 // ---- small device helpers ---------------------------------------------------
 // Spread the low 21 bits of v so bit b lands at bit 3b.

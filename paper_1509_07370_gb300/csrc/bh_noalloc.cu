@@ -131,6 +131,8 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   if (!(box_len > 0.0) || !std::isfinite(box_len) || !(theta > 0.0) || !(theta <= 1.0) ||
       !std::isfinite(G) || (density_is_fp64 != 0 && density_is_fp64 != 1))
     return BH_ERR_ARG;
+  for (int a = 0; a < 3; ++a)  // the box origin, as bh_build checks it
+    if (!std::isfinite(box_lo[a])) return BH_ERR_ARG;
   if ((nblocks - 1) % 7 != 0) return BH_ERR_GEOMETRY;
   Geometry g;
   int max_level = 0;
@@ -200,6 +202,6 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   bh_options opt;
   bh_default_options(&opt);
   NA_CUDA(launch_walk(s, opt, nb, d_rec, d_mom, nullptr, nullptr, d_blk, d_orig, fa, G, out,
-                      nullptr, nullptr, nullptr, 0));
+                      nullptr, nullptr, nullptr, WalkShape()));
   return BH_OK;
 }

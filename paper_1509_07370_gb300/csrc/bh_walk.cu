@@ -41,6 +41,11 @@ namespace {
 constexpr int kWalkThreads = 256;               // default CTA: 8 warps = one block
 constexpr int kWarpsPerCta = kWalkThreads / 32;
 constexpr int kMaxWalkThreads = 512;            // largest tunable CTA
+// Default launch shape of the per-cell walk (the fastest on GB300 for the
+// spheroid and cloud-core workloads at theta 0.24 - 0.72): one target pair
+// per lane (64-target octants), CTAs of 4 warps.
+constexpr int kDefaultPairs = 1;
+constexpr int kDefaultWarps = 4;
 
 __global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, WalkRec *__restrict__ rec,
                              float inv_theta) {
@@ -51,152 +56,332 @@ __global__ void k_prepare_s2(int64_t n, const float2 *__restrict__ aux, WalkRec 
   rec[i].s2 = __fmul_rn(s, s);
 }
 
-// ---- per-cell binary32 walk, two x-neighbour targets per lane ---------------
-// Interaction pair of an accepted node with the quadrupole term:
-// rinv (M + (d^T Q d / 2) rinv^4), i.e. M/d + (1/2) d^T Q d / d^5.
-__device__ __forceinline__ u64 quad_term2(const WalkQuad *qr, u64 mm, u64 rr, u64 dx2, float dy,
-                                          float dz) {
-  u64 w0, w1, w2, w3;
+// ---- per-cell binary32 walk, x-neighbour target pairs per lane -------------
+//
+// A warp walks for a group of targets that share every y and z coordinate
+// pattern: lane l owns NP pairs of x-neighbours, pair k at x offset 4k, so
+// all 2 NP targets of a lane have the same (y, z) and share dy, dz and
+// dy^2 + dz^2.  NP = 1: the group is a 4x4x4 octant of a block (64 targets);
+// NP = 2: two x-adjacent octants, a 8x4x4 slab (128 targets).  A larger group
+// walks only a few percent more nodes than a smaller one (the union of its
+// targets' walks), so every record loaded serves more targets: the record's
+// broadcast to all 32 lanes (8 registers each) is what the L1 return path
+// spends most of its time on.
+
+// Per-target state of one lane: NP packed pairs.
+template <int NP>
+struct Lanes {
+  u64 tx2[NP];              // {x_a, x_b} of pair k, box units
+  u64 sum[NP], comp[NP];    // Kahan pair sums
+  unsigned next_a[NP], next_b[NP];
+  int ni[2 * NP], nt[2 * NP], nl[2 * NP];  // counting walk
+};
+
+// dy, dz and h = fma(dz, dz, dy * dy) of the lane's targets to a record, the
+// shared part of the opening test's distance (fixed rounding: d2 = fma(dx,
+// dx, h)).
+__device__ __forceinline__ float dyz_part(float ty, float tz, u64 q1, float &dy, float &dz) {
+  float py, pz;
+  upk(q1, py, pz);
+  dy = __fsub_rn(ty, py);
+  dz = __fsub_rn(tz, pz);
+  return __fmaf_rn(dz, dz, __fmul_rn(dy, dy));
+}
+
+// The terms of an accepted node for one pair: M/d, or with the quadrupole
+// record w rinv (M + (d^T Q d / 2) rinv^4); qu = Qxy dy + Qxz dz and qc =
+// dy (Qyy/2 dy + Qyz dz) + Qzz/2 dz^2 are shared by all pairs of the lane.
+template <bool QUAD>
+__device__ __forceinline__ u64 node_term2(u64 mm, u64 rr, u64 dx2, u64 w0, float qu, float qc) {
+  if (!QUAD) return mul2(mm, rr);
+  const u64 hq = fma2(dx2, fma2(w0, dx2, pk(qu, qu)), pk(qc, qc));
+  const u64 r2 = mul2(rr, rr);
+  return mul2(rr, fma2(hq, mul2(r2, r2), mm));
+}
+
+// Loads the quadrupole record of node and forms its shared parts.
+__device__ __forceinline__ void quad_shared(const WalkQuad *qr, float dy, float dz, u64 &w0,
+                                            float &qu, float &qc) {
+  u64 w1, w2, w3;
   load_quad(qr, w0, w1, w2, w3);
   float hyy, hzz, qxy, qxz, qyz, unused;
   upk(w1, hyy, hzz);
   upk(w2, qxy, qxz);
   upk(w3, qyz, unused);
-  const float u = __fmaf_rn(qxz, dz, __fmul_rn(qxy, dy));    // shared by the pair
+  qu = __fmaf_rn(qxz, dz, __fmul_rn(qxy, dy));
   const float v = __fmaf_rn(hyy, dy, __fmul_rn(qyz, dz));
-  const float c = __fmaf_rn(dy, v, __fmul_rn(__fmul_rn(hzz, dz), dz));
-  const u64 hq = fma2(dx2, fma2(w0, dx2, pk(u, u)), pk(c, c));
-  const u64 r2 = mul2(rr, rr);
-  return mul2(rr, fma2(hq, mul2(r2, r2), mm));
+  qc = __fmaf_rn(dy, v, __fmul_rn(__fmul_rn(hzz, dz), dz));
 }
 
-// Walk of one 64-cell octant (unit u = 8 * sorted block + octant).
+// The 8 cells of a bottom node (node + 1 .. node + 8) for the targets that
+// opened it (bit 2k of `open` for target a of pair k, bit 2k + 1 for target
+// b): every cell but the target's own (d2 > 0).
+// Cells 2j and 2j + 1 are x-neighbours with the same y and z, so they share
+// dy, dz and h too.  The 8 positive cell terms are summed plainly (a
+// relative error of at most 7 units in the last place of their sum) and the
+// sum joins the compensated total once.
+template <int NP, bool KAHAN, bool COUNTS>
+__device__ __forceinline__ void bottom_cells(unsigned node, unsigned open,
+                                             const WalkRec *__restrict__ rec, float ty,
+                                             float tz, Lanes<NP> &L) {
+  u64 part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) part[k] = 0ull;
+#pragma unroll 1
+  for (unsigned c = node + 1; c < node + 9u; c += 2) {
+    u64 c0, c1, c2, c3, e0, e1, e2, e3;
+    load_rec(rec + c, c0, c1, c2, c3);
+    load_rec(rec + c + 1, e0, e1, e2, e3);
+    float dy, dz;
+    const float h = dyz_part(ty, tz, c1, dy, dz);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const u64 px = j ? e0 : c0, mm = j ? e2 : c2;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const u64 dx2 = sub2(L.tx2[k], px);
+        float e2a, e2b;
+        upk(fma2(dx2, dx2, pk(h, h)), e2a, e2b);
+        const bool la = ((open >> (2 * k)) & 1u) && e2a > 0.0f;
+        const bool lb = ((open >> (2 * k + 1)) & 1u) && e2b > 0.0f;
+        if (COUNTS) {
+          L.ni[2 * k] += la;
+          L.ni[2 * k + 1] += lb;
+          L.nl[2 * k] += la;
+          L.nl[2 * k + 1] += lb;
+        } else {
+          float ra = rsqrt_approx(e2a), rb = rsqrt_approx(e2b);
+          ra = la ? ra : 0.0f;
+          rb = lb ? rb : 0.0f;
+          part[k] = fma2(mm, pk(ra, rb), part[k]);
+        }
+      }
+    }
+  }
+  if (!COUNTS) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) accumulate2<KAHAN>(L.sum[k], L.comp[k], part[k]);
+  }
+}
+
+// Walk of one target group (unit u = (8 / NP) * sorted block + group; group
+// g covers octants NP g .. NP g + NP - 1).
+//
+// Two modes.  While every target of the warp is at the same node (all `next`
+// equal: "converged", as at the root), a step needs no per-target
+// bookkeeping: each target still applies its own test, and one vote tells
+// whether all accepted (add the terms, continue at skip), all opened
+// (continue at node + 1) or they differ.  Where they differ, the targets
+// part, and the subtree of that node is walked per target ("diverged").
+// There a target takes part in the step at `node` when its `next` <= node
+// (`next` is kept lazily: it only moves ahead of the warp when the target
+// accepts a node that another target opens); the warp goes on at node + 1
+// when some taking-part target opened the node, else at its skip index --
+// which is the smallest next of all targets, as the recursive walk requires.
+// Every target leaves a subtree at its skip index, so they all meet again at
+// the end of the parted subtree, and the warp is converged once more.  Both
+// modes take exactly the per-target decisions of the recursive definition;
+// they differ only in the bookkeeping.
 //
 // Bottom nodes (whose 8 children are cells, stored right after them, so
 // skip = node + 9) are taken in one step: the targets that open such a node
 // interact with its 8 cells in an unrolled loop that needs no per-cell
 // bookkeeping (cells are never opened), and every target then continues at
-// node + 9.  Targets that do not open it have next >= node + 9 already: a
-// target whose walk does not contain a node has accepted one of its
-// ancestors and skipped past the ancestor's whole subtree.
-template <bool KAHAN, bool COUNTS, bool QUAD>
-__device__ __forceinline__ void walk_octant(unsigned u, int lane, const WalkRec *__restrict__ rec,
-                                            const WalkQuad *__restrict__ qrec,
-                                            const int4 *__restrict__ blk,
-                                            const int *__restrict__ orig,
-                                            const int4 *__restrict__ fld,
-                                            const double *__restrict__ invL,
-                                            const unsigned long long *__restrict__ mmax, double G,
-                                            float *__restrict__ out, int32_t *__restrict__ n_int,
-                                            int32_t *__restrict__ n_test,
-                                            int32_t *__restrict__ n_leaf) {
-  const unsigned p = u >> 3;                          // sorted block
+// node + 9.  Cells are only reached through their bottom node, so the walk
+// never stops at a cell.
+template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
+__device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *__restrict__ rec,
+                                           const WalkQuad *__restrict__ qrec,
+                                           const int4 *__restrict__ blk,
+                                           const int *__restrict__ orig,
+                                           const int4 *__restrict__ fld,
+                                           const double *__restrict__ invL,
+                                           const unsigned long long *__restrict__ mmax, double G,
+                                           float *__restrict__ out, int32_t *__restrict__ n_int,
+                                           int32_t *__restrict__ n_test,
+                                           int32_t *__restrict__ n_leaf) {
+  constexpr unsigned kGroups = 8 / NP;                // groups per block
+  const unsigned p = u / kGroups;                     // sorted block
   const int4 F = fld[p];                              // this field's node range
   const unsigned n_nodes = (unsigned)F.y;
-  const int ma = (int)((u & 7) << 6) | (lane << 1);   // local Morton index, even: x bit 0
+  const int o = (int)(u % kGroups) * NP;              // octant of pair 0
+  const int ma = (o << 6) | (lane << 1);              // local Morton index, even: x bit 0
   const int4 B = blk[p];
   const int cx = (int)compact3(ma), cy = (int)compact3(ma >> 1), cz = (int)compact3(ma >> 2);
   const int lc = B.x + 3;
   // cell centres in box units, exact in binary32: (2 i + 1) * 2^-(lc+1)
   const float hh = pow2f(-(lc + 1));
-  const float txa = __fmul_rn((float)(2 * (8 * B.y + cx) + 1), hh);
-  const float txb = __fmul_rn((float)(2 * (8 * B.y + cx) + 3), hh);
   const float ty = __fmul_rn((float)(2 * (8 * B.z + cy) + 1), hh);
   const float tz = __fmul_rn((float)(2 * (8 * B.w + cz) + 1), hh);
-  const u64 tx2 = pk(txa, txb);
+  Lanes<NP> L;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int ix = 8 * B.y + cx + 4 * k;
+    L.tx2[k] = pk(__fmul_rn((float)(2 * ix + 1), hh), __fmul_rn((float)(2 * ix + 3), hh));
+    L.sum[k] = 0ull;  // (+0.0f, +0.0f)
+    L.comp[k] = 0ull;
+    L.ni[2 * k] = L.ni[2 * k + 1] = L.nt[2 * k] = L.nt[2 * k + 1] = 0;
+    L.nl[2 * k] = L.nl[2 * k + 1] = 0;
+  }
 
-  u64 sum = 0ull, comp = 0ull;  // (+0.0f, +0.0f) pairs
-  int nia = 0, nib = 0, nta = 0, ntb = 0, nla = 0, nlb = 0;
-  unsigned next_a = (unsigned)F.x, next_b = (unsigned)F.x;  // the field's root
-  unsigned node = (unsigned)F.x;
+  unsigned node = (unsigned)F.x;  // the field's root
   while (node < n_nodes) {
+    // ---- converged: every target is at `node`, an internal node ----
     u64 q0, q1, q2, q3;
     load_rec(rec + node, q0, q1, q2, q3);
     float s2, skf;
     upk(q3, s2, skf);
     const unsigned skip = __float_as_uint(skf);
-    float d2a, d2b, dy, dz;
-    u64 dx2;
-    dist2(tx2, ty, tz, q0, q1, d2a, d2b, dx2, dy, dz);
-    const bool mine_a = next_a == node, mine_b = next_b == node;
-    const bool take_a = mine_a && d2a > s2;
-    const bool take_b = mine_b && d2b > s2;
-    if (COUNTS) {
-      const bool internal = s2 > 0.0f;
-      nia += take_a;
-      nib += take_b;
-      nta += mine_a && internal;
-      ntb += mine_b && internal;
-      nla += take_a && !internal;
-      nlb += take_b && !internal;
-    } else {
-      float ra = rsqrt_approx(d2a), rb = rsqrt_approx(d2b);
-      ra = take_a ? ra : 0.0f;
-      rb = take_b ? rb : 0.0f;
-      const u64 rr = pk(ra, rb);
-      accumulate2<KAHAN>(sum, comp,
-                         QUAD ? quad_term2(qrec + node, q2, rr, dx2, dy, dz) : mul2(q2, rr));
+    float dy, dz;
+    const float h = dyz_part(ty, tz, q1, dy, dz);
+    u64 dx2[NP];
+    float d2a[NP], d2b[NP];
+    bool ta[NP], tb[NP];
+    bool all = true, any = false;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      dx2[k] = sub2(L.tx2[k], q0);
+      upk(fma2(dx2[k], dx2[k], pk(h, h)), d2a[k], d2b[k]);
+      ta[k] = d2a[k] > s2;
+      tb[k] = d2b[k] > s2;
+      all = all && ta[k] && tb[k];
+      any = any || ta[k] || tb[k];
+      if (COUNTS) {
+        ++L.nt[2 * k];
+        ++L.nt[2 * k + 1];
+        L.ni[2 * k] += ta[k];
+        L.ni[2 * k + 1] += tb[k];
+      }
     }
-    if (skip == node + 9u) {  // bottom node
-      const bool open_a = mine_a && !take_a, open_b = mine_b && !take_b;
-      if (__any_sync(kFull, open_a || open_b)) {
-#pragma unroll 2
-        for (unsigned c = node + 1; c < node + 9u; ++c) {
-          u64 c0, c1, c2, c3;
-          load_rec(rec + c, c0, c1, c2, c3);
-          float e2a, e2b, ey, ez;
-          u64 ex2;
-          dist2(tx2, ty, tz, c0, c1, e2a, e2b, ex2, ey, ez);
-          const bool la = open_a && e2a > 0.0f;  // every cell but the target's own
-          const bool lb = open_b && e2b > 0.0f;
-          if (COUNTS) {
-            nia += la;
-            nib += lb;
-            nla += la;
-            nlb += lb;
-          } else {
-            float ra = rsqrt_approx(e2a), rb = rsqrt_approx(e2b);
-            ra = la ? ra : 0.0f;
-            rb = lb ? rb : 0.0f;
-            accumulate2<KAHAN>(sum, comp, mul2(c2, pk(ra, rb)));
-          }
+    u64 w0 = 0ull;
+    float qu = 0.0f, qc = 0.0f;
+    if (__all_sync(kFull, all)) {  // every target accepts the node
+      if (!COUNTS) {
+        if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          const u64 rr = pk(rsqrt_approx(d2a[k]), rsqrt_approx(d2b[k]));
+          accumulate2<KAHAN>(L.sum[k], L.comp[k], node_term2<QUAD>(q2, rr, dx2[k], w0, qu, qc));
         }
       }
-      next_a = max(next_a, skip);
-      next_b = max(next_b, skip);
-    } else {
-      const unsigned n1 = node + 1;
-      next_a = max(next_a, take_a ? skip : n1);
-      next_b = max(next_b, take_b ? skip : n1);
+      node = skip;
+      continue;
     }
-    node = __reduce_min_sync(kFull, min(next_a, next_b));
+    const bool any_take = __any_sync(kFull, any);
+    if (!COUNTS && any_take) {
+      if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        float ra = rsqrt_approx(d2a[k]), rb = rsqrt_approx(d2b[k]);
+        ra = ta[k] ? ra : 0.0f;
+        rb = tb[k] ? rb : 0.0f;
+        accumulate2<KAHAN>(L.sum[k], L.comp[k],
+                           node_term2<QUAD>(q2, pk(ra, rb), dx2[k], w0, qu, qc));
+      }
+    }
+    if (skip == node + 9u) {  // bottom node: the openers meet its cells; all go on at skip
+      unsigned open = 0u;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) open |= (ta[k] ? 0u : 1u << (2 * k)) | (tb[k] ? 0u : 2u << (2 * k));
+      bottom_cells<NP, KAHAN, COUNTS>(node, open, rec, ty, tz, L);
+      node = skip;
+      continue;
+    }
+    if (!any_take) {  // every target opens the node
+      node = node + 1;
+      continue;
+    }
+    // ---- diverged: the targets part inside the subtree [node + 1, end) ----
+    const unsigned end = skip;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      L.next_a[k] = ta[k] ? skip : node + 1;
+      L.next_b[k] = tb[k] ? skip : node + 1;
+    }
+    node = node + 1;  // some target opened the node
+    while (node < end) {
+      load_rec(rec + node, q0, q1, q2, q3);
+      upk(q3, s2, skf);
+      const unsigned skp = __float_as_uint(skf);
+      const float hd = dyz_part(ty, tz, q1, dy, dz);
+      bool ma_[NP], mb_[NP];
+      unsigned open = 0u;
+      bool any_tk = false;
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        dx2[k] = sub2(L.tx2[k], q0);
+        upk(fma2(dx2[k], dx2[k], pk(hd, hd)), d2a[k], d2b[k]);
+        ma_[k] = L.next_a[k] <= node;
+        mb_[k] = L.next_b[k] <= node;
+        ta[k] = ma_[k] && d2a[k] > s2;
+        tb[k] = mb_[k] && d2b[k] > s2;
+        open |= (ma_[k] && !ta[k] ? 1u << (2 * k) : 0u) | (mb_[k] && !tb[k] ? 2u << (2 * k) : 0u);
+        any_tk = any_tk || ta[k] || tb[k];
+        if (COUNTS) {  // internal: cells are only reached through bottom nodes
+          L.ni[2 * k] += ta[k];
+          L.ni[2 * k + 1] += tb[k];
+          L.nt[2 * k] += ma_[k];
+          L.nt[2 * k + 1] += mb_[k];
+        }
+      }
+      if (!COUNTS && __any_sync(kFull, any_tk)) {
+        if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          float ra = rsqrt_approx(d2a[k]), rb = rsqrt_approx(d2b[k]);
+          ra = ta[k] ? ra : 0.0f;
+          rb = tb[k] ? rb : 0.0f;
+          accumulate2<KAHAN>(L.sum[k], L.comp[k],
+                             node_term2<QUAD>(q2, pk(ra, rb), dx2[k], w0, qu, qc));
+        }
+      }
+      const bool opened = __any_sync(kFull, open != 0u);
+      if (skp == node + 9u) {  // bottom node: all go on at skip
+        if (opened) bottom_cells<NP, KAHAN, COUNTS>(node, open, rec, ty, tz, L);
+        node = skp;
+      } else if (opened) {  // takers of a node others open move ahead of the warp
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          L.next_a[k] = ta[k] ? skp : L.next_a[k];
+          L.next_b[k] = tb[k] ? skp : L.next_b[k];
+        }
+        node = node + 1;
+      } else {
+        node = skp;
+      }
+    }
+    node = end;  // every target leaves the subtree at its skip index
   }
-  const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx;
-  if (COUNTS) {
-    n_int[cell] = nia;
-    n_int[cell + 1] = nib;
-    n_test[cell] = nta;
-    n_test[cell + 1] = ntb;
-    if (n_leaf) {
-      n_leaf[cell] = nla;
-      n_leaf[cell + 1] = nlb;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx + 4 * k;
+    if (COUNTS) {
+      n_int[cell] = L.ni[2 * k];
+      n_int[cell + 1] = L.ni[2 * k + 1];
+      n_test[cell] = L.nt[2 * k];
+      n_test[cell + 1] = L.nt[2 * k + 1];
+      if (n_leaf) {
+        n_leaf[cell] = L.nl[2 * k];
+        n_leaf[cell + 1] = L.nl[2 * k + 1];
+      }
+    } else {
+      u64 sm = L.sum[k];
+      sm = finish2<KAHAN>(sm, L.comp[k]);
+      float sa, sb;
+      upk(sm, sa, sb);
+      // -G/L times the field's binary32 mass unit 2^e (exact), rounded once
+      const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));
+      out[cell] = __fmul_rn(sa, scale);
+      out[cell + 1] = __fmul_rn(sb, scale);
     }
-  } else {
-    if (KAHAN) sum = sub2(sum, comp);
-    float sa, sb;
-    upk(sum, sa, sb);
-    // -G/L times the field's binary32 mass unit 2^e (exact), rounded once
-    const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));
-    out[cell] = __fmul_rn(sa, scale);
-    out[cell + 1] = __fmul_rn(sb, scale);
   }
 }
 
-// One warp per 64-cell octant; a CTA of 8 warps covers one block.  (A
+// One warp per target group (8 / NP groups per block).  (A
 // persistent SM-affine schedule with work stealing raised the L1 hit rate
 // from 44 % to 57 % but ran 8 % slower on GB300, so the hardware schedule of a
 // plain grid is kept.)
-template <bool KAHAN, bool COUNTS, bool QUAD>
+template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kMaxWalkThreads)
     k_walk_pair(unsigned nunits, const WalkRec *__restrict__ rec,
                 const WalkQuad *__restrict__ qrec, const int4 *__restrict__ blk,
@@ -207,8 +392,8 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
   const int lane = threadIdx.x & 31;
   const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_octant<KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
-                                   n_int, n_test, n_leaf);
+  walk_group<NP, KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
+                                      n_int, n_test, n_leaf);
 }
 
 // ---- one target per lane: binary64 interactions and/or the warp vote --------
@@ -299,10 +484,9 @@ __global__ void __launch_bounds__(kWalkThreads)
         const float r2 = r * r;
         term = r * (mf + hq * r2 * r2);
       }
-      if (KAHAN) {
-        const float y = __fsub_rn(term, comp);
-        const float t = __fadd_rn(sum, y);
-        comp = __fsub_rn(__fsub_rn(t, sum), y);
+      if (KAHAN) {  // compensated as accumulate2 (bh_walk_common.cuh)
+        const float t = __fadd_rn(sum, term);
+        comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(sum, t), term));
         sum = t;
       } else {
         sum = __fadd_rn(sum, term);
@@ -318,21 +502,33 @@ __global__ void __launch_bounds__(kWalkThreads)
   } else if (F64) {
     reinterpret_cast<double *>(out)[cell] = sumd * scale_d;
   } else {
-    const float total = KAHAN ? __fsub_rn(sum, comp) : sum;
+    const float total = KAHAN ? __fadd_rn(sum, comp) : sum;
     reinterpret_cast<float *>(out)[cell] = __fmul_rn(total, scale_f);
   }
+}
+
+template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
+cudaError_t go_pair_np(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *qrec,
+                       const int4 *blk, const int *orig, const FieldArgs &fa, double G, void *out,
+                       int32_t *ni, int32_t *nt, int32_t *nl, int warps) {
+  const unsigned nunits = (unsigned)nb * (8u / NP);
+  const int w = warps > 0 ? warps : kDefaultWarps;
+  const int grid = (int)((nunits + w - 1) / w);
+  k_walk_pair<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
+      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
+  return cudaGetLastError();
 }
 
 template <bool KAHAN, bool COUNTS, bool QUAD>
 cudaError_t go_pair(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *qrec,
                     const int4 *blk, const int *orig, const FieldArgs &fa, double G, void *out,
-                    int32_t *ni, int32_t *nt, int32_t *nl, int wpc) {
-  const unsigned nunits = (unsigned)nb * 8u;
-  const int w = wpc > 0 ? wpc : kWarpsPerCta;
-  const int grid = (int)((nunits + w - 1) / w);
-  k_walk_pair<KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
-      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
-  return cudaGetLastError();
+                    int32_t *ni, int32_t *nt, int32_t *nl, WalkShape shape) {
+  const int np = shape.pairs > 0 ? shape.pairs : kDefaultPairs;
+  if (np == 2)
+    return go_pair_np<2, KAHAN, COUNTS, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, ni, nt, nl,
+                                              shape.warps);
+  return go_pair_np<1, KAHAN, COUNTS, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, ni, nt, nl,
+                                            shape.warps);
 }
 
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
@@ -354,7 +550,7 @@ template <bool QUAD>
 cudaError_t launch_walk_q(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
                           const double4_32a *mom, const WalkQuad *qrec, const double *q64,
                           const int4 *blk, const int *orig, const FieldArgs &fa, double G,
-                          void *out, int wpc) {
+                          void *out, WalkShape shape) {
   const bool vote = opt.criterion == BH_CRIT_WARP_VOTE;
   if (opt.precision == BH_PREC_F64)
     return vote ? go_scalar<true, true, false, false, QUAD>(s, nb, rec, mom, qrec, q64, blk, orig,
@@ -370,9 +566,9 @@ cudaError_t launch_walk_q(cudaStream_t s, const bh_options &opt, int nb, const W
                                                                   blk, orig, fa, G, out, nullptr,
                                                                   nullptr, nullptr);
   return opt.kahan ? go_pair<true, false, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, nullptr,
-                                                nullptr, nullptr, wpc)
+                                                nullptr, nullptr, shape)
                    : go_pair<false, false, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out,
-                                                 nullptr, nullptr, nullptr, wpc);
+                                                 nullptr, nullptr, nullptr, shape);
 }
 
 }  // namespace
@@ -388,16 +584,17 @@ cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux
 cudaError_t launch_walk(cudaStream_t s, const bh_options &opt, int nb, const WalkRec *rec,
                         const double4_32a *mom, const WalkQuad *qrec, const double *q64,
                         const int4 *blk, const int *orig, const FieldArgs &fa, double G,
-                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf, int wpc) {
+                        void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
+                        WalkShape shape) {
   if (n_int)  // counting walk
     return opt.criterion == BH_CRIT_WARP_VOTE
                ? go_scalar<false, true, false, true, false>(s, nb, rec, mom, qrec, q64, blk, orig,
                                                            fa, G, out, n_int, n_test, n_leaf)
                : go_pair<false, true, false>(s, nb, rec, qrec, blk, orig, fa, G, out, n_int,
-                                             n_test, n_leaf, wpc);
+                                             n_test, n_leaf, shape);
   if (opt.quadrupole)
-    return launch_walk_q<true>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
-  return launch_walk_q<false>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, wpc);
+    return launch_walk_q<true>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, shape);
+  return launch_walk_q<false>(s, opt, nb, rec, mom, qrec, q64, blk, orig, fa, G, out, shape);
 }
 
 }  // namespace bhg

@@ -49,34 +49,56 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// One 32-byte walk record as four 64-bit lanes:
+// The six fields of a walk record (24 bytes: a 128-bit and a 64-bit load)
+// as four 64-bit pairs for the packed arithmetic:
 //   q0 = {Px, Px}, q1 = {Py, Pz}, q2 = {M, M}, q3 = {s2, skip}
 __device__ __forceinline__ void load_rec(const WalkRec *p, u64 &q0, u64 &q1, u64 &q2, u64 &q3) {
-  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-      : "=l"(q0), "=l"(q1), "=l"(q2), "=l"(q3)
+  float px, py, pz, m, s2, skf;
+  asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(px), "=f"(py), "=f"(pz), "=f"(m)
       : "l"(p));
+  asm("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(s2), "=f"(skf) : "l"(&p->s2));
+  q0 = pk(px, px);
+  q1 = pk(py, pz);
+  q2 = pk(m, m);
+  q3 = pk(s2, skf);
 }
 
-// One 32-byte quadrupole record: w0 = {Qxx/2, Qxx/2}, w1 = {Qyy/2, Qzz/2},
-// w2 = {Qxy, Qxz}, w3 = {Qyz, 0}.
+// The six fields of a quadrupole record (24 bytes) as w0 = {Qxx/2, Qxx/2},
+// w1 = {Qyy/2, Qzz/2}, w2 = {Qxy, Qxz}, w3 = {Qyz, 0}.
 __device__ __forceinline__ void load_quad(const WalkQuad *p, u64 &w0, u64 &w1, u64 &w2, u64 &w3) {
-  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-      : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+  float hxx, hyy, hzz, qxy, qxz, qyz;
+  asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(hxx), "=f"(hyy), "=f"(hzz), "=f"(qxy)
       : "l"(p));
+  asm("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(qxz), "=f"(qyz) : "l"(&p->qxz));
+  w0 = pk(hxx, hxx);
+  w1 = pk(hyy, hzz);
+  w2 = pk(qxy, qxz);
+  w3 = pk(qyz, 0.0f);
 }
 
 // ---- pair walk arithmetic ---------------------------------------------------
-// Adds the pair `term` to the running (Kahan-compensated) pair sums.
+// Compensated summation of the pair `term` into the running pair sums: the
+// rounding error of each addition, err = (sum - t) + term with t = sum + term
+// (exact while |sum| >= |term|, Fast2Sum), is accumulated apart in `comp`,
+// and the result is sum + comp (finish2).  Every term of the walk is
+// positive, so the sum grows past each term after the first few.  A zero
+// term (a masked target) leaves both exactly unchanged, so the result does
+// not depend on which other targets share the warp.
 template <bool KAHAN>
 __device__ __forceinline__ void accumulate2(u64 &sum, u64 &comp, u64 term) {
   if (KAHAN) {
-    const u64 y = sub2(term, comp);
-    const u64 t = add2(sum, y);
-    comp = sub2(sub2(t, sum), y);
+    const u64 t = add2(sum, term);
+    comp = add2(comp, add2(sub2(sum, t), term));
     sum = t;
   } else {
     sum = add2(sum, term);
   }
+}
+template <bool KAHAN>
+__device__ __forceinline__ u64 finish2(u64 sum, u64 comp) {
+  return KAHAN ? add2(sum, comp) : sum;
 }
 
 // Squared distances of the two targets (tx2 = {txa, txb}, ty, tz) to the

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kLWarps * 32, 3)
   __syncwarp();
   accumulate2<KAHAN>(sum, comp, pk(Q.corr[2 * lane], Q.corr[2 * lane + 1]));
   const int64_t cell = (int64_t)orig[p] * kCellsPerBlock + cz * 64 + cy * 8 + cx;
-  if (KAHAN) sum = sub2(sum, comp);
+  sum = finish2<KAHAN>(sum, comp);
   float sa, sb;
   upk(sum, sa, sb);
   const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));

@@ -183,7 +183,7 @@ __device__ __forceinline__ void walk_octant_periodic(
       n_leaf[cell + 1] = nlb;
     }
   } else {
-    if (KAHAN) sum = sub2(sum, comp);
+    sum = finish2<KAHAN>(sum, comp);
     float sa, sb;
     upk(sum, sa, sb);
     const float scale = (float)(-G * invL[F.w] * pow2i(mass_exponent(mmax[F.w])));

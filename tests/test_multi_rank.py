@@ -77,5 +77,6 @@ def test_committed_walk_profiles_match_the_sources():
     assert bench.captured_traffic(w, 0.72, "quadrupole") is not None
     assert bench.captured_traffic(w, 0.7, "periodic64") is not None
     assert bench.captured_traffic(w, 0.7, "quadrupole") is None
+    assert bench.captured_traffic(w, 0.24, "monopole") is not None
     assert bench.captured_traffic(w, 0.72, "monopole") is None
     assert bench.captured_traffic("cloud_core", 0.72, "quadrupole") is None

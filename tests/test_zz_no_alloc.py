@@ -5,9 +5,13 @@ reserved by their own allocator, or they must keep the library out of
 cudaMalloc/cudaFree, which may synchronise the device): the tree of a mesh of
 up to 64 blocks lives in a fixed device array inside the library.  Here it is
 called through the C-ABI and compared with the regular entry points
-(bh_build + bh_potential) within the binary32 parity tolerance of the other
-tests, on two calls in a row (with a differently sized mesh in between, so
-the second call runs over a scratch array the previous calls left filled).
+(bh_build + bh_potential) on two calls in a row (with a differently sized mesh
+in between, so the second call runs over a scratch array the previous calls
+left filled).  Both paths launch the same kernels with the same arguments on
+the same inputs, only with the tree in a different place, so their
+potentials must agree bit for bit; the first round of calls is also checked
+against the CPU oracle's walk within the binary32 parity tolerance of the
+other tests.
 
 This file is named so that pytest collects it last.
 """
@@ -18,6 +22,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import oracle as O  # noqa: E402
 from paper_1509_07370_gb300 import bhgrav as B  # noqa: E402
 from paper_1509_07370_gb300 import meshgen as mg  # noqa: E402
 
@@ -65,7 +70,13 @@ def test_noalloc_matches_regular_entry_points_on_consecutive_calls():
             torch.cuda.synchronize()
             got = out.cpu().numpy()
             assert np.all(np.isfinite(got))
-            assert np.max(np.abs(got / want - 1.0)) <= F32_TOL, (k, mesh.nblocks, theta)
+            # same kernels, same arguments: identical bits
+            assert np.array_equal(got, want), (k, mesh.nblocks, theta)
+            if k == 0:                                       # and the oracle's walk
+                rho64 = rho.cpu().numpy().astype(np.float64)
+                ref = O.Tree(mesh.level, mesh.ijk, rho64, mesh.box_lo,
+                             mesh.box_len).walk(theta, G=2.0)[0]
+                assert np.max(np.abs(got / ref - 1.0)) <= F32_TOL, (mesh.nblocks, theta)
 
 
 def test_noalloc_rejects_what_does_not_fit_or_is_invalid():
@@ -84,6 +95,9 @@ def test_noalloc_rejects_what_does_not_fit_or_is_invalid():
     bad = rho.clone()
     bad[7] = -1.0
     assert _noalloc(m, bad, 0.5, 1.0, out) == B.BH_ERR_ARG
+    for lo in ((float("nan"), 0.0, 0.0), (0.0, float("inf"), 0.0)):
+        shifted = mg.Mesh(m.level, m.ijk, box_lo=np.array(lo), box_len=m.box_len)
+        assert _noalloc(shifted, rho, 0.5, 1.0, out) == B.BH_ERR_ARG
     assert _noalloc(m, rho, 0.5, 1.0, out) == B.BH_OK        # still usable afterwards
     torch.cuda.synchronize()
     assert np.all(np.isfinite(out.cpu().numpy()))
