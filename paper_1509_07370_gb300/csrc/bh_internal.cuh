@@ -310,9 +310,10 @@ __host__ __device__ constexpr int tc_canon(int r, int k, int K) {
   return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 // n rows of features x[n][10] -> y[n] on the tensor cores; flags[0] |= 1 if a
-// bounded wait gave up.
+// bounded wait gave up.  probe_limit > 0 (tests of the time-out path only):
+// no MMA is issued and the first wait gives up after probe_limit tries.
 cudaError_t launch_mlp_tc(cudaStream_t s, int64_t n, const float *x, const MlpTc *w, float *y,
-                          unsigned *flags);
+                          unsigned *flags, int probe_limit = 0);
 cudaError_t prepare_mlp_tc_kernel();
 // The learned walk with the network on tcgen05 (bh_walk_learned_tc.cu).
 cudaError_t prepare_learned_tc_kernel();

@@ -20,6 +20,7 @@
 // and bh_set_mlp, which rounds trained weights to bf16 for the tensor-core
 // evaluation inside the walk (bh_walk.cu).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -416,9 +417,17 @@ bh_status bh_mlp_eval(bh_ctx *ctx, int64_t n, const float *x, float *y) {
   if (n < 0 || (n > 0 && (!x || !y))) return ctx_fail(ctx, BH_ERR_ARG, "bh_mlp_eval: bad arguments");
   if (n == 0) return BH_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx_fail(ctx, BH_ERR_CUDA, "device");
+  // Test of the time-out path (host-side switch, no device fault): with
+  // BHGRAV_TC_WAIT_PROBE=k (k > 0) the kernel issues no MMA and gives up its
+  // first wait for the tensor core after k tries.
+  int probe = 0;
+  if (const char *env = std::getenv("BHGRAV_TC_WAIT_PROBE")) {
+    const long v = std::strtol(env, nullptr, 10);
+    probe = v > 0 ? (int)(v < (1L << 20) ? v : (1L << 20)) : 0;
+  }
   unsigned flag = 0;
   if (cudaMemsetAsync(ctx->d_tc_flag, 0, sizeof(unsigned), ctx->stream) != cudaSuccess ||
-      launch_mlp_tc(ctx->stream, n, x, ctx->d_mlp_tc, y, ctx->d_tc_flag) != cudaSuccess ||
+      launch_mlp_tc(ctx->stream, n, x, ctx->d_mlp_tc, y, ctx->d_tc_flag, probe) != cudaSuccess ||
       cudaMemcpyAsync(&flag, ctx->d_tc_flag, sizeof(unsigned), cudaMemcpyDeviceToHost,
                       ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {

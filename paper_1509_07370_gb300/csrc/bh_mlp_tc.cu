@@ -17,7 +17,12 @@
 // b1 enters through a constant input 10, as in the walk.
 //
 // Waits on the mbarrier are bounded: on time-out the kernel raises a flag,
-// stops, and the call returns BH_ERR_DEVICE_TIMEOUT.
+// stops, and the call returns BH_ERR_DEVICE_TIMEOUT.  probe_limit > 0 is the
+// test of that path: the MMA-issuing thread issues and commits nothing, so
+// the first wait (limited to probe_limit tries) runs out on a barrier no one
+// arrives at, with no tensor-core work in flight; the kernel then takes the
+// same failure path as a real time-out (flag, drain wait, tensor-memory
+// release).
 #include "bh_tc.cuh"
 
 namespace bhg {
@@ -38,7 +43,7 @@ struct __align__(1024) TcSmem {
 
 __global__ void __launch_bounds__(kTcThreads)
     k_mlp_tc(int64_t n, const float *__restrict__ x, const MlpTc *__restrict__ wts,
-             float *__restrict__ y, unsigned *flags) {
+             float *__restrict__ y, unsigned *flags, int probe_limit) {
   extern __shared__ unsigned char smem_raw[];
   TcSmem &S = *reinterpret_cast<TcSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -86,11 +91,11 @@ __global__ void __launch_bounds__(kTcThreads)
     fence_before();
     __syncthreads();
     fence_after();
-    if (t == 0) {  // layer 1
+    if (t == 0 && probe_limit == 0) {  // layer 1
       mma(tmem, sdesc(S.a1, 128, 256), sdesc(S.w.b1, 128, 256), idesc(128, 64), 0u);
       commit(&S.mbar);
     }
-    ok = __syncthreads_and(mbar_wait(&S.mbar, phase));
+    ok = __syncthreads_and(mbar_wait(&S.mbar, phase, probe_limit ? probe_limit : kTcSpinLimit));
     if (!ok) break;
     phase ^= 1u;
     fence_after();
@@ -150,12 +155,12 @@ constexpr int kTcSmem = (int)sizeof(TcSmem) + 1024 > 56 * 1024 ? (int)sizeof(TcS
                                                                  : 56 * 1024;
 
 cudaError_t launch_mlp_tc(cudaStream_t s, int64_t n, const float *x, const MlpTc *w, float *y,
-                          unsigned *flags) {
+                          unsigned *flags, int probe_limit) {
   const int smem = kTcSmem;
   const int64_t ntiles = (n + kTcRows - 1) / kTcRows;
   const int grid = (int)(ntiles < 4 * 152 ? ntiles : 4 * 152);
   if (grid <= 0) return cudaSuccess;
-  k_mlp_tc<<<grid, kTcThreads, smem, s>>>(n, x, w, y, flags);
+  k_mlp_tc<<<grid, kTcThreads, smem, s>>>(n, x, w, y, flags, probe_limit);
   return cudaGetLastError();
 }
 

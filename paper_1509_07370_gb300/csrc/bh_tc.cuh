@@ -8,7 +8,11 @@
 namespace bhg {
 namespace {
 
-constexpr int kTcSpinLimit = 1 << 20;  // bounded waits on the MMA barrier
+// Bounded waits on the MMA barrier: at most kTcSpinLimit tries, each of which
+// suspends the thread for at most kTcSuspendNs (it resumes as soon as the
+// phase completes), so a wait that runs out takes about a second.
+constexpr int kTcSpinLimit = 1 << 20;
+constexpr uint32_t kTcSuspendNs = 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -44,15 +48,16 @@ __device__ __forceinline__ void commit(unsigned long long *mbar) {
           smem_u32(mbar))
       : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t phase,
+                                          int limit = kTcSpinLimit) {
   const uint32_t a = smem_u32(mbar);
-  for (int i = 0; i < kTcSpinLimit; ++i) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(a), "r"(phase)
+        : "r"(a), "r"(phase), "r"(kTcSuspendNs)
         : "memory");
     if (done) return true;
   }

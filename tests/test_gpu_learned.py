@@ -170,6 +170,35 @@ def test_tensor_core_network_matches_oracle(n):
     assert np.abs(y - ref).max() <= 0.02 * np.abs(ref).max() + 1e-6
 
 
+def test_tensor_core_wait_timeout_reported_and_recoverable(monkeypatch):
+    """The bounded wait for the tensor core, made to run out without a fault:
+    with BHGRAV_TC_WAIT_PROBE=k the evaluator issues no MMA (nothing is in
+    flight) and gives up its first wait on a barrier no one arrives at after
+    k tries; bh_mlp_eval returns BH_ERR_DEVICE_TIMEOUT with its reason, the
+    kernel releases its tensor memory, and the same context then evaluates
+    the same rows as a fresh one does, bit for bit (3,000 rows: several CTAs,
+    a ragged last tile)."""
+    import time
+    rng = np.random.default_rng(7)
+    w = L.init_weights(5) + rng.normal(0, 0.05, B.MLP_NW).astype(np.float32)
+    x = torch.as_tensor(rng.normal(0, 1, (3000, 10)).astype(np.float32)).cuda()
+    s = B.Solver(learned=True)
+    s.set_mlp(w)
+    monkeypatch.setenv("BHGRAV_TC_WAIT_PROBE", "16")
+    t0 = time.perf_counter()
+    with pytest.raises(B.BHError) as e:
+        s.mlp_eval(x)
+    assert time.perf_counter() - t0 < 60.0
+    assert e.value.status == B.BH_ERR_DEVICE_TIMEOUT
+    assert "wait" in str(e.value) and "gave up" in str(e.value)
+    monkeypatch.delenv("BHGRAV_TC_WAIT_PROBE")
+    got = s.mlp_eval(x).cpu().numpy()
+    fresh = B.Solver(learned=True)
+    fresh.set_mlp(w)
+    want = fresh.mlp_eval(x).cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.array_equal(got, want)
+
+
 def test_tensor_core_learned_walk_matches_the_warp_level_one_and_the_oracle():
     """The learned walk with the network on tcgen05 (learned = 2): the same
     per-row arithmetic as the mma.sync walk up to FP32 accumulation order,
