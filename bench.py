@@ -6,7 +6,7 @@ bh_build (block keys, tree topology, FP64 moments and quadrupoles) +
 bh_potential (opening radii for theta, walk).  Default workload: the Maclaurin
 spheroid (eccentricity 0.9, 2,039,808 cells, 3 AMR levels at the surface),
 per-cell opening test at theta 0.72 with the quadrupole term, binary32 walk
-with Kahan sum -- a setting that keeps the max relative error against the
+with compensated sum -- a setting that keeps the max relative error against the
 direct sum below 1e-3 over every cell (7.0e-4, `accuracy_all_cells`: the
 same worst case as theta 0.7, 4 % less work; 0.74 reaches 8.0e-4, 0.76
 1.02e-3).
@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--train-fields", type=int, default=200,
                     help="--workload learned: seeded training fields")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--walk-shape", default=None,
+                    help="W,P,T: the walk's launch shape (warps per CTA, target pairs per "
+                         "lane, groups per take; 0 = plain grid) instead of bh_autotune")
     ap.add_argument("--all-cells-limit", type=int, default=4_200_000,
                     help="largest field (cells) whose potentials are compared with the "
                          "exhaustive direct sum over every cell (N^2 work)")
@@ -410,7 +413,7 @@ def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=Fals
     deepest cell level): the smallest internal node has side 2^-(maxlev-1),
     so l/theta = 2 exceeds every box-unit distance (at most sqrt(3)) and no
     internal node is ever accepted -- every cell meets every other cell
-    singly, the direct sum of Eq. 2 in binary32 with Kahan summation; the
+    singly, the direct sum of Eq. 2 in binary32 with compensated summation; the
     interaction counts are checked to be N - 1 everywhere.  Relative per
     cell, or, for the zero-mean periodic field, relative to max |Phi|.
     Skipped (None) above `limit` cells (N^2 interactions)."""
@@ -433,7 +436,7 @@ def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=Fals
     t_direct = time.perf_counter() - t0
     ref.close()
     out = {"direct": f"the library at theta 2^-{maxlev}: every pair direct (counts N-1 "
-                     "checked), binary32 + Kahan", "cells": n, "direct_s": t_direct}
+                     "checked), binary32, compensated sum", "cells": n, "direct_s": t_direct}
     for key, phi in phis.items():
         if phi is None:
             continue
@@ -572,7 +575,7 @@ def batched_arm(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s = bh.Solver(device=dev.index, stream=stream)
     s.build_batch(nb, level, ijk, d_rho, lo, ln)
-    wpc, npairs = s.autotune(theta)
+    wpc, npairs, ticket = s.autotune(theta)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.solve_graph(d_rho, theta, 1.0, out)
@@ -688,9 +691,10 @@ def batched_arm(args):
             "config": {"workload": "batched: 64 fields of 16^3-128^3 cells, 1-8 Gaussian blobs "
                                    "(seeds 5000-5063)", "cells": n, "fields": len(ws),
                        "field_cells": sorted({w.ncells for w in ws}), "theta": theta,
-                       "walk": "binary32, Kahan sum, per-cell opening test, monopole nodes",
+                       "walk": "binary32, compensated sum, per-cell opening test, monopole nodes",
                        "step": "one CUDA-graph launch: moments + walk of all fields",
                        "tuned_warps_per_cta": wpc, "tuned_target_pairs_per_lane": npairs,
+                       "tuned_groups_per_take": ticket,
                        "l2": "flushed between steps"},
             "vs_plain": {"how": "the same fields one after the other: bh_build + bh_potential",
                          "value": p_value, "ms_per_step": p_ms, "speedup": value / p_value,
@@ -852,7 +856,7 @@ def learned_arm(args):
         "data": "synthetic",
         "config": {"workload": w.name + " learned", "cells": n, "nodes": nn,
                    "theta": args.theta,
-                   "walk": "binary32, Kahan sum, per-cell opening test, monopole nodes times "
+                   "walk": "binary32, compensated sum, per-cell opening test, monopole nodes times "
                            "(1 + s^2 MLP(x)); MLP 10-64-64-1 GELU, bf16 weights and "
                            "activations, FP32 accumulate (mma.sync m16n8k16)",
                    "training": {"fields": args.train_fields, "pairs": npairs,
@@ -874,7 +878,7 @@ def learned_arm(args):
                                 "peak": bf16_peak / 1e12,
                                 "frac": mlp_flops / walk_s / bf16_peak,
                                 "peak_basis": "measured bf16 dense (burst)"}},
-        "vs_plain": {"theta": args.plain_theta, "walk": "binary32, Kahan sum, per-cell, monopole",
+        "vs_plain": {"theta": args.plain_theta, "walk": "binary32, compensated sum, per-cell, monopole",
                      **{k: v for k, v in res["plain"].items() if k != "theta"},
                      "speedup": L_["value"] / res["plain"]["value"]},
         "vs_same_theta": {"theta": args.theta, "walk": "the plain walk, no network",
@@ -970,6 +974,15 @@ def main():
     out = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
+    # the walk's launch shape, tuned on this tree (CTA width, targets per warp,
+    # plain or persistent grid); untimed
+    with torch.cuda.stream(stream):
+        solver.build(mesh.level, mesh.ijk, d_rho)
+    if args.walk_shape:
+        shape = tuple(int(v) for v in args.walk_shape.split(","))
+        solver.set_walk_shape(*shape)
+    else:
+        shape = solver.autotune(args.theta)
     if world > 1:
         dist.barrier()
     clk = ClockSampler(local)
@@ -1015,6 +1028,9 @@ def main():
     if not args.no_plain and not periodic:
         psolver = bh.Solver(device=local, stream=stream)
         pout = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            psolver.build(mesh.level, mesh.ijk, d_rho)
+        pshape = psolver.autotune(args.plain_theta)
         psteps = max(5, args.steps // 3)
         p_step, p_build, p_walk = timed_steps(psolver, mesh, d_rho, args.plain_theta, pout,
                                               psteps, args.warmup, flush, stream)
@@ -1022,7 +1038,9 @@ def main():
         p_value = job_rate(world, n, psteps, p_total)
         pi, pt, pc, pflops = work(psolver, args.plain_theta, False)
         phi_plain = pout.double().cpu().numpy()
-        plain = {"theta": args.plain_theta, "walk": "binary32, Kahan sum, per-cell, monopole",
+        plain = {"theta": args.plain_theta, "walk": "binary32, compensated sum, per-cell, monopole",
+                 "walk_shape": {"warps_per_cta": pshape[0], "target_pairs_per_lane": pshape[1],
+                                "groups_per_take": pshape[2]},
                  "value": p_value, "unit": "cells/s", "steps": psteps,
                  "ms_per_step": p_total / psteps,
                  "phases_ms": {"build": float(np.mean(p_build)),
@@ -1082,13 +1100,19 @@ def main():
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "cells": n, "nodes": nn, "theta": args.theta,
-                       "walk": "binary32, Kahan sum, "
+                       "walk": "binary32, compensated sum, "
                                + ("warp vote (paper)" if args.vote else "per-cell opening test")
                                + (f", periodic boundaries (Ewald table {args.ewald_grid}, "
                                   "series 3)" if periodic else "")
                                + (", quadrupole nodes" if quad else ", monopole nodes"),
                        "moments": "f64", "density_input": "f32",
                        "l2": "flushed between steps (256 MiB write)",
+                       "walk_shape": {"warps_per_cta": shape[0],
+                                      "target_pairs_per_lane": shape[1],
+                                      "groups_per_take": shape[2],
+                                      "how": ("set by --walk-shape" if args.walk_shape else
+                                              "bh_autotune on this tree before timing")
+                                             + " (0 groups per take: plain grid)"},
                        "parallelism": f"replicas x{world}"},
             "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms)),
                           "step_median": float(np.median(step_ms)),

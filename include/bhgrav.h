@@ -176,14 +176,27 @@ bh_status bh_update_density(bh_ctx *ctx, const void *density, int density_is_fp6
 bh_status bh_sync_status(bh_ctx *ctx);
 
 /* Times the binary32 per-cell walk of the current tree at this theta for
- * every launch shape it offers -- CTAs of 2, 4, 8 and 16 warps, and warps
- * that walk for 64 targets (a 4x4x4 octant of a block, one pair of
- * x-neighbours per lane) or 128 targets (a 8x4x4 slab, two pairs per lane;
- * not for the periodic walk) -- and keeps the fastest for later walks.  All
- * shapes give bit-identical potentials.  shape (may be NULL) receives two
- * ints: {warps per CTA, target pairs per lane} ({0, 0} for walk modes with a
- * fixed launch shape).  Allocates a scratch output once. */
+ * every launch shape it offers -- CTAs of 2, 4, 8 and 16 warps; warps that
+ * walk for 64 targets (a 4x4x4 octant of a block, one pair of x-neighbours
+ * per lane) or 128 targets (a 8x4x4 slab, two pairs per lane); and either a
+ * plain grid of one warp per group or a persistent grid (as many CTAs as the
+ * GPU holds at once) whose warps take 1, 2 or 4 groups at a time from a work
+ * counter (the periodic walk: CTA width only) -- and keeps the fastest for
+ * later walks.  All shapes give bit-identical potentials.  shape (may be
+ * NULL) receives three ints: {warps per CTA, target pairs per lane, groups
+ * per take (0 = plain grid)}; all 0 for walk modes with a fixed launch
+ * shape.  Allocates a scratch output once. */
 bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape);
+
+/* Sets the launch shape of the binary32 per-cell walk (the three values
+ * bh_autotune chooses among), e.g. one found by an earlier bh_autotune on
+ * the same kind of mesh: warps per CTA (1..16), target pairs per lane (1 or
+ * 2) and groups per take of the persistent grid (0 = plain grid, 1..64); 0
+ * for the first two means the default.  Potentials do not depend on the
+ * shape (bit for bit).  Drops a captured bh_solve_graph graph.  BH_ERR_ARG
+ * for values out of range (the periodic walk: one pair, plain grid). */
+bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
+                            int groups_per_take);
 
 /* bh_update_density + bh_potential as ONE CUDA graph launch: the first call
  * (or a call with a different density/out pointer, density type, theta or G)

@@ -22,7 +22,8 @@ BH_PREC_F32, BH_PREC_F64 = 0, 1
 BH_CRIT_PER_CELL, BH_CRIT_WARP_VOTE = 0, 1
 
 EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
-            "bh_update_density", "bh_sync_status", "bh_autotune", "bh_solve_graph",
+            "bh_update_density", "bh_sync_status", "bh_autotune", "bh_set_walk_shape",
+            "bh_solve_graph",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
             "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats",
@@ -80,6 +81,7 @@ def load(build_if_needed: bool = True):
         lib.bh_update_density.argtypes = [P, P, I]
         lib.bh_sync_status.argtypes = [P]
         lib.bh_autotune.argtypes = [P, D, P]
+        lib.bh_set_walk_shape.argtypes = [P, I, I, I]
         lib.bh_solve_graph.argtypes = [P, P, I, D, D, P]
         lib.bh_walk_counts.argtypes = [P, D, P, P, P]
         lib.bh_tree_size.argtypes = [P, P, P, P]
@@ -101,7 +103,8 @@ def load(build_if_needed: bool = True):
         lib.bh_destroy.argtypes = [P]
         lib.bh_destroy.restype = None
         for name in ("bh_create", "bh_build", "bh_build_batch", "bh_update_density",
-                     "bh_sync_status", "bh_autotune", "bh_solve_graph", "bh_potential",
+                     "bh_sync_status", "bh_autotune", "bh_set_walk_shape", "bh_solve_graph",
+                     "bh_potential",
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
@@ -190,10 +193,16 @@ def bh_sync_status(ctx) -> None:
 
 
 def bh_autotune(ctx, theta: float) -> tuple:
-    """Returns the chosen (warps per CTA, target pairs per lane)."""
-    sh = (ctypes.c_int * 2)()
+    """Returns the chosen (warps per CTA, target pairs per lane, groups per
+    take of the persistent walk; 0 = plain grid)."""
+    sh = (ctypes.c_int * 3)()
     _check(ctx, load().bh_autotune(ctx, float(theta), sh), "bh_autotune")
-    return int(sh[0]), int(sh[1])
+    return int(sh[0]), int(sh[1]), int(sh[2])
+
+
+def bh_set_walk_shape(ctx, warps: int, pairs: int, groups_per_take: int) -> None:
+    _check(ctx, load().bh_set_walk_shape(ctx, int(warps), int(pairs), int(groups_per_take)),
+           "bh_set_walk_shape")
 
 
 def bh_solve_graph(ctx, density, theta: float, G: float, out) -> None:
@@ -434,8 +443,13 @@ class Solver:
         bh_sync_status(self._ctx)
 
     def autotune(self, theta: float) -> tuple:
-        """Tunes the walk's launch shape: (warps per CTA, target pairs per lane)."""
+        """Tunes the walk's launch shape: (warps per CTA, target pairs per lane,
+        groups per take of the persistent walk or 0)."""
         return bh_autotune(self._ctx, theta)
+
+    def set_walk_shape(self, warps: int, pairs: int = 0, groups_per_take: int = 0):
+        """Pins the walk's launch shape (see bh_set_walk_shape)."""
+        bh_set_walk_shape(self._ctx, warps, pairs, groups_per_take)
 
     def solve_graph(self, density, theta: float, G: float = 1.0, out=None):
         import torch

@@ -421,6 +421,7 @@ static cudaError_t enqueue_walk(bh_ctx *ctx, cudaStream_t s, double G, void *out
                                      n_test, n_leaf, shape.warps);
   if (!n_int && ctx->opt.learned == 2) return bhg::launch_walk_learned_tc(s, ctx, G, out);
   if (!n_int && ctx->opt.learned) return bhg::launch_walk_learned(s, ctx, G, out);
+  shape.counter = t.d_flags + 4;  // the work counter of the persistent walk
   return bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
                           t.d_orig, field_args(t), G, out, n_int, n_test, n_leaf, shape);
 }
@@ -459,7 +460,7 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
   if (cudaSetDevice(device) != cudaSuccess || bhg::prepare_learned_kernels() != cudaSuccess ||
       bhg::prepare_mlp_tc_kernel() != cudaSuccess ||
       bhg::prepare_learned_tc_kernel() != cudaSuccess ||
-      bhg::dev_malloc(&ctx->tree.d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
+      bhg::dev_malloc(&ctx->tree.d_flags, 8 * sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->tree.h_flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->tree.d_flags) cudaFree(ctx->tree.d_flags);
@@ -732,15 +733,19 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
     BH_CUDA(cudaEventCreate(&e0));
     BH_CUDA(cudaEventCreate(&e1));
     const int cand[4] = {2, 4, 8, 16};
+    const int tickets[4] = {0, 1, 2, 4};  // plain grid, or persistent with 1/2/4 groups a grab
+    const int nticket = ctx->opt.periodic ? 1 : 4;
     float best = 1e30f;
     bhg::WalkShape best_s;
-    best_s.warps = 8;
+    best_s.warps = 4;
     best_s.pairs = 1;
     for (int np = 1; np <= npairs; ++np) {
-      for (int w : cand) {
+      for (int ti = 0; ti < nticket * 4; ++ti) {
+        const int w = cand[ti % 4];
         bhg::WalkShape sh;
         sh.warps = w;
         sh.pairs = np;
+        sh.ticket = tickets[ti / 5];
         float tmin = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
           BH_CUDA(cudaEventRecord(e0, ctx->stream));
@@ -766,7 +771,26 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
   if (shape) {
     shape[0] = tunable ? t.shape.warps : 0;
     shape[1] = tunable ? t.shape.pairs : 0;
+    shape[2] = tunable ? t.shape.ticket : 0;
   }
+  return BH_OK;
+}
+
+bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
+                            int groups_per_take) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!(warps_per_cta == 0 || (warps_per_cta >= 1 && warps_per_cta <= 16)) ||
+      !(pairs_per_lane >= 0 && pairs_per_lane <= 2) ||
+      !(groups_per_take >= 0 && groups_per_take <= 64))
+    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: warps 0..16, pairs 0..2, groups 0..64");
+  if (ctx->opt.periodic && (pairs_per_lane > 1 || groups_per_take > 0))
+    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: the periodic walk has one pair per lane "
+                                 "and a plain grid");
+  ctx->tree.shape.warps = warps_per_cta;
+  ctx->tree.shape.pairs = pairs_per_lane;
+  ctx->tree.shape.ticket = groups_per_take;
+  drop_graph(ctx->tree);  // a captured walk holds the old shape
   return BH_OK;
 }
 

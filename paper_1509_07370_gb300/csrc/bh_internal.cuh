@@ -80,12 +80,17 @@ struct __align__(32) WalkQuad {
 };
 static_assert(sizeof(WalkQuad) == 32, "quadrupole record must be 32 bytes");
 
-// Launch shape of the per-cell binary32 walk: warps per CTA and x-neighbour
+// Launch shape of the per-cell binary32 walk: warps per CTA, x-neighbour
 // target pairs per lane (a warp's group of targets: 1 pair = a 4x4x4 octant,
-// 2 pairs = a 8x4x4 slab); 0 = the default.
+// 2 pairs = a 8x4x4 slab), and the schedule: ticket = 0 a plain grid of one
+// warp per group; ticket = k > 0 a persistent grid (as many CTAs as fit on
+// the GPU at once) whose warps take k groups at a time from `counter` (a
+// device word that the launch resets) until all are taken.  0 = defaults.
 struct WalkShape {
   int warps = 0;
   int pairs = 0;
+  int ticket = 0;
+  unsigned *counter = nullptr;
 };
 
 struct Tree {
@@ -98,7 +103,8 @@ struct Tree {
   int *d_orig = nullptr;
   int *d_pos = nullptr;         // sorted position of each caller block
   int *d_child = nullptr;       // child lists of the top nodes: 8 per top node (2 nb_cap ints)
-  unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total
+  unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total,
+                                // [4] work counter of the persistent walk (8 entries)
   unsigned *h_flags = nullptr;  // pinned mirror of d_flags
   // fields
   int nfields = 0;

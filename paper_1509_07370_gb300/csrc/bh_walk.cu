@@ -119,7 +119,10 @@ __device__ __forceinline__ void quad_shared(const WalkQuad *qr, float dy, float 
 // Cells 2j and 2j + 1 are x-neighbours with the same y and z, so they share
 // dy, dz and h too.  The 8 positive cell terms are summed plainly (a
 // relative error of at most 7 units in the last place of their sum) and the
-// sum joins the compensated total once.
+// sum joins the compensated total once.  (A second form of this loop for
+// bottom nodes that hold none of the warp's targets, the openers' mask a
+// factor on the mass instead of a compare and select per cell, took 8 more
+// registers and made the walk slower.)
 template <int NP, bool KAHAN, bool COUNTS>
 __device__ __forceinline__ void bottom_cells(unsigned node, unsigned open,
                                              const WalkRec *__restrict__ rec, float ty,
@@ -396,6 +399,33 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
                                       n_int, n_test, n_leaf);
 }
 
+// The same walk on a persistent grid: each warp takes `per_ticket`
+// consecutive groups at a time from the work counter (one atomic add by lane
+// 0; no waiting on other warps) until every group is taken.  Consecutive
+// groups are neighbouring octants, so the warps of one CTA tend to walk
+// through the same nodes.
+template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
+__global__ void __launch_bounds__(kMaxWalkThreads)
+    k_walk_queue(unsigned nunits, unsigned per_ticket, unsigned *__restrict__ counter,
+                 const WalkRec *__restrict__ rec, const WalkQuad *__restrict__ qrec,
+                 const int4 *__restrict__ blk, const int *__restrict__ orig,
+                 const int4 *__restrict__ fld, const double *__restrict__ invL,
+                 const unsigned long long *__restrict__ mmax, double G, float *__restrict__ out,
+                 int32_t *__restrict__ n_int, int32_t *__restrict__ n_test,
+                 int32_t *__restrict__ n_leaf) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned u0 = 0u;
+    if (lane == 0) u0 = atomicAdd(counter, per_ticket);
+    u0 = __shfl_sync(kFull, u0, 0);
+    if (u0 >= nunits) return;
+    const unsigned u1 = u0 + per_ticket < nunits ? u0 + per_ticket : nunits;
+    for (unsigned u = u0; u < u1; ++u)
+      walk_group<NP, KAHAN, COUNTS, QUAD>(u, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
+                                          n_int, n_test, n_leaf);
+  }
+}
+
 // ---- one target per lane: binary64 interactions and/or the warp vote --------
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kWalkThreads)
@@ -510,9 +540,28 @@ __global__ void __launch_bounds__(kWalkThreads)
 template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 cudaError_t go_pair_np(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *qrec,
                        const int4 *blk, const int *orig, const FieldArgs &fa, double G, void *out,
-                       int32_t *ni, int32_t *nt, int32_t *nl, int warps) {
+                       int32_t *ni, int32_t *nt, int32_t *nl, const WalkShape &shape) {
   const unsigned nunits = (unsigned)nb * (8u / NP);
-  const int w = warps > 0 ? warps : kDefaultWarps;
+  const int w = shape.warps > 0 ? shape.warps : kDefaultWarps;
+  if (shape.ticket > 0 && shape.counter) {  // persistent: the CTAs that fit at once
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, k_walk_queue<NP, KAHAN, COUNTS, QUAD>, 32 * w, 0);
+    if (e != cudaSuccess) return e;
+    const unsigned warps_needed = (nunits + (unsigned)shape.ticket - 1) / (unsigned)shape.ticket;
+    const unsigned ctas_needed = (warps_needed + (unsigned)w - 1) / (unsigned)w;
+    const unsigned resident = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    const unsigned grid = ctas_needed < resident ? ctas_needed : resident;
+    e = cudaMemsetAsync(shape.counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_walk_queue<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
+        nunits, (unsigned)shape.ticket, shape.counter, rec, qrec, blk, orig, fa.fld, fa.invL,
+        fa.mmax, G, (float *)out, ni, nt, nl);
+    return cudaGetLastError();
+  }
   const int grid = (int)((nunits + w - 1) / w);
   k_walk_pair<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
       nunits, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
@@ -526,9 +575,9 @@ cudaError_t go_pair(cudaStream_t s, int nb, const WalkRec *rec, const WalkQuad *
   const int np = shape.pairs > 0 ? shape.pairs : kDefaultPairs;
   if (np == 2)
     return go_pair_np<2, KAHAN, COUNTS, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, ni, nt, nl,
-                                              shape.warps);
+                                              shape);
   return go_pair_np<1, KAHAN, COUNTS, QUAD>(s, nb, rec, qrec, blk, orig, fa, G, out, ni, nt, nl,
-                                            shape.warps);
+                                            shape);
 }
 
 template <bool F64, bool VOTE, bool KAHAN, bool COUNTS, bool QUAD>

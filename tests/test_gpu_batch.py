@@ -93,8 +93,8 @@ def test_update_density_graph_replay_and_autotune():
         got = s.potential(0.7)
     s.stream.synchronize()
     assert np.array_equal(got.cpu().numpy(), want)
-    w, npairs = s.autotune(0.7)
-    assert w in (2, 4, 8, 16) and npairs in (1, 2)
+    w, npairs, ticket = s.autotune(0.7)
+    assert w in (2, 4, 8, 16) and npairs in (1, 2) and ticket in (0, 1, 2, 4)
     out = torch.empty(s.ncells, device="cuda")
     for _ in range(3):                                  # capture once, replay twice
         out.fill_(float("nan"))
@@ -131,3 +131,50 @@ def test_batch_errors():
     with pytest.raises(B.BHError) as e:
         plain.solve_graph(torch.as_tensor(ws[0].density.reshape(-1)).cuda(), 0.5)
     assert e.value.status == B.BH_ERR_ARG
+
+
+SHAPES = [(4, 1, 0), (2, 1, 0), (16, 1, 0), (8, 2, 0), (4, 1, 1), (8, 1, 4), (4, 2, 2),
+          (1, 2, 64), (16, 1, 1), (16, 2, 0)]
+
+
+@pytest.mark.parametrize("quad", [False, True])
+def test_every_walk_shape_gives_identical_potentials(quad):
+    """Every launch shape the autotuner can choose -- CTA width, 64- or
+    128-target groups, plain or persistent grid with 1-64 groups per take --
+    gives the potentials of the default shape bit for bit (the same
+    decisions and the same additions in the same order, a masked target's
+    zero term changing nothing), on the batch of uneven fields and through
+    the graph replay; the counting walk gives the same counts."""
+    ws = _fields()
+    nb, level, ijk, lo, ln, rho = mg.concat_fields(ws)
+    d = torch.as_tensor(rho).cuda()
+    s = _solver(quadrupole=quad)
+    s.build_batch(nb, level, ijk, d, lo, ln)
+    with torch.cuda.stream(s.stream):
+        want = s.potential(0.6).cpu().numpy()
+        wi, wt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+    out = torch.empty(s.ncells, device="cuda")
+    for shape in SHAPES:
+        s.set_walk_shape(*shape)
+        with torch.cuda.stream(s.stream):
+            got = s.potential(0.6).cpu().numpy()
+            gi, gt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+        assert np.array_equal(got, want), shape
+        assert np.array_equal(gi, wi) and np.array_equal(gt, wt), shape
+        out.fill_(float("nan"))
+        s.solve_graph(d, 0.6, 1.0, out)
+        s.stream.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want), shape
+
+
+def test_walk_shape_arguments_checked():
+    s = _solver()
+    for bad in [(17, 1, 0), (4, 3, 0), (4, 1, 65), (-1, 1, 0)]:
+        with pytest.raises(B.BHError) as e:
+            s.set_walk_shape(*bad)
+        assert e.value.status == B.BH_ERR_ARG
+    p = B.Solver(periodic=True)
+    for bad in [(4, 2, 0), (4, 1, 1)]:
+        with pytest.raises(B.BHError):
+            p.set_walk_shape(*bad)
+    p.set_walk_shape(16, 1, 0)
