@@ -704,9 +704,10 @@ def batched_arm(args):
                              "value": n / (u_ms * 1e-3), "ms_per_step": u_ms,
                              "speedup": value / (n / (u_ms * 1e-3))}},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
-            # per graph launch: largest-mass pass, k_blocks, one top-moment
-            # launch per block level above 0, opening radii, walk
-            "gpu_launches": (s.tree_size()[2] - 3 + 4) * args.steps}
+            # per graph launch: largest-mass pass, k_blocks and its two upper
+            # levels, one top-moment launch per block level above 0, opening
+            # radii, walk
+            "gpu_launches": (s.tree_size()[2] - 3 + 6) * args.steps}
     print(json.dumps(line), flush=True)
     for ps in solvers:
         ps.close()
@@ -886,7 +887,7 @@ def learned_arm(args):
                           "speedup": L_["value"] / res["same"]["value"]},
         "accuracy_all_cells": all_cells,
         "clocks": clocks, "e2e": e2e,
-        "gpu_launches": (8 + (maxlev - 3) + 1) * args.steps,
+        "gpu_launches": (10 + (maxlev - 3) + 1) * args.steps,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -1018,9 +1019,9 @@ def main():
     traffic = captured_traffic(w.name, args.theta, mode) if not args.vote else None
     _, nn, maxlev = solver.tree_size()
     # keys, sort, tiling, scan, top nodes, top-node child lists, largest mass,
-    # blocks, one top-moment launch per block level (max block level =
-    # maxlev - 3), walk
-    launches_per_step = 8 + (maxlev - 3) + 1
+    # blocks and their two upper levels, one top-moment launch per block
+    # level (max block level = maxlev - 3), walk
+    launches_per_step = 10 + (maxlev - 3) + 1
 
     # the plain walk (monopole, per-cell) at the theta of equal accuracy
     plain = None

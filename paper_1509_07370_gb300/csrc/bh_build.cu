@@ -520,11 +520,6 @@ __global__ void __launch_bounds__(kBlockThreads)
              unsigned *flags) {
   __shared__ double cm[512], cxs[512], cys[512], czs[512];  // cells, local Morton order
   __shared__ float cmu[512];                                // cell mass, binary32 unit
-  __shared__ double gm[64], gx[64], gy[64], gz[64];         // level lb+2 nodes
-  __shared__ double pm[8], px[8], py[8], pz[8];             // level lb+1 nodes
-  __shared__ double gq[64][6], pq[8][6];                    // their quadrupoles (FP64)
-  __shared__ float gqf[64][6], pqf[8][6];                   // (binary32)
-  __shared__ float go[64][3], po[8][3], gmu[64], pmu[8];    // binary32 offsets R - c, masses
   const bool quad64 = q64 != nullptr;                       // FP64 quadrupoles
   const bool quad32 = !quad64 && qrec != nullptr;           // binary32 quadrupoles
   const int p = blockIdx.x;
@@ -590,19 +585,14 @@ __global__ void __launch_bounds__(kBlockThreads)
     for (int o = 0; o < 8; ++o)
       accumulate(M, Sx, Sy, Sz, cm[8 * q + o], cxs[8 * q + o], cys[8 * q + o], czs[8 * q + o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    gm[q] = r.m;
-    gx[q] = r.x;
-    gy[q] = r.y;
-    gz[q] = r.z;
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    gmu[q] = store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
         const int k = 8 * q + o;
         add_shifted(Q, nullptr, cm[k], cxs[k] - r.x, cys[k] - r.y, czs[k] - r.z);
       }
-      for (int a = 0; a < 6; ++a) gq[q][a] = Q[a];
       store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
       // children: cells at c +- h/2 (h = 2^-(lb+3)) with o = 0
@@ -615,84 +605,82 @@ __global__ void __launch_bounds__(kBlockThreads)
         add_shifted_ff(Q, nullptr, cmu[8 * q + o], __fsub_rn(dx, ox), __fsub_rn(dy, oy),
                        __fsub_rn(dz, oz));
       }
-      for (int a = 0; a < 6; ++a) gqf[q][a] = Q[a];
-      go[q][0] = ox;
-      go[q][1] = oy;
-      go[q][2] = oz;
       store_quad_f(id, Q, qrec);
     }
   }
-  __syncthreads();
-  if (t < 8) {  // nodes at level lb+1
-    const int c = t;
-    const double cx = centre_coord(2 * B.y + (c & 1), lb + 1);
-    const double cy = centre_coord(2 * B.z + ((c >> 1) & 1), lb + 1);
-    const double cz = centre_coord(2 * B.w + ((c >> 2) & 1), lb + 1);
-    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+}
+
+// The 8 nodes at level lb+1 of every block (STAGE 1) or every block's root
+// (STAGE 0), one node per thread over all blocks, so that the FP64 work runs
+// in full warps (in one CTA per block these levels kept 8 and 1 lanes of a
+// warp busy at the cost of a whole warp).  Their children -- written by
+// k_blocks (stage 1) or by stage 1 (stage 0) -- are read back from the node
+// arrays; the arithmetic is that of k_blocks (Eq. 5 in octant order; the
+// binary32 quadrupole shift from the children's binary32 centre-of-mass
+// offsets), so the results are the same bit for bit.
+template <int STAGE>
+__global__ void __launch_bounds__(256)
+    k_block_upper(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
+                  const int *__restrict__ count, const int *__restrict__ prestart,
+                  const int *__restrict__ fid, const unsigned long long *__restrict__ mmax,
+                  float inv_theta, int64_t n_nodes, double4_32a *__restrict__ mom,
+                  WalkRec *__restrict__ rec, float2 *__restrict__ aux, uint8_t *__restrict__ lvl,
+                  double *__restrict__ q64, WalkQuad *__restrict__ qrec) {
+  constexpr int kPer = STAGE ? 8 : 1;  // nodes of this level per block
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nb * kPer) return;
+  const int p = (int)(i / kPer), c = (int)(i % kPer);
+  const int4 B = blk[p];
+  const int lb = B.x;
+  if (lb < 0 || lb > kMaxBlockLevel) return;  // flagged by k_block_keys
+  const int64_t root = (int64_t)prestart[p] + count[p];
+  if (root < 0 || root + kNodesPerBlock > n_nodes) return;  // flagged by k_blocks
+  const double inv_unit = pow2i(-mass_exponent(mmax[fid[orig[p]]]));
+  const int lev = STAGE ? lb + 1 : lb;
+  const int ix = STAGE ? 2 * B.y + (c & 1) : B.y;
+  const int iy = STAGE ? 2 * B.z + ((c >> 1) & 1) : B.z;
+  const int iz = STAGE ? 2 * B.w + ((c >> 2) & 1) : B.w;
+  const int64_t id = STAGE ? root + 1 + 73 * c : root;
+  const int64_t skip = STAGE ? id + 73 : root + kNodesPerBlock;
+  const int64_t first = id + 1, stride = STAGE ? 9 : 73;  // child o at first + stride o
+  const double cx = centre_coord(ix, lev), cy = centre_coord(iy, lev), cz = centre_coord(iz, lev);
+  double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
 #pragma unroll
-    for (int o = 0; o < 8; ++o)
-      accumulate(M, Sx, Sy, Sz, gm[8 * c + o], gx[8 * c + o], gy[8 * c + o], gz[8 * c + o]);
-    const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    pm[c] = r.m;
-    px[c] = r.x;
-    py[c] = r.y;
-    pz[c] = r.z;
-    const int64_t id = root + 1 + 73 * c;
-    pmu[c] = store_internal(id, id + 73, lb + 1, r, mom, rec, aux, lvl, inv_unit, inv_theta);
-    if (quad64) {
-      double Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int o = 0; o < 8; ++o) {
-        const int k = 8 * c + o;
-        add_shifted(Q, gq[k], gm[k], gx[k] - r.x, gy[k] - r.y, gz[k] - r.z);
-      }
-      for (int a = 0; a < 6; ++a) pq[c][a] = Q[a];
-      store_quad(id, Q, q64, qrec, inv_unit);
-    } else if (quad32) {
-      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
-                  oz = __double2float_rn(r.oz);
-      const float hc = pow2f(-(lb + 3));  // child centre - centre: +-2^-(lb+3)
-      float Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int o = 0; o < 8; ++o) {
-        const int k = 8 * c + o;
-        const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
-        add_shifted_ff(Q, gqf[k], gmu[k], __fsub_rn(__fadd_rn(dx, go[k][0]), ox),
-                       __fsub_rn(__fadd_rn(dy, go[k][1]), oy),
-                       __fsub_rn(__fadd_rn(dz, go[k][2]), oz));
-      }
-      for (int a = 0; a < 6; ++a) pqf[c][a] = Q[a];
-      po[c][0] = ox;
-      po[c][1] = oy;
-      po[c][2] = oz;
-      store_quad_f(id, Q, qrec);
-    }
+  for (int o = 0; o < 8; ++o) {
+    const double4_32a ch = mom[first + stride * o];
+    accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
   }
-  __syncthreads();
-  if (t == 0) {  // the block itself
-    const double cx = centre_coord(B.y, lb);
-    const double cy = centre_coord(B.z, lb);
-    const double cz = centre_coord(B.w, lb);
-    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-#pragma unroll
-    for (int o = 0; o < 8; ++o) accumulate(M, Sx, Sy, Sz, pm[o], px[o], py[o], pz[o]);
-    const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-    store_internal(root, root + kNodesPerBlock, lb, r, mom, rec, aux, lvl, inv_unit, inv_theta);
-    if (quad64) {
-      double Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int o = 0; o < 8; ++o) add_shifted(Q, pq[o], pm[o], px[o] - r.x, py[o] - r.y, pz[o] - r.z);
-      store_quad(root, Q, q64, qrec, inv_unit);
-    } else if (quad32) {
-      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
-                  oz = __double2float_rn(r.oz);
-      const float hc = pow2f(-(lb + 2));
-      float Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int o = 0; o < 8; ++o) {
-        const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
-        add_shifted_ff(Q, pqf[o], pmu[o], __fsub_rn(__fadd_rn(dx, po[o][0]), ox),
-                       __fsub_rn(__fadd_rn(dy, po[o][1]), oy),
-                       __fsub_rn(__fadd_rn(dz, po[o][2]), oz));
-      }
-      store_quad_f(root, Q, qrec);
+  const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
+  store_internal(id, skip, lev, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+  if (q64) {
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+      const int64_t k = first + stride * o;
+      const double4_32a ch = mom[k];
+      add_shifted(Q, q64 + 6 * k, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
     }
+    store_quad(id, Q, q64, qrec, inv_unit);
+  } else if (qrec) {
+    const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
+                oz = __double2float_rn(r.oz);
+    const float hc = pow2f(-(lev + 2));  // child centre - centre: +-2^-(lev+2)
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+    for (int o = 0; o < 8; ++o) {
+      const int64_t k = first + stride * o;
+      const double4_32a ch = mom[k];
+      // the child's binary32 offset R - c from its own centre, as k_blocks formed it
+      const float gx = __double2float_rn(__dsub_rn(ch.x, centre_coord(2 * ix + (o & 1), lev + 1)));
+      const float gy =
+          __double2float_rn(__dsub_rn(ch.y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
+      const float gz =
+          __double2float_rn(__dsub_rn(ch.z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
+      float Qc[6];
+      load_quad_f(qrec[k], Qc);
+      const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
+      add_shifted_ff(Q, Qc, rec[k].m, __fsub_rn(__fadd_rn(dx, gx), ox),
+                     __fsub_rn(__fadd_rn(dy, gy), oy), __fsub_rn(__fadd_rn(dz, gz), oz));
+    }
+    store_quad_f(id, Q, qrec);
   }
 }
 
@@ -881,6 +869,15 @@ cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *or
                                                   (const float *)density, fa.L, fa.fid, fa.mmax,
                                                   fa.inv_theta, n_nodes, mom, rec, aux, lvl, q64,
                                                   qrec, flags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_block_upper<1><<<grid_for((int64_t)nb * 8, 256), 256, 0, s>>>(
+      nb, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux, lvl,
+      q64, qrec);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_block_upper<0><<<grid_for(nb, 256), 256, 0, s>>>(
+      nb, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux, lvl,
+      q64, qrec);
   return cudaGetLastError();
 }
 
