@@ -280,7 +280,7 @@ def captured_traffic(workload_name, theta, mode):
 
 # ------------------------------------------------------------ CPU oracle --
 def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, periodic=False,
-               ewald_grid=64):
+               ewald_grid=64, worst=None):
     """Times the CPU oracle (tree + FP64 moments in full, walk on a sample of
     targets) and extrapolates to cells/s for the whole field."""
     from oracle import oracle as O
@@ -384,6 +384,22 @@ def oracle_leg(w, theta, cpu_seconds, phi_gpu=None, quad=False, plain=None, peri
             out["accuracy"]["plain_max_rel_vs_direct"] = float(
                 np.max(np.abs(phi_plain[dt] / d - 1.0)))
             out["accuracy"]["plain_theta"] = plain_theta
+        if worst is not None:
+            # the all-cells check's worst cells, against the oracle's FP64 direct sum: the
+            # walks' errors there and the library's own direct sum (the all-cells reference)
+            cells, lib_direct = worst
+            dw = tree.direct(targets=cells)
+            acc = {"cells": int(len(cells)),
+                   "how": "the 128 cells of largest error of each walk over every cell "
+                          "(against the library's direct sum), against the oracle's FP64 "
+                          "direct sum",
+                   "library_direct_max_rel_vs_oracle_direct": float(
+                       np.max(np.abs(lib_direct / dw - 1.0))),
+                   "max_rel_vs_oracle_direct": float(np.max(np.abs(phi_gpu[cells] / dw - 1.0)))}
+            if plain is not None:
+                acc["plain_max_rel_vs_oracle_direct"] = float(
+                    np.max(np.abs(plain[0][cells] / dw - 1.0)))
+            out["accuracy"]["worst_cells_vs_oracle_direct"] = acc
     return out
 
 
@@ -437,14 +453,19 @@ def all_cells_error(bh, mesh, d_rho, maxlev, phis, device, stream, periodic=Fals
     ref.close()
     out = {"direct": f"the library at theta 2^-{maxlev}: every pair direct (counts N-1 "
                      "checked), binary32, compensated sum", "cells": n, "direct_s": t_direct}
+    worst = []
     for key, phi in phis.items():
         if phi is None:
             continue
         p = torch.as_tensor(phi, device=device)
-        if periodic:
-            out[key] = float(((p - d).abs().max() / d.abs().max()).item())
-        else:
-            out[key] = float(((p / d - 1.0).abs().max()).item())
+        err = (p - d).abs() / d.abs().max() if periodic else (p / d - 1.0).abs()
+        out[key] = float(err.max().item())
+        worst.append(torch.topk(err, min(128, n)).indices)
+    # the cells where the walks err most, for the oracle's FP64 direct sum
+    if worst:
+        cells = torch.unique(torch.cat(worst))
+        out["_worst_cells"] = cells.cpu().numpy()
+        out["_direct_at_worst"] = d[cells].cpu().numpy()
     return out
 
 
@@ -847,6 +868,9 @@ def learned_arm(args):
         {"learned_max_rel_vs_direct": phi["learned"], "plain_max_rel_vs_direct": phi["plain"],
          "plain_same_theta_max_rel_vs_direct": phi["same"]}, dev, stream,
         limit=args.all_cells_limit)
+    if all_cells is not None:  # (the worst cells go to the oracle in the main arm only)
+        all_cells.pop("_worst_cells", None)
+        all_cells.pop("_direct_at_worst", None)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = learned_oracle_leg(w, args.theta, wts_dev, args.plain_theta, phi, args.cpu_seconds)
@@ -1088,11 +1112,15 @@ def main():
         if all_cells is not None and phi_plain is not None:
             all_cells["plain_theta"] = args.plain_theta
 
+    worst = None
+    if all_cells is not None and "_worst_cells" in all_cells:
+        worst = (all_cells.pop("_worst_cells"), all_cells.pop("_direct_at_worst"))
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_leg(w, args.theta, args.cpu_seconds, phi_gpu, quad=quad,
                          plain=(phi_plain, args.plain_theta) if phi_plain is not None else None,
-                         periodic=periodic, ewald_grid=args.ewald_grid)
+                         periodic=periodic, ewald_grid=args.ewald_grid,
+                         worst=None if periodic else worst)
 
     if rank == 0:
         line = {

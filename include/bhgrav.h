@@ -299,6 +299,13 @@ bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const int32_t *ijk
 bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int64_t *targets,
                          int64_t cap, float *feat, float *eps, int64_t *node, int64_t *count);
 
+/* Training targets of n pairs: z = eps / s^2 with s = feat[3] (DEVICE float
+ * arrays feat[n][10], eps[n] from bh_learn_pairs; z[n] written), the network
+ * output for which the learned walk's term (M/d)(1 + s^2 z) equals the
+ * node's exact contribution.  Not in the paper.  Enqueued on cuda_stream. */
+bh_status bh_learn_targets(int64_t n, const float *feat, const float *eps, float *z,
+                           void *cuda_stream);
+
 /* Gradient of the mean squared error of MLP(x) against z over n samples
  * (DEVICE x[n][10], z[n], weights w), written to DEVICE grad[4865]; the loss
  * to DEVICE *loss.  FP32.  Enqueued on cuda_stream. */

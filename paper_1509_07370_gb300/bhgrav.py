@@ -26,6 +26,7 @@ EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_solve_graph",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
+            "bh_learn_targets",
             "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats",
             "bh_set_ewald", "bh_ewald_eval", "bh_last_error", "bh_destroy")
 
@@ -91,6 +92,7 @@ def load(build_if_needed: bool = True):
         lib.bh_solve_noalloc.argtypes = [I, P, P, P, D, P, I, D, D, P, P]
         lib.bh_learn_pairs.argtypes = [P, D, ctypes.c_int64, P, ctypes.c_int64, P, P, P, P]
         lib.bh_mlp_grad.argtypes = [ctypes.c_int64, P, P, P, P, P, P]
+        lib.bh_learn_targets.argtypes = [ctypes.c_int64, P, P, P, P]
         lib.bh_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, P]
         lib.bh_set_mlp.argtypes = [P, P]
         lib.bh_get_mlp.argtypes = [P, P]
@@ -107,7 +109,8 @@ def load(build_if_needed: bool = True):
                      "bh_potential",
                      "bh_walk_counts",
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
-                     "bh_solve_noalloc", "bh_learn_pairs", "bh_mlp_grad", "bh_mlp_adam",
+                     "bh_solve_noalloc", "bh_learn_pairs", "bh_learn_targets", "bh_mlp_grad",
+                     "bh_mlp_adam",
                      "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats", "bh_set_ewald",
                      "bh_ewald_eval"):
             getattr(lib, name).restype = I
@@ -308,6 +311,18 @@ def bh_learn_pairs(ctx, theta: float, targets, cap: int, with_nodes: bool = Fals
     if with_nodes:
         return feat[:n], eps[:n], cnt.value, node[:n]
     return feat[:n], eps[:n], cnt.value
+
+
+def bh_learn_targets(feat, eps, stream: int = 0):
+    """z = eps / s^2 of every pair (s = feat[:, 3]), on the device."""
+    import torch
+    z = torch.empty_like(eps)
+    st = load().bh_learn_targets(int(eps.numel()), ctypes.c_void_p(_dev_ptr(feat, torch.float32)),
+                                 ctypes.c_void_p(_dev_ptr(eps, torch.float32)),
+                                 ctypes.c_void_p(_dev_ptr(z, torch.float32)),
+                                 ctypes.c_void_p(int(stream)))
+    _check(None, st, "bh_learn_targets")
+    return z
 
 
 def bh_mlp_grad(x, z, w, grad, loss, stream: int = 0) -> None:

@@ -283,12 +283,33 @@ int frag_reg(int k) { return (k & 15) >> 3; }
 void frag_put(uint32_t &word, int k, uint16_t v) { word |= (uint32_t)v << (16 * (k & 1)); }
 uint16_t frag_get(uint32_t word, int k) { return (uint16_t)(word >> (16 * (k & 1))); }
 
+// Training target of a pair: z = eps / s^2 (s = feature 3), the network's
+// output for which the walk's term (M/d)(1 + s^2 z) is the node's exact
+// contribution.
+__global__ void k_learn_targets(int64_t n, const float *__restrict__ x,
+                                const float *__restrict__ eps, float *__restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = x[i * kMlpIn + 3];
+  z[i] = __fdiv_rn(eps[i], __fmul_rn(s, s));
+}
+
 }  // namespace
 }  // namespace bhg
 
 using namespace bhg;
 
 extern "C" {
+
+bh_status bh_learn_targets(int64_t n, const float *feat, const float *eps, float *z,
+                           void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!feat || !eps || !z))) return BH_ERR_ARG;
+  if (n == 0) return BH_OK;
+  k_learn_targets<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(n, feat,
+                                                                                        eps, z);
+  if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+  return BH_OK;
+}
 
 bh_status bh_learn_pairs(bh_ctx *ctx, double theta, int64_t ntargets, const int64_t *targets,
                          int64_t cap, float *feat, float *eps, int64_t *node, int64_t *count) {

@@ -88,8 +88,10 @@ def pairs_of(solver: bh.Solver, ncells: int, theta: float, ntargets: int, seed: 
         cells = np.unique(np.concatenate([cells, np.asarray(extra, dtype=cells.dtype)]))
     tg = torch.as_tensor(cells, dtype=torch.int64, device=solver.device)
     feat, eps, _ = solver.learn_pairs(theta, tg, cap)
-    s = feat[:, 3]
-    return feat, eps / (s * s)
+    with torch.cuda.stream(solver.stream):
+        z = bh.bh_learn_targets(feat, eps, solver.stream.cuda_stream)
+    solver.stream.synchronize()
+    return feat, z
 
 
 def make_dataset(nfields: int = 200, theta: float = 0.8, targets_per_field: int = 32,

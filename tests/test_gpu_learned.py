@@ -170,6 +170,20 @@ def test_tensor_core_network_matches_oracle(n):
     assert np.abs(y - ref).max() <= 0.02 * np.abs(ref).max() + 1e-6
 
 
+def test_training_targets_normalised_in_the_library():
+    """bh_learn_targets: z = eps / s^2 of each pair, s = feature 3, the same
+    binary32 operations as the definition (s * s rounded, then divided)."""
+    w = _field()
+    s = _gpu(w, learned=True)
+    tg = torch.as_tensor(np.arange(0, w.ncells, 997), dtype=torch.int64).cuda()
+    feat, eps, _ = s.learn_pairs(0.8, tg, 1 << 18)
+    z = B.bh_learn_targets(feat, eps).cpu().numpy()
+    f = feat.cpu().numpy()
+    e = eps.cpu().numpy()
+    sq = (f[:, 3] * f[:, 3]).astype(np.float32)
+    assert len(z) > 1000 and np.array_equal(z, (e / sq).astype(np.float32))
+
+
 def test_tensor_core_wait_timeout_reported_and_recoverable(monkeypatch):
     """The bounded wait for the tensor core, made to run out without a fault:
     with BHGRAV_TC_WAIT_PROBE=k the evaluator issues no MMA (nothing is in
