@@ -5,11 +5,10 @@ One step = the whole hot path on one synthetic field already resident in HBM:
 bh_build (block keys, tree topology, FP64 moments and quadrupoles) +
 bh_potential (opening radii for theta, walk).  Default workload: the Maclaurin
 spheroid (eccentricity 0.9, 2,039,808 cells, 3 AMR levels at the surface),
-per-cell opening test at theta 0.72 with the quadrupole term, binary32 walk
-with compensated sum -- a setting that keeps the max relative error against the
-direct sum below 1e-3 over every cell (7.0e-4, `accuracy_all_cells`: the
-same worst case as theta 0.7, 4 % less work; 0.74 reaches 8.0e-4, 0.76
-1.02e-3).
+per-cell opening test at theta 0.75 with the quadrupole term, binary32 walk
+with compensated sum -- the largest theta (in steps of 0.01) that keeps the
+max relative error against the direct sum below 1e-3 over every cell (9.1e-4,
+`accuracy_all_cells`; 0.72 gives 7.0e-4, 0.74 8.0e-4, 0.76 1.02e-3).
 
 Prints one JSON line (rank 0).  `value` is cells/s of the device-resident
 step over all ranks; `e2e` the same through bh_solve_host with pinned host
@@ -67,7 +66,7 @@ def parse():
     ap.add_argument("--workload", default="maclaurin",
                     choices=["maclaurin", "cloud_core", "uniform_sphere", "batched", "learned"])
     ap.add_argument("--theta", type=float, default=None,
-                    help="default 0.72 (the quadrupole headline), 0.7 with --monopole, "
+                    help="default 0.75 (the quadrupole headline), 0.7 with --monopole, "
                          "--vote or --periodic; 0.5 for --workload batched; 0.8 for "
                          "--workload learned")
     ap.add_argument("--monopole", action="store_true",
@@ -249,7 +248,7 @@ def captured_traffic(workload_name, theta, mode):
     import hashlib
     import re
     profile, files = {
-        "quadrupole": ("walk_pair_quadrupole_theta0.72_maclaurin_2M.md",
+        "quadrupole": ("walk_pair_quadrupole_theta0.75_maclaurin_2M.md",
                        ("bh_walk.cu", "bh_walk_common.cuh")),
         "monopole": ("walk_pair_monopole_theta0.24_maclaurin_2M.md",
                      ("bh_walk.cu", "bh_walk_common.cuh")),
@@ -960,7 +959,7 @@ def main():
     if args.theta is None:
         headline = not (args.monopole or args.vote or args.periodic)
         args.theta = {"batched": 0.5, "learned": 0.8}.get(args.workload,
-                                                          0.72 if headline else 0.7)
+                                                          0.75 if headline else 0.7)
     if args.plain_theta is None:
         args.plain_theta = 0.4 if args.workload == "learned" else 0.24
     if args.impl == "reference":

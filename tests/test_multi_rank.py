@@ -74,7 +74,8 @@ def test_committed_walk_profiles_match_the_sources():
     workloads; any other workload or mode gets no traffic figure."""
     import bench
     w = "maclaurin_e0.9_L2+3"
-    assert bench.captured_traffic(w, 0.72, "quadrupole") is not None
+    assert bench.captured_traffic(w, 0.75, "quadrupole") is not None
+    assert bench.captured_traffic(w, 0.72, "quadrupole") is None
     assert bench.captured_traffic(w, 0.7, "periodic64") is not None
     assert bench.captured_traffic(w, 0.7, "quadrupole") is None
     assert bench.captured_traffic(w, 0.24, "monopole") is not None
