@@ -724,10 +724,9 @@ def batched_arm(args):
                              "value": n / (u_ms * 1e-3), "ms_per_step": u_ms,
                              "speedup": value / (n / (u_ms * 1e-3))}},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
-            # per graph launch: largest-mass pass, k_blocks and its two upper
-            # levels, one top-moment launch per block level above 0, opening
-            # radii, walk
-            "gpu_launches": (s.tree_size()[2] - 3 + 6) * args.steps}
+            # per graph launch: largest-mass pass, k_blocks, k_upper_tree (the
+            # rest of the blocks and the top tree), opening radii, walk
+            "gpu_launches": 5 * args.steps}
     print(json.dumps(line), flush=True)
     for ps in solvers:
         ps.close()
@@ -910,7 +909,7 @@ def learned_arm(args):
                           "speedup": L_["value"] / res["same"]["value"]},
         "accuracy_all_cells": all_cells,
         "clocks": clocks, "e2e": e2e,
-        "gpu_launches": (10 + (maxlev - 3) + 1) * args.steps,
+        "gpu_launches": 9 * args.steps,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -1041,10 +1040,10 @@ def main():
             else "quadrupole" if quad else "monopole")
     traffic = captured_traffic(w.name, args.theta, mode) if not args.vote else None
     _, nn, maxlev = solver.tree_size()
-    # keys, sort, tiling, scan, top nodes, top-node child lists, largest mass,
-    # blocks and their two upper levels, one top-moment launch per block
-    # level (max block level = maxlev - 3), walk
-    launches_per_step = 10 + (maxlev - 3) + 1
+    # keys with the largest mass, sort, tiling, scan, top nodes, top-node
+    # child lists, k_blocks, k_upper_tree (the rest of the blocks and the top
+    # tree), walk
+    launches_per_step = 9
 
     # the plain walk (monopole, per-cell) at the theta of equal accuracy
     plain = None

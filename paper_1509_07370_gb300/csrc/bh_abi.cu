@@ -4,6 +4,7 @@
 // arithmetic lives in the other translation units (bh_build.cu, bh_walk.cu,
 // bh_walk_periodic.cu with bh_ewald.cu, bh_walk_learned*.cu with bh_learn.cu
 // and bh_mlp_tc.cu); this file only holds the small export kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -73,8 +74,6 @@ void release(T *&p) {
 }
 
 void free_blocks(bhg::Tree &t) {
-  release(t.d_level);
-  release(t.d_ijk);
   release(t.d_key[0]);
   release(t.d_key[1]);
   release(t.d_idx[0]);
@@ -86,7 +85,7 @@ void free_blocks(bhg::Tree &t) {
   release(t.d_fid);
   release(t.d_fld);
   release(t.d_pos);
-  release(t.d_child);
+  release(t.d_top);
   t.nb_cap = 0;
 }
 
@@ -106,8 +105,6 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   if (t.nb_cap >= nb) return BH_OK;
   free_blocks(t);
   const size_t n = (size_t)nb;
-  BH_CUDA(bhg::dev_malloc(&t.d_level, n * sizeof(int)));
-  BH_CUDA(bhg::dev_malloc(&t.d_ijk, 3 * n * sizeof(int)));
   BH_CUDA(bhg::dev_malloc(&t.d_key[0], n * sizeof(unsigned long long)));
   BH_CUDA(bhg::dev_malloc(&t.d_key[1], n * sizeof(unsigned long long)));
   BH_CUDA(bhg::dev_malloc(&t.d_idx[0], n * sizeof(int)));
@@ -119,8 +116,7 @@ bh_status ensure_blocks(bh_ctx *ctx, int nb) {
   BH_CUDA(bhg::dev_malloc(&t.d_fid, n * sizeof(int)));
   BH_CUDA(bhg::dev_malloc(&t.d_pos, n * sizeof(int)));
   BH_CUDA(bhg::dev_malloc(&t.d_fld, n * sizeof(int4)));
-  // top nodes: (nb_f - 1)/7 per field, so fewer than nb/4 of them in all
-  BH_CUDA(bhg::dev_malloc(&t.d_child, 2 * n * sizeof(int)));
+  BH_CUDA(bhg::dev_malloc(&t.d_top, (size_t)bhg::top_ints(nb) * sizeof(int)));
   t.nb_cap = nb;
   return BH_OK;
 }
@@ -150,12 +146,33 @@ bh_status use_device(bh_ctx *ctx) {
   return BH_OK;
 }
 
+// The geometry a build takes from the host lives in one device region with a
+// pinned host mirror, so that a build uploads it in one copy:
+// [mmax (nf u64, zeroed) | L, 1/L (nf f64 each) | fstart (nf + 1 int) |
+//  level (nb int) | ijk (3 nb int)], nf = nf_cap, nb = geo_nb_cap.
+struct GeoLayout {
+  size_t L, invL, fstart, level, ijk, end;
+};
+GeoLayout geo_layout(int64_t nf, int64_t nb) {
+  GeoLayout g;
+  g.L = 8 * nf;
+  g.invL = 16 * nf;
+  g.fstart = 24 * nf;
+  g.level = (g.fstart + 4 * (nf + 1) + 15) & ~(size_t)15;
+  g.ijk = g.level + 4 * nb;
+  g.end = g.ijk + 12 * nb;
+  return g;
+}
+
 void free_fields(bhg::Tree &t) {
-  release(t.d_fstart);
-  release(t.d_invL);
-  release(t.d_L);
-  release(t.d_mmax);
+  release(t.d_geo);
+  if (t.h_geo) cudaFreeHost(t.h_geo);
+  t.h_geo = nullptr;
+  t.d_mmax = nullptr;
+  t.d_L = t.d_invL = nullptr;
+  t.d_fstart = t.d_level = t.d_ijk = nullptr;
   t.nf_cap = 0;
+  t.geo_nb_cap = 0;
 }
 
 void drop_graph(bhg::Tree &t) {
@@ -167,15 +184,23 @@ void drop_graph(bhg::Tree &t) {
   t.graph_out = nullptr;
 }
 
-bh_status ensure_fields(bh_ctx *ctx, int nfields) {
+bh_status ensure_fields(bh_ctx *ctx, int nfields, int nb) {
   bhg::Tree &t = ctx->tree;
-  if (t.nf_cap >= nfields) return BH_OK;
+  if (t.nf_cap >= nfields && t.geo_nb_cap >= nb) return BH_OK;
+  const int64_t nf = std::max<int64_t>(nfields, t.nf_cap);
+  const int64_t nbc = std::max<int64_t>(nb, t.geo_nb_cap);
   free_fields(t);
-  BH_CUDA(bhg::dev_malloc(&t.d_fstart, (size_t)(nfields + 1) * sizeof(int)));
-  BH_CUDA(bhg::dev_malloc(&t.d_invL, (size_t)nfields * sizeof(double)));
-  BH_CUDA(bhg::dev_malloc(&t.d_L, (size_t)nfields * sizeof(double)));
-  BH_CUDA(bhg::dev_malloc(&t.d_mmax, (size_t)nfields * sizeof(unsigned long long)));
-  t.nf_cap = nfields;
+  const GeoLayout g = geo_layout(nf, nbc);
+  BH_CUDA(bhg::dev_malloc(&t.d_geo, g.end));
+  BH_CUDA(cudaHostAlloc((void **)&t.h_geo, g.end, cudaHostAllocDefault));
+  t.d_mmax = reinterpret_cast<unsigned long long *>(t.d_geo);
+  t.d_L = reinterpret_cast<double *>(t.d_geo + g.L);
+  t.d_invL = reinterpret_cast<double *>(t.d_geo + g.invL);
+  t.d_fstart = reinterpret_cast<int *>(t.d_geo + g.fstart);
+  t.d_level = reinterpret_cast<int *>(t.d_geo + g.level);
+  t.d_ijk = reinterpret_cast<int *>(t.d_geo + g.ijk);
+  t.nf_cap = (int)nf;
+  t.geo_nb_cap = nbc;
   return BH_OK;
 }
 
@@ -194,23 +219,22 @@ bhg::FieldArgs field_args(bhg::Tree &t) {
 
 // Moments of the current geometry from a density (k_blocks + one launch per
 // level above the blocks); stream-ordered, no host synchronisation.
-bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64) {
+bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64,
+                          bool mmax_ready = false) {
   bhg::Tree &t = ctx->tree;
   cudaStream_t s = ctx->stream;
   // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
   double *q64 = ctx->opt.quadrupole && ctx->opt.precision == BH_PREC_F64 ? t.d_q64 : nullptr;
   bhg::WalkQuad *qrec = (ctx->opt.quadrupole || ctx->opt.learned) ? t.d_qrec : nullptr;
   const bhg::FieldArgs fa = field_args(t);
-  // binary32 mass unit of every field (largest cell mass), then the moments
-  BH_CUDA(cudaMemsetAsync(t.d_mmax, 0, (size_t)t.nfields * sizeof(unsigned long long), s));
-  BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa));
-  BH_CUDA(bhg::launch_blocks(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density,
-                             density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, t.d_lvl,
-                             q64, qrec, t.d_flags));
-  const int64_t n_top = t.n_nodes - (int64_t)bhg::kNodesPerBlock * t.nb;
-  BH_CUDA(bhg::launch_top_tree(s, t.nb, t.max_block_level, n_top, t.d_key[0], t.d_blk, t.d_count,
-                               t.d_prestart, t.n_nodes, t.d_mom, t.d_rec, t.d_aux, q64, qrec,
-                               t.d_flags, fa, t.d_child, t.nb_cap / 4));
+  // binary32 mass unit of every field (largest cell mass), unless the build's
+  // first kernel found it, then the moments
+  if (!mmax_ready) {
+    BH_CUDA(cudaMemsetAsync(t.d_mmax, 0, (size_t)t.nfields * sizeof(unsigned long long), s));
+    BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa));
+  }
+  BH_CUDA(bhg::launch_moments(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density, density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux,
+                              t.d_lvl, q64, qrec, t.d_flags, bhg::top_args(t.d_top, t.nb_cap)));
   return BH_OK;
 }
 
@@ -311,7 +335,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   bh_status st = use_device(ctx);
   if (st != BH_OK) return st;
   if ((st = ensure_blocks(ctx, nb)) != BH_OK) return st;
-  if ((st = ensure_fields(ctx, nfields)) != BH_OK) return st;
+  if ((st = ensure_fields(ctx, nfields, nb)) != BH_OK) return st;
   if ((st = ensure_nodes(ctx, n_nodes)) != BH_OK) return st;
   t.nfields = nfields;
   t.nb = nb;
@@ -321,26 +345,33 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   t.h_fnode = fnode;
   cudaStream_t s = ctx->stream;
   const bhg::FieldArgs fa = field_args(t);
+  const bhg::TopArgs top = bhg::top_args(t.d_top, t.nb_cap);
+  // the host geometry, with zeroed largest masses, into the pinned mirror and
+  // up in one copy (the last build's copy ended at its synchronisation)
+  const GeoLayout g = geo_layout(t.nf_cap, t.geo_nb_cap);
+  if (t.geo_done) BH_CUDA(cudaEventSynchronize(t.geo_done));  // a copy left by a failed build
+  else BH_CUDA(cudaEventCreateWithFlags(&t.geo_done, cudaEventDisableTiming));
+  memset(t.h_geo, 0, (size_t)nfields * sizeof(unsigned long long));
+  memcpy(t.h_geo + g.L, L.data(), (size_t)nfields * sizeof(double));
+  memcpy(t.h_geo + g.invL, invL.data(), (size_t)nfields * sizeof(double));
+  memcpy(t.h_geo + g.fstart, fstart.data(), (size_t)(nfields + 1) * sizeof(int));
+  memcpy(t.h_geo + g.level, level, (size_t)nb * sizeof(int));
+  memcpy(t.h_geo + g.ijk, ijk, 3 * (size_t)nb * sizeof(int));
   ctx->build_timed = false;
   const bool timed = timing_mark(ctx, 0);
   BH_CUDA(cudaMemsetAsync(t.d_flags, 0, 4 * sizeof(unsigned), s));
-  BH_CUDA(cudaMemcpyAsync(t.d_level, level, nb * sizeof(int), cudaMemcpyHostToDevice, s));
-  BH_CUDA(cudaMemcpyAsync(t.d_ijk, ijk, 3 * (size_t)nb * sizeof(int), cudaMemcpyHostToDevice, s));
-  BH_CUDA(cudaMemcpyAsync(t.d_fstart, fstart.data(), (nfields + 1) * sizeof(int),
-                          cudaMemcpyHostToDevice, s));
-  BH_CUDA(cudaMemcpyAsync(t.d_invL, invL.data(), nfields * sizeof(double),
-                          cudaMemcpyHostToDevice, s));
-  BH_CUDA(cudaMemcpyAsync(t.d_L, L.data(), nfields * sizeof(double), cudaMemcpyHostToDevice, s));
-  BH_CUDA(bhg::launch_block_keys(s, nb, t.d_level, t.d_ijk, t.d_key[0], t.d_idx[0], t.d_flags,
-                                 fa));
+  BH_CUDA(cudaMemcpyAsync(t.d_geo, t.h_geo, g.ijk + 12 * (size_t)nb, cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaEventRecord(t.geo_done, s));
+  BH_CUDA(bhg::launch_keys_mass(s, nb, t.d_level, t.d_ijk, t.d_key[0], t.d_idx[0], t.d_flags, fa,
+                                density, density_is_fp64));
   BH_CUDA(bhg::launch_sort_blocks(s, t.d_key, t.d_idx, t.d_flags, fa));
   BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
-                                     t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, t.d_pos));
+                                     t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, top, t.d_pos));
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
   BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
                                 t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig,
-                                max_level, t.d_child, t.nb_cap / 4));
-  if ((st = enqueue_moments(ctx, density, density_is_fp64)) != BH_OK) return st;
+                                max_level, top));
+  if ((st = enqueue_moments(ctx, density, density_is_fp64, true)) != BH_OK) return st;
   ctx->build_timed = timed && timing_mark(ctx, 1);
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
@@ -983,6 +1014,7 @@ void bh_destroy(bh_ctx *ctx) {
   for (cudaEvent_t &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->tree.h_flags) cudaFreeHost(ctx->tree.h_flags);
+  if (ctx->tree.geo_done) cudaEventDestroy(ctx->tree.geo_done);
   delete ctx;
 }
 

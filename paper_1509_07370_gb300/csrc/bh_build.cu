@@ -8,8 +8,9 @@
 // holds more than one block is split into 8, every block is an 8^3 subtree.
 // So:
 //   1. each block gets the Morton key of its lower corner on the level-21
-//      lattice (k_block_keys) and blocks are put in key order (k_sort_blocks,
-//      only if the caller's order is not already sorted);
+//      lattice (k_keys_mass, which also finds each field's largest cell
+//      mass, the binary32 mass unit) and blocks are put in key order
+//      (k_sort_blocks, only if the caller's order is not already sorted);
 //   2. consecutive keys must abut exactly (k_tile_and_count): this checks that
 //      the blocks tile the box, and the trailing zero bits of a block's key
 //      tell how many internal "top" nodes (cubes above the blocks) start at it
@@ -18,17 +19,16 @@
 //      node (k_prestart_scan), from which top nodes get their skip pointers
 //      (k_top_nodes) and their child lists (k_top_children: one binary
 //      search per top node and octant, all in parallel);
-//   4. one CTA per block reduces its 512 cells to 64, 8 and 1 nodes in shared
-//      memory (k_blocks), and one short launch per level reduces the top
-//      nodes, deepest level first (k_top_moments), reading each node's
-//      children from its list.  (Measured: following skip pointers from the
-//      first child instead took 13 us more per build -- a chain of 8
-//      dependent loads per node and level; so did searching the children
-//      one after another in one thread.  Not faster either: a single CTA
-//      walking the levels with barriers, and a cluster of 8 CTAs doing so
-//      with cluster barriers (0.330-0.345 ms per build instead of 0.310):
-//      spread over the whole GPU a level's FP64 work finishes sooner than
-//      the launches it saves.)
+//   4. one CTA per block reduces its 512 cells to its 64 bottom nodes in
+//      shared memory (k_blocks); one more launch (k_upper_tree) does the
+//      rest: the 8 level-one nodes and the root of every block, in full
+//      warps, then the top tree, which it climbs by arrival counts -- the
+//      thread that finishes the last of a node's 8 children computes the
+//      node and climbs on, so no thread waits and no launch per level is
+//      needed.  (Measured before: one launch per top level, each reading its
+//      nodes from child lists, cost 12-18 us a level, mostly launch and
+//      latency for a few hundred nodes; the paper's version has threads
+//      wait on children still marked by a negative mass.)
 // Moments follow Eq. 5 with the children summed in octant order, in FP64 with
 // explicitly rounded operations (no contraction), so results are
 // reproducible bit for bit.
@@ -79,13 +79,15 @@ __device__ __forceinline__ int field_of(int b, int nfields, const int *fstart) {
   return a;
 }
 
-__global__ void k_block_keys(int nb, const int *__restrict__ level, const int *__restrict__ ijk,
-                             unsigned long long *__restrict__ key, int *__restrict__ idx,
-                             unsigned *flags, int nfields, const int *__restrict__ fstart,
-                             int *__restrict__ fid) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
-  const int f = field_of(b, nfields, fstart);
+// Morton key of caller block b (field f) and its field index; notes in
+// flags[1] whether the caller's order differs from the key order (compared
+// with block b+1 of the same field).
+__device__ __forceinline__ void key_of_block(int b, int f, const int *__restrict__ level,
+                                             const int *__restrict__ ijk,
+                                             unsigned long long *__restrict__ key,
+                                             int *__restrict__ idx, unsigned *flags,
+                                             const int *__restrict__ fstart,
+                                             int *__restrict__ fid) {
   fid[b] = f;
   const int lb = level[b];
   const int i = ijk[3 * b], j = ijk[3 * b + 1], k = ijk[3 * b + 2];
@@ -93,8 +95,6 @@ __global__ void k_block_keys(int nb, const int *__restrict__ level, const int *_
   if (valid_block(lb, i, j, k, flags)) kb = block_key(lb, i, j, k);
   key[b] = kb;
   idx[b] = b;
-  // is the caller's order already the key order?  (compare with block b+1
-  // of the same field)
   if (b + 1 < fstart[f + 1]) {
     const int l2 = level[b + 1];
     unsigned long long k2 = ~0ull;
@@ -176,11 +176,13 @@ __global__ void k_tile_and_count(int nb, const unsigned long long *__restrict__ 
                                  const int *__restrict__ ijk, int *__restrict__ count,
                                  int4 *__restrict__ blk, int *__restrict__ orig,
                                  unsigned *flags, const int *__restrict__ fstart,
-                                 const int *__restrict__ fid, int *__restrict__ pos) {
+                                 const int *__restrict__ fid, int *__restrict__ pos,
+                                 int *__restrict__ bparent) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int b = idx[p];
   if (pos) pos[b] = p;  // sorted position of caller block b
+  bparent[p] = -1;      // a field's only block has no parent; k_top_children sets the rest
   const int lb = level[b];
   const unsigned long long kp = key[p];
   const int f = fid[b];
@@ -239,6 +241,19 @@ __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023,
   return __longlong_as_double((long long)(1023 + e) << 52);
 }
 
+// binary64 <-> binary32 conversions of the moment kernels.  (Measured: a
+// bit-level version on the integer pipes -- 64-bit integer arithmetic is
+// several instructions a step -- made k_blocks 7 % and the level-one nodes
+// 75 % slower than the conversion instructions.)
+__device__ __forceinline__ double widen(float f) { return (double)f; }
+// fl32(x 2^k), 2^k a power of two that scales x exactly
+__device__ __forceinline__ float narrow_scaled(double x, int k) {
+  return __double2float_rn(x * pow2d(k));
+}
+__device__ __forceinline__ float narrow(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ double as_f64(float v) { return widen(v); }
+__device__ __forceinline__ double as_f64(double v) { return v; }
+
 // Also records, per block, its field's node range: fld[p] = {first node of
 // the field (its root), one past its last node, first block of the next
 // field, field index}.
@@ -248,7 +263,8 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
                             WalkRec *__restrict__ rec, float2 *__restrict__ aux,
                             uint8_t *__restrict__ lvl, unsigned *flags, int nfields,
                             const int *__restrict__ fstart, const int *__restrict__ fid,
-                            const int *__restrict__ orig, int4 *__restrict__ fld) {
+                            const int *__restrict__ orig, int4 *__restrict__ fld,
+                            TopArgs top) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nb) return;
   const int f = fid[orig[p]];
@@ -270,13 +286,20 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
       if (key[m] < lim) a = m + 1; else e = m;
     }
     const int64_t skip = a < fend ? (int64_t)prestart[a] : node_end;
-    if (id < 0 || id >= n_nodes || skip > n_nodes) {
+    const int64_t slot = id - (int64_t)kNodesPerBlock * p;
+    if (id < 0 || id >= n_nodes || skip > n_nodes || slot < 0 || slot >= top.slots) {
       atomicOr(flags, kErrIndex);
       continue;
     }
     rec[id].skip = (unsigned)skip;
     aux[id] = make_float2(pow2f(-k), 0.0f);
     lvl[id] = (uint8_t)k;
+    const int sh = kKeyLevels - k;
+    top.slot[2 * slot] = make_int4((int)id, (int)skip, (int)(compact3(kp) >> sh),
+                                   (int)(compact3(kp >> 1) >> sh));
+    top.slot[2 * slot + 1] = make_int4((int)(compact3(kp >> 2) >> sh), k, f, p);
+    top.parent[slot] = -1;  // a field's root; k_top_children sets the others
+    top.arrive[slot] = 0u;
   }
 }
 
@@ -288,13 +311,14 @@ __global__ void k_top_nodes(int nb, const unsigned long long *__restrict__ key,
 // found by one binary search, and the child is q's top node of level k + 1
 // or, if q is a block of level k + 1, q's root.  One thread per (top node,
 // octant), all independent: the moment pass then reads its children
-// directly instead of chasing skip pointers one after another.
+// directly instead of chasing skip pointers one after another.  Also records
+// each child's parent slot (TopArgs::parent, TopArgs::bparent), by which the
+// moment pass climbs the top tree.
 __global__ void k_top_children(int nb, const unsigned long long *__restrict__ key,
                                const int4 *__restrict__ blk, const int *__restrict__ count,
                                const int *__restrict__ prestart, int64_t n_nodes,
                                const int *__restrict__ fstart, const int *__restrict__ fid,
-                               const int *__restrict__ orig, int *__restrict__ child,
-                               int64_t child_slots, unsigned *flags) {
+                               const int *__restrict__ orig, TopArgs top, unsigned *flags) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)nb * 8) return;
   const int p = (int)(tid >> 3), o = (int)(tid & 7);
@@ -304,7 +328,7 @@ __global__ void k_top_children(int nb, const unsigned long long *__restrict__ ke
   const int lb = blk[p].x, k = lb - cnt + r;
   const int fend = fstart[fid[orig[p]] + 1];
   const int64_t slot = (int64_t)prestart[p] - (int64_t)kNodesPerBlock * p + r;
-  if (k < 0 || k >= kKeyLevels || slot < 0 || slot >= child_slots) {
+  if (k < 0 || k >= kKeyLevels || slot < 0 || slot >= top.slots) {
     atomicOr(flags, kErrIndex);
     return;
   }
@@ -330,7 +354,17 @@ __global__ void k_top_children(int nb, const unsigned long long *__restrict__ ke
     atomicOr(flags, kErrIndex);
     return;
   }
-  child[8 * slot + o] = (int)idx;
+  top.child[8 * slot + o] = (int)idx;
+  if (k + 1 < lq) {  // a top node: its slot
+    const int64_t cs = idx - (int64_t)kNodesPerBlock * q;
+    if (cs < 0 || cs >= top.slots) {
+      atomicOr(flags, kErrIndex);
+      return;
+    }
+    top.parent[cs] = (int)slot;
+  } else {  // block q's root
+    top.bparent[q] = (int)slot;
+  }
 }
 
 // Moments of one internal node from its 8 children (Eq. 5), children in
@@ -345,6 +379,15 @@ __device__ __forceinline__ void accumulate(double &M, double &Sx, double &Sy, do
   Sx = __dadd_rn(Sx, __dmul_rn(m, x));
   Sy = __dadd_rn(Sy, __dmul_rn(m, y));
   Sz = __dadd_rn(Sz, __dmul_rn(m, z));
+}
+// The first term of the sums: 0 + m = m and 0 + fl(m x) = fl(m x) (masses and
+// box coordinates are >= 0), so the sums start from it.
+__device__ __forceinline__ void accumulate_first(double &M, double &Sx, double &Sy, double &Sz,
+                                                 double m, double x, double y, double z) {
+  M = m;
+  Sx = __dmul_rn(m, x);
+  Sy = __dmul_rn(m, y);
+  Sz = __dmul_rn(m, z);
 }
 __device__ __forceinline__ Moment finish(double M, double Sx, double Sy, double Sz, double cx,
                                          double cy, double cz) {
@@ -374,33 +417,35 @@ __device__ __forceinline__ float centre_coord_f(int i, int level) {
   return __fmul_rn((float)(2 * i + 1), pow2f(-(level + 1)));
 }
 __device__ __forceinline__ double centre_coord(int i, int level) {
-  return (double)centre_coord_f(i, level);
+  return widen(centre_coord_f(i, level));
 }
 
-__device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m,
+// ku: the exponent of the field's inverse binary32 mass unit (the record's
+// mass is fl(m 2^ku)).
+__device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double m, int ku,
                                             int64_t skip) {
   WalkRec w;
-  w.px = __double2float_rn(x);
-  w.py = __double2float_rn(y);
-  w.pz = __double2float_rn(z);
-  w.m = __double2float_rn(m);
+  w.px = narrow(x);
+  w.py = narrow(y);
+  w.pz = narrow(z);
+  w.m = narrow_scaled(m, ku);
   w.s2 = 0.0f;
   w.skip = (unsigned)skip;
   w.pad[0] = w.pad[1] = 0.0f;
   return w;
 }
 
-// inv_unit = 2^-e of the field's binary32 mass unit (the record's mass).
+// ku = -e for the field's binary32 mass unit 2^e (the record's mass).
 // inv_theta > 0: also the squared opening radius s2 = fl(fl(l fl(1/theta)) +
 // delta)^2 from the same binary32 l and delta as k_prepare_s2 (identical).
 // Returns the record's binary32 mass (in the field's unit).
 __device__ __forceinline__ float store_internal(int64_t id, int64_t skip, int level,
                                                 const Moment &r, double4_32a *mom, WalkRec *rec,
-                                                float2 *aux, uint8_t *lvl, double inv_unit,
+                                                float2 *aux, uint8_t *lvl, int ku,
                                                 float inv_theta) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
-  WalkRec w = make_rec(r.x, r.y, r.z, r.m * inv_unit, skip);
-  const float l = pow2f(-level), delta = __double2float_rn(r.delta);
+  WalkRec w = make_rec(r.x, r.y, r.z, r.m, ku, skip);
+  const float l = pow2f(-level), delta = narrow(r.delta);
   if (inv_theta > 0.0f) {
     const float s = __fadd_rn(__fmul_rn(l, inv_theta), delta);
     w.s2 = __fmul_rn(s, s);
@@ -434,7 +479,7 @@ __device__ __forceinline__ void add_shifted(double Q[6], const double *Qc, doubl
 // then rounded (top nodes), or inside a block from binary32 offsets (below).
 __device__ __forceinline__ void add_shifted_f(float Q[6], const float *Qc, float fm, double sx,
                                               double sy, double sz) {
-  const float x = __double2float_rn(sx), y = __double2float_rn(sy), z = __double2float_rn(sz);
+  const float x = narrow(sx), y = narrow(sy), z = narrow(sz);
   const float s2 = x * x + y * y + z * z;
   Q[0] += fm * (3.0f * x * x - s2);
   Q[1] += fm * (3.0f * y * y - s2);
@@ -535,7 +580,8 @@ __global__ void __launch_bounds__(kBlockThreads)
   const int lc = lb + 3;
   const int field = fid[orig[p]];
   const double L = Lf[field];                  // box side of this block's field
-  const double inv_unit = pow2i(-mass_exponent(mmax[field]));  // binary32 mass unit
+  const int ku = -mass_exponent(mmax[field]);  // binary32 mass unit 2^-ku
+  const double inv_unit = pow2i(ku);
   const double hs = pow2d(-lc);               // cell side, box units
   const double h = __dmul_rn(L, hs);          // cell side, physical
   const double vol = __dmul_rn(__dmul_rn(h, h), h);
@@ -544,15 +590,15 @@ __global__ void __launch_bounds__(kBlockThreads)
   for (int i = t; i < kCellsPerBlock; i += kBlockThreads) {
     const T rv = rho[i];
     if (!(rv >= T(0)) || isinf(rv)) bad = true;  // checked in the input's precision
-    const double r = (double)rv;
+    const double r = as_f64(rv);
     const int cx = i & 7, cy = (i >> 3) & 7, cz = i >> 6;
     const int m = (int)(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
     const float fx = centre_coord_f(8 * B.y + cx, lc);
     const float fy = centre_coord_f(8 * B.z + cy, lc);
     const float fz = centre_coord_f(8 * B.w + cz, lc);
-    const double ux = fx, uy = fy, uz = fz;
+    const double ux = widen(fx), uy = widen(fy), uz = widen(fz);
     const double mass = __dmul_rn(r, vol);
-    const float mu = __double2float_rn(mass * inv_unit);
+    const float mu = narrow_scaled(mass, ku);
     cm[m] = mass;
     cmu[m] = mu;
     cxs[m] = ux;
@@ -574,19 +620,23 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
   if (bad) atomicOr(flags, kErrDensity);
   __syncthreads();
-  if (t < 64) {  // nodes at level lb+2: q = 8p + r, children = cells 8q..8q+7
-    const int q = t;
+  // nodes at level lb+2: q = 8p + r, children = cells 8q..8q+7; warps 0-1
+  // on even CTAs, 2-3 on odd ones, so that this FP64 work of the CTAs on an
+  // SM is spread over its four schedulers
+  if ((t >> 6) == (p & 1)) {
+    const int q = t & 63;
     const int qx = (int)compact3(q), qy = (int)compact3(q >> 1), qz = (int)compact3(q >> 2);
     const double cx = centre_coord(4 * B.y + qx, lb + 2);
     const double cy = centre_coord(4 * B.z + qy, lb + 2);
     const double cz = centre_coord(4 * B.w + qz, lb + 2);
-    double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    double M, Sx, Sy, Sz;
+    accumulate_first(M, Sx, Sy, Sz, cm[8 * q], cxs[8 * q], cys[8 * q], czs[8 * q]);
 #pragma unroll
-    for (int o = 0; o < 8; ++o)
+    for (int o = 1; o < 8; ++o)
       accumulate(M, Sx, Sy, Sz, cm[8 * q + o], cxs[8 * q + o], cys[8 * q + o], czs[8 * q + o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, ku, inv_theta);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -596,8 +646,7 @@ __global__ void __launch_bounds__(kBlockThreads)
       store_quad(id, Q, q64, qrec, inv_unit);
     } else if (quad32) {
       // children: cells at c +- h/2 (h = 2^-(lb+3)) with o = 0
-      const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
-                  oz = __double2float_rn(r.oz);
+      const float ox = narrow(r.ox), oy = narrow(r.oy), oz = narrow(r.oz);
       const float hc = pow2f(-(lb + 4));
       float Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -610,70 +659,66 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
 }
 
-// The 8 nodes at level lb+1 of every block (STAGE 1) or every block's root
-// (STAGE 0), one node per thread over all blocks, so that the FP64 work runs
-// in full warps (in one CTA per block these levels kept 8 and 1 lanes of a
-// warp busy at the cost of a whole warp).  Their children -- written by
-// k_blocks (stage 1) or by stage 1 (stage 0) -- are read back from the node
-// arrays; the arithmetic is that of k_blocks (Eq. 5 in octant order; the
-// binary32 quadrupole shift from the children's binary32 centre-of-mass
-// offsets), so the results are the same bit for bit.
-template <int STAGE>
-__global__ void __launch_bounds__(256)
-    k_block_upper(int nb, const int4 *__restrict__ blk, const int *__restrict__ orig,
-                  const int *__restrict__ count, const int *__restrict__ prestart,
-                  const int *__restrict__ fid, const unsigned long long *__restrict__ mmax,
-                  float inv_theta, int64_t n_nodes, double4_32a *__restrict__ mom,
-                  WalkRec *__restrict__ rec, float2 *__restrict__ aux, uint8_t *__restrict__ lvl,
-                  double *__restrict__ q64, WalkQuad *__restrict__ qrec) {
-  constexpr int kPer = STAGE ? 8 : 1;  // nodes of this level per block
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)nb * kPer) return;
-  const int p = (int)(i / kPer), c = (int)(i % kPer);
-  const int4 B = blk[p];
-  const int lb = B.x;
-  if (lb < 0 || lb > kMaxBlockLevel) return;  // flagged by k_block_keys
-  const int64_t root = (int64_t)prestart[p] + count[p];
-  if (root < 0 || root + kNodesPerBlock > n_nodes) return;  // flagged by k_blocks
-  const double inv_unit = pow2i(-mass_exponent(mmax[fid[orig[p]]]));
-  const int lev = STAGE ? lb + 1 : lb;
-  const int ix = STAGE ? 2 * B.y + (c & 1) : B.y;
-  const int iy = STAGE ? 2 * B.z + ((c >> 1) & 1) : B.z;
-  const int iz = STAGE ? 2 * B.w + ((c >> 2) & 1) : B.w;
-  const int64_t id = STAGE ? root + 1 + 73 * c : root;
-  const int64_t skip = STAGE ? id + 73 : root + kNodesPerBlock;
-  const int64_t first = id + 1, stride = STAGE ? 9 : 73;  // child o at first + stride o
+// Loads of node data written by other CTAs of the same launch: through L2
+// (ld.global.cg), after the arrival count has said that the writers are done.
+__device__ __forceinline__ double4_32a ld_mom_cg(const double4_32a *p) {
+  const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+  return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ WalkQuad ld_quad_cg(const WalkQuad *p) {
+  const float4 a = __ldcg(reinterpret_cast<const float4 *>(p));
+  const float2 b = __ldcg(reinterpret_cast<const float2 *>(p) + 2);
+  WalkQuad w;
+  w.hxx = a.x;
+  w.hyy = a.y;
+  w.hzz = a.z;
+  w.qxy = a.w;
+  w.qxz = b.x;
+  w.qyz = b.y;
+  w.pad[0] = w.pad[1] = 0.0f;
+  return w;
+}
+
+// A level-one node of a block (level lev = lb + 1) from its 8 children, the
+// bottom nodes at first + 9 o, one thread per node.  Eq. 5 in octant order;
+// the binary32 quadrupole shift from the children's binary32 centre-of-mass
+// offsets, as k_blocks forms it.
+__device__ __forceinline__ void level_one_node(int lev, int ix, int iy, int iz, int64_t id,
+                                               int64_t skip, int64_t first, int ku,
+                                               double inv_unit, float inv_theta,
+                                               double4_32a *mom, WalkRec *rec, float2 *aux,
+                                               uint8_t *lvl, double *q64, WalkQuad *qrec) {
+  constexpr int64_t stride = 9;
   const double cx = centre_coord(ix, lev), cy = centre_coord(iy, lev), cz = centre_coord(iz, lev);
-  double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+  double4_32a ch[8];
 #pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    const double4_32a ch = mom[first + stride * o];
-    accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
-  }
+  for (int o = 0; o < 8; ++o) ch[o] = mom[first + stride * o];
+  double M, Sx, Sy, Sz;
+  accumulate_first(M, Sx, Sy, Sz, ch[0].w, ch[0].x, ch[0].y, ch[0].z);
+#pragma unroll
+  for (int o = 1; o < 8; ++o) accumulate(M, Sx, Sy, Sz, ch[o].w, ch[o].x, ch[o].y, ch[o].z);
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-  store_internal(id, skip, lev, r, mom, rec, aux, lvl, inv_unit, inv_theta);
+  store_internal(id, skip, lev, r, mom, rec, aux, lvl, ku, inv_theta);
   if (q64) {
     double Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int64_t k = first + stride * o;
-      const double4_32a ch = mom[k];
-      add_shifted(Q, q64 + 6 * k, ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
+      add_shifted(Q, q64 + 6 * k, ch[o].w, ch[o].x - r.x, ch[o].y - r.y, ch[o].z - r.z);
     }
     store_quad(id, Q, q64, qrec, inv_unit);
   } else if (qrec) {
-    const float ox = __double2float_rn(r.ox), oy = __double2float_rn(r.oy),
-                oz = __double2float_rn(r.oz);
+    const float ox = narrow(r.ox), oy = narrow(r.oy), oz = narrow(r.oz);
     const float hc = pow2f(-(lev + 2));  // child centre - centre: +-2^-(lev+2)
     float Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int64_t k = first + stride * o;
-      const double4_32a ch = mom[k];
-      // the child's binary32 offset R - c from its own centre, as k_blocks formed it
-      const float gx = __double2float_rn(__dsub_rn(ch.x, centre_coord(2 * ix + (o & 1), lev + 1)));
-      const float gy =
-          __double2float_rn(__dsub_rn(ch.y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
-      const float gz =
-          __double2float_rn(__dsub_rn(ch.z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
+      // the child's binary32 offset R - c from its own centre, as it was formed
+      const float gx = narrow(__dsub_rn(ch[o].x, centre_coord(2 * ix + (o & 1), lev + 1)));
+      const float gy = narrow(__dsub_rn(ch[o].y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
+      const float gz = narrow(__dsub_rn(ch[o].z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
       float Qc[6];
       load_quad_f(qrec[k], Qc);
       const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
@@ -684,103 +729,224 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// The top node of sorted block p at `level` (the block starts cnt = count[p]
-// top nodes, levels lb - cnt .. lb - 1): its children are top nodes one level
-// down or block roots, read from its child list (k_top_children).
-__device__ __forceinline__ void top_moment(int p, int level, const unsigned long long *key,
-                                           const int4 *blk, const int *count,
-                                           const int *prestart, int64_t n_nodes,
-                                           double4_32a *mom, WalkRec *rec, float2 *aux,
-                                           double *q64, WalkQuad *qrec, unsigned *flags,
-                                           const int4 *fld, const unsigned long long *mmax,
-                                           float inv_theta, const int *__restrict__ child_list,
-                                           int64_t child_slots) {
-  const int cnt = count[p];
-  const int lb = blk[p].x;
-  const int j0 = lb - cnt;
-  const int64_t id = (int64_t)prestart[p] + (level - j0);
-  const unsigned long long kp = key[p];
-  const int sh = kKeyLevels - level;
-  const double cx = centre_coord((int)(compact3(kp) >> sh), level);
-  const double cy = centre_coord((int)(compact3(kp >> 1) >> sh), level);
-  const double cz = centre_coord((int)(compact3(kp >> 2) >> sh), level);
-  double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-  const int64_t slot = id - (int64_t)kNodesPerBlock * p;
-  if (slot < 0 || slot >= child_slots) {
-    atomicOr(flags, kErrIndex);
+// One node computed by a group of 8 lanes of a warp (lanes gbase..gbase+7,
+// mask gmask); lane o of the group brings child o (node index `child`).  A
+// lone thread spends about 90 clocks on each dependent FP64 instruction here,
+// so the node's FP64 work is spread over the group: the four sums of Eq. 5
+// on lanes k = o & 3 (k = 0: M, as fl(m 1) = m; 1-3: the x, y, z moments),
+// each in octant order; the divisions by M on lanes 1-3; the FP64
+// differences of the quadrupole shifts on all eight.  The binary32
+// quadrupole sum then runs on every lane from the shuffled terms in octant
+// order.  Every value is the one the one-thread form computes, bit for bit.
+// ROOT: a block's root (children: its level-one nodes; shift from their
+// binary32 offsets, as inside a block; ix, iy, iz its cube); else a top
+// node (children from its list; shift = the FP64 difference of the centres
+// of mass, rounded).  CG: read the children through L2.
+template <bool ROOT, bool CG>
+__device__ __forceinline__ void group_node(unsigned gmask, int gbase, int o, int lev, int ix,
+                                           int iy, int iz, double cx, double cy, double cz,
+                                           int64_t id, int64_t skip, int64_t child, int ku,
+                                           double inv_unit, float inv_theta, double4_32a *mom,
+                                           WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
+                                           WalkQuad *qrec) {
+  const double4_32a c = CG ? ld_mom_cg(mom + child) : mom[child];
+  WalkQuad qc = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, {0.0f, 0.0f}};
+  float fm = 0.0f;
+  if (qrec && !q64) {  // issued with the moments, used after the FP64 part
+    qc = CG ? ld_quad_cg(qrec + child) : qrec[child];
+    fm = CG ? __ldcg(&rec[child].m) : rec[child].m;
+  }
+  const int k = o & 3;
+  double S = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const double mj = __shfl_sync(gmask, c.w, gbase + j);
+    const double xj = __shfl_sync(gmask, c.x, gbase + j);
+    const double yj = __shfl_sync(gmask, c.y, gbase + j);
+    const double zj = __shfl_sync(gmask, c.z, gbase + j);
+    const double t = __dmul_rn(mj, k == 0 ? 1.0 : (k == 1 ? xj : (k == 2 ? yj : zj)));
+    S = j == 0 ? t : __dadd_rn(S, t);
+  }
+  const double M = __shfl_sync(gmask, S, gbase);
+  const double cc = k == 1 ? cx : (k == 2 ? cy : cz);
+  const double R = M > 0.0 ? __ddiv_rn(S, M) : cc;  // a massless node sits at its centre
+  const double off = __dsub_rn(R, cc);
+  const double sq = __dmul_rn(off, off);
+  Moment r;
+  r.m = M;
+  r.x = __shfl_sync(gmask, R, gbase + 1);
+  r.y = __shfl_sync(gmask, R, gbase + 2);
+  r.z = __shfl_sync(gmask, R, gbase + 3);
+  r.ox = __shfl_sync(gmask, off, gbase + 1);
+  r.oy = __shfl_sync(gmask, off, gbase + 2);
+  r.oz = __shfl_sync(gmask, off, gbase + 3);
+  r.delta = __dsqrt_rn(__dadd_rn(__dadd_rn(__shfl_sync(gmask, sq, gbase + 1),
+                                           __shfl_sync(gmask, sq, gbase + 2)),
+                                 __shfl_sync(gmask, sq, gbase + 3)));
+  if (o == 0) store_internal(id, skip, lev, r, mom, rec, aux, lvl, ku, inv_theta);
+  if (q64) {  // FP64 quadrupoles (the FP64 walk): on lane 0, as the one-thread form
+    int64_t kids[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) kids[j] = __shfl_sync(gmask, child, gbase + j);
+    if (o == 0) {
+      double Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int j = 0; j < 8; ++j) {
+        const int64_t kj = kids[j];
+        const double4_32a cj = CG ? ld_mom_cg(mom + kj) : mom[kj];
+        double Qc[6];
+        for (int a = 0; a < 6; ++a) Qc[a] = CG ? __ldcg(q64 + 6 * kj + a) : q64[6 * kj + a];
+        add_shifted(Q, Qc, cj.w, cj.x - r.x, cj.y - r.y, cj.z - r.z);
+      }
+      store_quad(id, Q, q64, qrec, inv_unit);
+    }
     return;
   }
-  int64_t child[8];  // from the child list, kept for the quadrupoles
-  for (int o = 0; o < 8; ++o) {
-    const int64_t c = child_list[8 * slot + o];
-    if (c <= 0 || c >= n_nodes) {
-      atomicOr(flags, kErrIndex);
-      return;
-    }
-    child[o] = c;
+  if (!qrec) return;
+  float sx, sy, sz;  // this lane's child: its shift from the node's centre of mass
+  if (ROOT) {
+    const float hc = pow2f(-(lev + 2));
+    const float gx = narrow(__dsub_rn(c.x, centre_coord(2 * ix + (o & 1), lev + 1)));
+    const float gy = narrow(__dsub_rn(c.y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
+    const float gz = narrow(__dsub_rn(c.z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
+    const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
+    sx = __fsub_rn(__fadd_rn(dx, gx), narrow(r.ox));
+    sy = __fsub_rn(__fadd_rn(dy, gy), narrow(r.oy));
+    sz = __fsub_rn(__fadd_rn(dz, gz), narrow(r.oz));
+  } else {
+    sx = narrow(c.x - r.x);
+    sy = narrow(c.y - r.y);
+    sz = narrow(c.z - r.z);
   }
-  for (int o = 0; o < 8; ++o) {
-    const double4_32a ch = mom[child[o]];
-    accumulate(M, Sx, Sy, Sz, ch.w, ch.x, ch.y, ch.z);
+  float Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const WalkQuad qj = {__shfl_sync(gmask, qc.hxx, gbase + j), __shfl_sync(gmask, qc.hyy, gbase + j),
+                         __shfl_sync(gmask, qc.hzz, gbase + j), __shfl_sync(gmask, qc.qxy, gbase + j),
+                         __shfl_sync(gmask, qc.qxz, gbase + j), __shfl_sync(gmask, qc.qyz, gbase + j),
+                         {0.0f, 0.0f}};
+    float Qc[6];
+    load_quad_f(qj, Qc);
+    add_shifted_ff(Q, Qc, __shfl_sync(gmask, fm, gbase + j), __shfl_sync(gmask, sx, gbase + j),
+                   __shfl_sync(gmask, sy, gbase + j), __shfl_sync(gmask, sz, gbase + j));
   }
-  const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-  const int64_t skip = rec[id].skip;
-  const double inv_unit = pow2i(-mass_exponent(mmax[fld[p].w]));
-  store_internal(id, skip, level, r, mom, rec, aux, nullptr, inv_unit, inv_theta);
-  if (q64) {
-    double Q[6] = {0, 0, 0, 0, 0, 0};
-    for (int o = 0; o < 8; ++o) {
-      const double4_32a ch = mom[child[o]];
-      add_shifted(Q, q64 + 6 * child[o], ch.w, ch.x - r.x, ch.y - r.y, ch.z - r.z);
-    }
-    store_quad(id, Q, q64, qrec, inv_unit);
-  } else if (qrec) {
-    float Q[6] = {0, 0, 0, 0, 0, 0};
-    for (int o = 0; o < 8; ++o) {
-      const double4_32a ch = mom[child[o]];
-      float Qc[6];
-      load_quad_f(qrec[child[o]], Qc);
-      add_shifted_f(Q, Qc, __double2float_rn(ch.w * inv_unit), ch.x - r.x, ch.y - r.y,
-                    ch.z - r.z);
-    }
-    store_quad_f(id, Q, qrec);
-  }
+  if (o == 0) store_quad_f(id, Q, qrec);
 }
 
-// One launch per level (any number of top nodes).
-__global__ void k_top_moments(int nb, int level, const unsigned long long *__restrict__ key,
-                              const int4 *__restrict__ blk, const int *__restrict__ count,
-                              const int *__restrict__ prestart, int64_t n_nodes,
-                              double4_32a *__restrict__ mom, WalkRec *__restrict__ rec,
-                              float2 *__restrict__ aux, double *__restrict__ q64,
-                              WalkQuad *__restrict__ qrec, unsigned *flags,
-                              const int4 *__restrict__ fld,
-                              const unsigned long long *__restrict__ mmax, float inv_theta,
-                              const int *__restrict__ child_list, int64_t child_slots) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// The top node whose slot holds {a, b} (made by k_top_nodes: node, skip, cube,
+// level, field) and whose child o is c, by a group of 8 lanes; its
+// children -- top nodes one level down or block roots -- were written by
+// other CTAs and are read through L2.  ku: the field's mass-unit exponent.
+// False when the slot is inconsistent (a failed geometry).
+__device__ __forceinline__ bool top_node(unsigned gmask, int gbase, int o, int4 a, int4 b,
+                                         int64_t c, int ku, int nb, int nfields,
+                                         int64_t n_nodes, double4_32a *mom, WalkRec *rec,
+                                         float2 *aux, double *q64, WalkQuad *qrec,
+                                         float inv_theta) {
+  const int level = b.y;
+  if (a.x < 0 || a.x >= n_nodes || level < 0 || level >= kKeyLevels || b.z < 0 ||
+      b.z >= nfields || b.w < 0 || b.w >= nb)
+    return false;
+  if (__any_sync(gmask, c <= 0 || c >= n_nodes)) return false;
+  group_node<false, true>(gmask, gbase, o, level, 0, 0, 0, centre_coord(a.z, level),
+                          centre_coord(a.w, level), centre_coord(b.x, level), a.x, a.y, c, ku,
+                          pow2i(ku), inv_theta, mom, rec, aux, nullptr, q64, qrec);
+  return true;
+}
+
+// Everything above the 64 bottom nodes of the blocks, in one launch.  A CTA
+// takes kUpperBlocks sorted blocks: (1) their 8 level-one nodes, one per
+// thread, so that the FP64 work runs in full warps; (2) after a CTA barrier,
+// their roots, one per group of 8 lanes; (3) the top tree, climbed without
+// waiting: a group that has finished a node adds one to its parent's
+// arrival count, and the group that brings it to 8 computes the parent (the
+// other seven are done) and climbs on; the rest stop.  No thread ever waits
+// for another, the count is put back to 0 by the group that used it, and
+// the results do not depend on which group computes a node: every node is
+// the same function of its children in octant order, as in the paper's
+// bottom-up pass (Sec. 3.2.3, there with threads that wait on their
+// children).
+constexpr int kUpperBlocks = 16;
+__global__ void __launch_bounds__(8 * kUpperBlocks)
+    k_upper_tree(int nb, int nfields, const int4 *__restrict__ blk, const int *__restrict__ orig,
+                 const int *__restrict__ count, const int *__restrict__ prestart,
+                 const int *__restrict__ fid, const unsigned long long *__restrict__ mmax,
+                 float inv_theta, int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
+                 uint8_t *lvl, double *q64, WalkQuad *qrec, unsigned *flags, TopArgs top) {
+  const int p0 = blockIdx.x * kUpperBlocks;
+  const int t = threadIdx.x;
+  {  // (1) level-one nodes: block p0 + t/8, octant t%8
+    const int p = p0 + t / 8, c = t % 8;
+    if (p < nb) {
+      const int4 B = blk[p];
+      const int lb = B.x;
+      const int64_t root = (int64_t)prestart[p] + count[p];
+      if (lb >= 0 && lb <= kMaxBlockLevel && root >= 0 && root + kNodesPerBlock <= n_nodes) {
+        const int ku = -mass_exponent(mmax[fid[orig[p]]]);
+        const int64_t id = root + 1 + 73 * c;
+        level_one_node(lb + 1, 2 * B.y + (c & 1), 2 * B.z + ((c >> 1) & 1),
+                       2 * B.w + ((c >> 2) & 1), id, id + 73, id + 1, ku, pow2i(ku), inv_theta,
+                       mom, rec, aux, lvl, q64, qrec);
+      }
+    }
+  }
+  __syncthreads();
+  // (2) roots: block p0 + t/8 by the group of lanes t & ~7
+  const int o = t & 7, gbase = t & 24;
+  const unsigned gmask = 0xFFu << gbase;
+  const int p = p0 + t / 8;
   if (p >= nb) return;
-  const int cnt = count[p];
-  const int lb = blk[p].x;
-  if (cnt == 0 || level < lb - cnt || level >= lb) return;
-  top_moment(p, level, key, blk, count, prestart, n_nodes, mom, rec, aux, q64, qrec, flags, fld,
-             mmax, inv_theta, child_list, child_slots);
+  const int4 B = blk[p];
+  const int lb = B.x;
+  const int64_t root = (int64_t)prestart[p] + count[p];
+  if (lb < 0 || lb > kMaxBlockLevel || root < 0 || root + kNodesPerBlock > n_nodes) return;
+  const int ku = -mass_exponent(mmax[fid[orig[p]]]);
+  group_node<true, false>(gmask, gbase, o, lb, B.y, B.z, B.w, centre_coord(B.y, lb),
+                          centre_coord(B.z, lb), centre_coord(B.w, lb), root,
+                          root + kNodesPerBlock, root + 1 + 73 * o, ku, pow2i(ku), inv_theta, mom,
+                          rec, aux, lvl, q64, qrec);
+  // (3) climb: the parent top node of this root, then its parents
+  int s = top.bparent[p];
+  while (s >= 0) {
+    if (s >= top.slots) {  // a failed geometry
+      if (o == 0) atomicOr(flags, kErrIndex);
+      return;
+    }
+    // what the parent's computation needs from earlier launches, read before
+    // the arrival so that only its children's moments remain after it
+    const int4 a = top.slot[2 * (int64_t)s], b = top.slot[2 * (int64_t)s + 1];
+    const int64_t c = top.child[8 * (int64_t)s + o];
+    const int up = top.parent[s];
+    const int kuf = b.z >= 0 && b.z < nfields ? -mass_exponent(mmax[b.z]) : 0;
+    unsigned before = 0u;
+    if (o == 0) {
+      __threadfence();  // this node's moments (lane 0 wrote them) before the arrival
+      before = atomicAdd(top.arrive + s, 1u);
+    }
+    before = __shfl_sync(gmask, before, gbase);
+    if (before != 7u) {
+      if (before > 7u && o == 0) atomicOr(flags, kErrIndex);
+      return;
+    }
+    __threadfence();  // the other children's moments after their arrivals
+    if (o == 0) top.arrive[s] = 0u;
+    if (!top_node(gmask, gbase, o, a, b, c, kuf, nb, nfields, n_nodes, mom, rec, aux, q64, qrec,
+                  inv_theta)) {
+      if (o == 0) atomicOr(flags, kErrIndex);
+      return;
+    }
+    s = up;
+  }
 }
 
 // Largest cell mass m = rho h^3 of each field (FP64, rounded as in k_blocks),
-// as an atomic max on its bits (a non-negative double orders like its bits).
-// One CTA per caller block; invalid levels and densities are skipped here
-// and reported by the other kernels.
+// as an atomic max on its bits (a non-negative double orders like its bits):
+// the part of caller block b (level lb, field f), by all threads of a CTA.
+// Invalid densities are skipped here and reported by k_blocks.
 template <typename T>
-__global__ void __launch_bounds__(kBlockThreads)
-    k_mass_max(int nb, const int *__restrict__ level, const T *__restrict__ density,
-               const double *__restrict__ Lf, const int *__restrict__ fid,
-               unsigned long long *__restrict__ mmax) {
-  const int b = blockIdx.x;
-  const int lb = level[b];
-  if (lb < 0 || lb > kMaxBlockLevel) return;
-  const int field = fid[b];
-  const double h = __dmul_rn(Lf[field], pow2d(-(lb + 3)));
-  const double vol = __dmul_rn(__dmul_rn(h, h), h);
+__device__ __forceinline__ void block_mass_max(int b, int field, int lb,
+                                               const T *__restrict__ density,
+                                               const double *__restrict__ Lf,
+                                               unsigned long long *__restrict__ mmax) {
   const T *rho = density + (int64_t)b * kCellsPerBlock;
   T mx = 0;  // the largest density, in its own precision (max is exact)
   for (int i = threadIdx.x; i < kCellsPerBlock; i += kBlockThreads) {
@@ -797,22 +963,60 @@ __global__ void __launch_bounds__(kBlockThreads)
   if (threadIdx.x == 0) {  // one atomic per block, and only when it can raise the max
     for (int w = 1; w < kBlockThreads / 32; ++w) mx = warp_max[w] > mx ? warp_max[w] : mx;
     if (mx > T(0)) {
+      const double h = __dmul_rn(Lf[field], pow2d(-(lb + 3)));
+      const double vol = __dmul_rn(__dmul_rn(h, h), h);
       const unsigned long long bits =
-          (unsigned long long)__double_as_longlong(__dmul_rn((double)mx, vol));
+          (unsigned long long)__double_as_longlong(__dmul_rn(as_f64(mx), vol));
       if (bits > *(volatile unsigned long long *)(mmax + field)) atomicMax(mmax + field, bits);
     }
   }
+}
+
+// The largest cell mass alone (a new density on the same tree).  One CTA per
+// caller block.
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_mass_max(int nb, const int *__restrict__ level, const T *__restrict__ density,
+               const double *__restrict__ Lf, const int *__restrict__ fid,
+               unsigned long long *__restrict__ mmax) {
+  const int b = blockIdx.x;
+  const int lb = level[b];
+  if (lb < 0 || lb > kMaxBlockLevel) return;
+  block_mass_max(b, fid[b], lb, density, Lf, mmax);
+}
+
+// The build's first kernel: block keys and the largest cell mass together,
+// one CTA per caller block (thread 0 forms the key).
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_keys_mass(int nb, const int *__restrict__ level, const int *__restrict__ ijk,
+                unsigned long long *__restrict__ key, int *__restrict__ idx, unsigned *flags,
+                int nfields, const int *__restrict__ fstart, int *__restrict__ fid,
+                const T *__restrict__ density, const double *__restrict__ Lf,
+                unsigned long long *__restrict__ mmax) {
+  const int b = blockIdx.x;
+  const int f = field_of(b, nfields, fstart);
+  if (threadIdx.x == 0) key_of_block(b, f, level, ijk, key, idx, flags, fstart, fid);
+  const int lb = level[b];
+  if (lb < 0 || lb > kMaxBlockLevel) return;
+  block_mass_max(b, f, lb, density, Lf, mmax);
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
 
 }  // namespace
 
-cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
-                              unsigned long long *key, int *idx, unsigned *flags,
-                              const FieldArgs &fa) {
-  k_block_keys<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
-                                                  fa.fstart, fa.fid);
+cudaError_t launch_keys_mass(cudaStream_t s, int nb, const int *level, const int *ijk,
+                             unsigned long long *key, int *idx, unsigned *flags,
+                             const FieldArgs &fa, const void *density, int density_is_fp64) {
+  if (density_is_fp64)
+    k_keys_mass<double><<<nb, kBlockThreads, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
+                                                      fa.fstart, fa.fid, (const double *)density,
+                                                      fa.L, fa.mmax);
+  else
+    k_keys_mass<float><<<nb, kBlockThreads, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
+                                                     fa.fstart, fa.fid, (const float *)density,
+                                                     fa.L, fa.mmax);
   return cudaGetLastError();
 }
 
@@ -826,9 +1030,9 @@ cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk, int *count,
                                   int4 *blk, int *orig, unsigned *flags, const FieldArgs &fa,
-                                  int *pos) {
+                                  const TopArgs &top, int *pos) {
   k_tile_and_count<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, idx, level, ijk, count, blk, orig,
-                                                      flags, fa.fstart, fa.fid, pos);
+                                                      flags, fa.fstart, fa.fid, pos, top.bparent);
   return cudaGetLastError();
 }
 
@@ -842,42 +1046,15 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
                              unsigned *flags, const FieldArgs &fa, const int *orig,
-                             int max_level, int *child, int64_t child_slots) {
+                             int max_level, const TopArgs &top) {
   k_top_nodes<<<grid_for(nb, 256), 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, rec,
                                                  aux, lvl, flags, fa.nfields, fa.fstart, fa.fid,
-                                                 orig, fa.fld);
+                                                 orig, fa.fld, top);
   if (max_level > 0) {  // a block starts at most max_level top nodes
     const dim3 grid((unsigned)grid_for((int64_t)nb * 8, 256), (unsigned)max_level);
     k_top_children<<<grid, 256, 0, s>>>(nb, key, blk, count, prestart, n_nodes, fa.fstart,
-                                         fa.fid, orig, child, child_slots, flags);
+                                         fa.fid, orig, top, flags);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
-                          const int *count, const int *prestart, const void *density,
-                          int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
-                          double4_32a *mom, WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
-                          WalkQuad *qrec, unsigned *flags) {
-  if (density_is_fp64)
-    k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                   (const double *)density, fa.L, fa.fid,
-                                                   fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux,
-                                                   lvl, q64, qrec, flags);
-  else
-    k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
-                                                  (const float *)density, fa.L, fa.fid, fa.mmax,
-                                                  fa.inv_theta, n_nodes, mom, rec, aux, lvl, q64,
-                                                  qrec, flags);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_block_upper<1><<<grid_for((int64_t)nb * 8, 256), 256, 0, s>>>(
-      nb, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux, lvl,
-      q64, qrec);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_block_upper<0><<<grid_for(nb, 256), 256, 0, s>>>(
-      nb, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux, lvl,
-      q64, qrec);
   return cudaGetLastError();
 }
 
@@ -892,29 +1069,26 @@ cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void
   return cudaGetLastError();
 }
 
-cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top,
-                            const unsigned long long *key, const int4 *blk, const int *count,
-                            const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
-                            float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
-                            const FieldArgs &fa, const int *child, int64_t child_slots) {
-  if (n_top <= 0) return cudaSuccess;
-  for (int lev = max_level - 1; lev >= 0; --lev) {
-    const cudaError_t e = launch_top_moments(s, nb, lev, key, blk, count, prestart, n_nodes, mom,
-                                             rec, aux, q64, qrec, flags, fa, child, child_slots);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
-                               const int4 *blk, const int *count, const int *prestart,
-                               int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa,
-                               const int *child, int64_t child_slots) {
-  k_top_moments<<<grid_for(nb, 256), 256, 0, s>>>(nb, level, key, blk, count, prestart,
-                                                   n_nodes, mom, rec, aux, q64, qrec, flags,
-                                                   fa.fld, fa.mmax, fa.inv_theta, child,
-                                                   child_slots);
+cudaError_t launch_moments(cudaStream_t s, int nb, const int4 *blk, const int *orig,
+                           const int *count, const int *prestart, const void *density, int density_is_fp64, const FieldArgs &fa,
+                           int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
+                           uint8_t *lvl, double *q64, WalkQuad *qrec, unsigned *flags,
+                           const TopArgs &top) {
+  if (density_is_fp64)
+    k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
+                                                   (const double *)density, fa.L, fa.fid,
+                                                   fa.mmax, fa.inv_theta, n_nodes, mom, rec, aux,
+                                                   lvl, q64, qrec, flags);
+  else
+    k_blocks<float><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
+                                                  (const float *)density, fa.L, fa.fid, fa.mmax,
+                                                  fa.inv_theta, n_nodes, mom, rec, aux, lvl, q64,
+                                                  qrec, flags);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_upper_tree<<<grid_for(nb, kUpperBlocks), 8 * kUpperBlocks, 0, s>>>(
+      nb, fa.nfields, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom,
+      rec, aux, lvl, q64, qrec, flags, top);
   return cudaGetLastError();
 }
 

@@ -93,6 +93,34 @@ struct WalkShape {
   unsigned *counter = nullptr;
 };
 
+// Top nodes (the cubes above the blocks), by slot = their rank among the
+// top nodes in pre-order, made once per geometry by k_top_nodes and
+// k_top_children for the moment pass, which climbs the top tree by arrival
+// counts.  All in one allocation of top_ints(nb_cap) ints.
+struct TopArgs {
+  int *child = nullptr;         // 8 per slot: pre-order index of child o
+  int4 *slot = nullptr;         // 2 per slot: {node, skip, cube x, cube y},
+                                //             {cube z, level, field, sorted block}
+  int *parent = nullptr;        // per slot: parent slot, -1 for a field's root
+  unsigned *arrive = nullptr;   // per slot: children done in this pass (0 between passes)
+  int *bparent = nullptr;       // per sorted block: the slot of its root's parent, or -1
+  int64_t slots = 0;            // capacity in slots
+};
+// Top nodes number (nb_f - 1)/7 per field, so fewer than nb/4 in all.
+constexpr int64_t top_slots(int64_t nb_cap) { return nb_cap / 4; }
+constexpr int64_t top_ints(int64_t nb_cap) { return 18 * top_slots(nb_cap) + nb_cap; }
+inline TopArgs top_args(int *base, int64_t nb_cap) {
+  TopArgs a;
+  const int64_t S = top_slots(nb_cap);
+  a.child = base;
+  a.slot = reinterpret_cast<int4 *>(base + 8 * S);
+  a.parent = base + 16 * S;
+  a.arrive = reinterpret_cast<unsigned *>(base + 17 * S);
+  a.bparent = base + 18 * S;
+  a.slots = S;
+  return a;
+}
+
 struct Tree {
   // block arrays (capacity nb_cap)
   int *d_level = nullptr, *d_ijk = nullptr;
@@ -102,7 +130,7 @@ struct Tree {
   int4 *d_blk = nullptr;
   int *d_orig = nullptr;
   int *d_pos = nullptr;         // sorted position of each caller block
-  int *d_child = nullptr;       // child lists of the top nodes: 8 per top node (2 nb_cap ints)
+  int *d_top = nullptr;         // top-node lists (TopArgs, top_ints(nb_cap) ints)
   unsigned *d_flags = nullptr;  // [0] error bits, [1] unsorted flag, [2] top-node total,
                                 // [4] work counter of the persistent walk (8 entries)
   unsigned *h_flags = nullptr;  // pinned mirror of d_flags
@@ -115,6 +143,11 @@ struct Tree {
   double *d_L = nullptr;        // per field
   unsigned long long *d_mmax = nullptr;  // per field, largest cell mass (bits)
   int nf_cap = 0;
+  // d_mmax, d_L, d_invL, d_fstart, d_level and d_ijk live in d_geo, which a
+  // build fills from its pinned mirror h_geo in one copy (geo_done: that copy)
+  unsigned char *d_geo = nullptr, *h_geo = nullptr;
+  int64_t geo_nb_cap = 0;
+  cudaEvent_t geo_done = nullptr;
   std::vector<double> h_L;      // per field, host copy
   std::vector<int64_t> h_fnode; // first node of each field, then the total
   // batched solve: CUDA graph of (moments for new densities + walk)
@@ -189,49 +222,39 @@ __host__ __device__ inline double pow2i(int e) {
 
 // ---- build kernels (bh_build.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
-cudaError_t launch_block_keys(cudaStream_t s, int nb, const int *level, const int *ijk,
-                              unsigned long long *key, int *idx, unsigned *flags,
-                              const FieldArgs &fa);
+// Block keys (caller order, fid too) and the largest cell mass of every field
+// (atomic max on fa.mmax, which the caller zeroes first): one launch.
+cudaError_t launch_keys_mass(cudaStream_t s, int nb, const int *level, const int *ijk,
+                             unsigned long long *key, int *idx, unsigned *flags,
+                             const FieldArgs &fa, const void *density, int density_is_fp64);
 cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *idx[2],
                                unsigned *flags, const FieldArgs &fa);
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,
                                   const int *idx, const int *level, const int *ijk,
                                   int *count, int4 *blk, int *orig, unsigned *flags,
-                                  const FieldArgs &fa, int *pos = nullptr);
+                                  const FieldArgs &fa, const TopArgs &top, int *pos = nullptr);
 cudaError_t launch_prestart_scan(cudaStream_t s, int nb, const int *count, int *prestart,
                                  unsigned *flags);
-// Skip pointers of the top nodes, and their child lists: child[8 slot + o]
-// (child_slots = capacity in top nodes) for the moment pass; max_level =
-// the largest block level.
+// Skip pointers of the top nodes and their lists (TopArgs); max_level = the
+// largest block level.
 cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *key,
                              const int4 *blk, const int *count, const int *prestart,
                              int64_t n_nodes, WalkRec *rec, float2 *aux, uint8_t *lvl,
                              unsigned *flags, const FieldArgs &fa, const int *orig,
-                             int max_level, int *child, int64_t child_slots);
-// Largest cell mass of every field (atomic max on fa.mmax, which the caller
-// zeroes first); caller block order.
+                             int max_level, const TopArgs &top);
+// Largest cell mass of every field alone (a new density on the same tree).
 cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
                             int density_is_fp64, const FieldArgs &fa);
-cudaError_t launch_blocks(cudaStream_t s, int nb, const int4 *blk, const int *orig,
-                          const int *count, const int *prestart, const void *density,
-                          int density_is_fp64, const FieldArgs &fa, int64_t n_nodes,
-                          double4_32a *mom, WalkRec *rec, float2 *aux, uint8_t *lvl, double *q64,
-                          WalkQuad *qrec, unsigned *flags);
+// Every node's moments: cells and bottom nodes (k_blocks), then the rest of
+// the blocks and the top tree (k_upper_tree), two launches.
+cudaError_t launch_moments(cudaStream_t s, int nb, const int4 *blk, const int *orig,
+                           const int *count, const int *prestart, const void *density, int density_is_fp64, const FieldArgs &fa,
+                           int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
+                           uint8_t *lvl, double *q64, WalkQuad *qrec, unsigned *flags,
+                           const TopArgs &top);
 // Raises the dynamic shared-memory limit of the learned walk (more than 48 KB)
 // on the current device; called once per context, outside any graph capture.
 cudaError_t prepare_learned_kernels();
-// Every top level, deepest first, one launch per level; n_top = number of
-// top nodes (all fields).
-cudaError_t launch_top_tree(cudaStream_t s, int nb, int max_level, int64_t n_top,
-                            const unsigned long long *key, const int4 *blk, const int *count,
-                            const int *prestart, int64_t n_nodes, double4_32a *mom, WalkRec *rec,
-                            float2 *aux, double *q64, WalkQuad *qrec, unsigned *flags,
-                            const FieldArgs &fa, const int *child, int64_t child_slots);
-cudaError_t launch_top_moments(cudaStream_t s, int nb, int level, const unsigned long long *key,
-                               const int4 *blk, const int *count, const int *prestart,
-                               int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
-                               double *q64, WalkQuad *qrec, unsigned *flags, const FieldArgs &fa,
-                               const int *child, int64_t child_slots);
 
 // ---- walk kernels (bh_walk.cu) ---------------------------------------------
 cudaError_t launch_prepare_s2(cudaStream_t s, int64_t n_nodes, const float2 *aux, WalkRec *rec,

@@ -57,9 +57,8 @@ constexpr size_t kOffMom = up256(kOffMmax + sizeof(unsigned long long));
 constexpr size_t kOffRec = up256(kOffMom + sizeof(double4_32a) * kNoAllocMaxNodes);
 constexpr size_t kOffAux = up256(kOffRec + sizeof(WalkRec) * kNoAllocMaxNodes);
 constexpr size_t kOffLvl = up256(kOffAux + sizeof(float2) * kNoAllocMaxNodes);
-constexpr int64_t kNoAllocChildSlots = kNoAllocMaxBlocks / 4;  // > (64 - 1)/7 top nodes
-constexpr size_t kOffChild = up256(kOffLvl + sizeof(uint8_t) * kNoAllocMaxNodes);
-constexpr size_t kScratchBytes = up256(kOffChild + 8 * sizeof(int) * kNoAllocChildSlots);  // ~2.7 MB
+constexpr size_t kOffTop = up256(kOffLvl + sizeof(uint8_t) * kNoAllocMaxNodes);  // TopArgs
+constexpr size_t kScratchBytes = up256(kOffTop + sizeof(int) * top_ints(kNoAllocMaxBlocks));  // ~2.7 MB
 
 // The fixed scratch.  In host code this name is only a stand-in for the
 // symbol: host code must use the address returned by cudaGetSymbolAddress.
@@ -162,7 +161,7 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   WalkRec *d_rec = (WalkRec *)(base + kOffRec);
   float2 *d_aux = (float2 *)(base + kOffAux);
   uint8_t *d_lvl = (uint8_t *)(base + kOffLvl);
-  int *d_child = (int *)(base + kOffChild);
+  const TopArgs top = top_args((int *)(base + kOffTop), kNoAllocMaxBlocks);
   int *d_fstart = (int *)(base + kOffFstart);
   double *d_box = (double *)(base + kOffBox);
   FieldArgs fa;
@@ -178,19 +177,17 @@ extern "C" bh_status bh_solve_noalloc(int nblocks, const int32_t *level, const i
   k_stage_geometry<<<1, 256, 0, s>>>(g, nb, d_level, d_ijk, d_flags, d_fstart, d_box, box_len,
                                      fa.mmax);
   NA_CUDA(cudaGetLastError());
-  NA_CUDA(launch_block_keys(s, nb, d_level, d_ijk, d_key[0], d_idx[0], d_flags, fa));
+  NA_CUDA(launch_keys_mass(s, nb, d_level, d_ijk, d_key[0], d_idx[0], d_flags, fa, density,
+                           density_is_fp64));
   NA_CUDA(launch_sort_blocks(s, d_key, d_idx, d_flags, fa));
   NA_CUDA(launch_tile_and_count(s, nb, d_key[0], d_idx[0], d_level, d_ijk, d_count, d_blk,
-                                d_orig, d_flags, fa));
+                                d_orig, d_flags, fa, top));
   NA_CUDA(launch_prestart_scan(s, nb, d_count, d_prestart, d_flags));
   NA_CUDA(launch_top_nodes(s, nb, d_key[0], d_blk, d_count, d_prestart, n_nodes, d_rec, d_aux,
-                           d_lvl, d_flags, fa, d_orig, max_level, d_child, kNoAllocChildSlots));
-  NA_CUDA(launch_mass_max(s, nb, d_level, density, density_is_fp64, fa));
-  NA_CUDA(launch_blocks(s, nb, d_blk, d_orig, d_count, d_prestart, density, density_is_fp64, fa,
-                        n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr, d_flags));
-  NA_CUDA(launch_top_tree(s, nb, max_level, (nb - 1) / 7, d_key[0], d_blk, d_count, d_prestart,
-                          n_nodes, d_mom, d_rec, d_aux, nullptr, nullptr, d_flags, fa, d_child,
-                          kNoAllocChildSlots));
+                           d_lvl, d_flags, fa, d_orig, max_level, top));
+  NA_CUDA(launch_moments(s, nb, d_blk, d_orig, d_count, d_prestart, density,
+                         density_is_fp64, fa, n_nodes, d_mom, d_rec, d_aux, d_lvl, nullptr, nullptr,
+                         d_flags, top));
   // the walk must only run on a valid tree: check the flags first
   unsigned h_flags[4] = {0, 0, 0, 0};
   NA_CUDA(cudaMemcpyAsync(h_flags, d_flags, sizeof(h_flags), cudaMemcpyDeviceToHost, s));
