@@ -84,8 +84,10 @@ def parse():
                     help="--workload learned: seeded training fields")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--walk-shape", default=None,
-                    help="W,P,T: the walk's launch shape (warps per CTA, target pairs per "
-                         "lane, groups per take; 0 = plain grid) instead of bh_autotune")
+                    help="W,P,T[,L]: the walk's launch shape (warps per CTA, target pairs "
+                         "per lane, groups per take; 0 = plain grid; L = 1: the groups longest "
+                         "walk first, the order bh_autotune makes, run untimed before) "
+                         "instead of the shape bh_autotune picks")
     ap.add_argument("--all-cells-limit", type=int, default=4_200_000,
                     help="largest field (cells) whose potentials are compared with the "
                          "exhaustive direct sum over every cell (N^2 work)")
@@ -595,7 +597,7 @@ def batched_arm(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s = bh.Solver(device=dev.index, stream=stream)
     s.build_batch(nb, level, ijk, d_rho, lo, ln)
-    wpc, npairs, ticket = s.autotune(theta)
+    wpc, npairs, ticket, longest = s.autotune(theta)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s.solve_graph(d_rho, theta, 1.0, out)
@@ -714,7 +716,7 @@ def batched_arm(args):
                        "walk": "binary32, compensated sum, per-cell opening test, monopole nodes",
                        "step": "one CUDA-graph launch: moments + walk of all fields",
                        "tuned_warps_per_cta": wpc, "tuned_target_pairs_per_lane": npairs,
-                       "tuned_groups_per_take": ticket,
+                       "tuned_groups_per_take": ticket, "tuned_longest_first": longest,
                        "l2": "flushed between steps"},
             "vs_plain": {"how": "the same fields one after the other: bh_build + bh_potential",
                          "value": p_value, "ms_per_step": p_ms, "speedup": value / p_value,
@@ -1002,7 +1004,9 @@ def main():
     with torch.cuda.stream(stream):
         solver.build(mesh.level, mesh.ijk, d_rho)
     if args.walk_shape:
-        shape = tuple(int(v) for v in args.walk_shape.split(","))
+        shape = (tuple(int(v) for v in args.walk_shape.split(",")) + (0,))[:4]
+        if shape[3]:
+            solver.autotune(args.theta)  # makes the longest-first order
         solver.set_walk_shape(*shape)
     else:
         shape = solver.autotune(args.theta)
@@ -1063,7 +1067,7 @@ def main():
         phi_plain = pout.double().cpu().numpy()
         plain = {"theta": args.plain_theta, "walk": "binary32, compensated sum, per-cell, monopole",
                  "walk_shape": {"warps_per_cta": pshape[0], "target_pairs_per_lane": pshape[1],
-                                "groups_per_take": pshape[2]},
+                                "groups_per_take": pshape[2], "longest_first": pshape[3]},
                  "value": p_value, "unit": "cells/s", "steps": psteps,
                  "ms_per_step": p_total / psteps,
                  "phases_ms": {"build": float(np.mean(p_build)),
@@ -1137,9 +1141,12 @@ def main():
                        "walk_shape": {"warps_per_cta": shape[0],
                                       "target_pairs_per_lane": shape[1],
                                       "groups_per_take": shape[2],
+                                      "longest_first": shape[3],
                                       "how": ("set by --walk-shape" if args.walk_shape else
                                               "bh_autotune on this tree before timing")
-                                             + " (0 groups per take: plain grid)"},
+                                             + " (0 groups per take: plain grid; longest "
+                                               "first: the groups sorted by the work of "
+                                               "their walks, made by bh_autotune)"},
                        "parallelism": f"replicas x{world}"},
             "phases_ms": {"build": float(np.mean(build_ms)), "potential": float(np.mean(walk_ms)),
                           "step_median": float(np.median(step_ms)),

@@ -178,25 +178,34 @@ bh_status bh_sync_status(bh_ctx *ctx);
 /* Times the binary32 per-cell walk of the current tree at this theta for
  * every launch shape it offers -- CTAs of 2, 4, 8 and 16 warps; warps that
  * walk for 64 targets (a 4x4x4 octant of a block, one pair of x-neighbours
- * per lane) or 128 targets (a 8x4x4 slab, two pairs per lane); and either a
+ * per lane) or 128 targets (a 8x4x4 slab, two pairs per lane); either a
  * plain grid of one warp per group or a persistent grid (as many CTAs as the
  * GPU holds at once) whose warps take 1, 2 or 4 groups at a time from a work
- * counter (the periodic walk: CTA width only) -- and keeps the fastest for
- * later walks.  All shapes give bit-identical potentials.  shape (may be
- * NULL) receives three ints: {warps per CTA, target pairs per lane, groups
- * per take (0 = plain grid)}; all 0 for walk modes with a fixed launch
- * shape.  Allocates a scratch output once. */
+ * counter; and the groups in their own (Morton) order or longest walk first
+ * (the periodic walk: CTA width only) -- and keeps the fastest for later
+ * walks.  For the longest-first order it first runs the counting walk at
+ * this theta and sorts the groups by the interactions and opening tests of
+ * their targets (on the host); that order is kept with the context, like
+ * the shape, and used while the tree has the same number of groups (a
+ * permutation of the groups: it can only change the speed).  All shapes
+ * give bit-identical potentials.  shape (may be NULL) receives four ints:
+ * {warps per CTA, target pairs per lane, groups per take (0 = plain grid),
+ * longest first (0/1)}; all 0 for walk modes with a fixed launch shape.
+ * Allocates a scratch output once and the order (4 bytes per group). */
 bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape);
 
-/* Sets the launch shape of the binary32 per-cell walk (the three values
+/* Sets the launch shape of the binary32 per-cell walk (the four values
  * bh_autotune chooses among), e.g. one found by an earlier bh_autotune on
  * the same kind of mesh: warps per CTA (1..16), target pairs per lane (1 or
- * 2) and groups per take of the persistent grid (0 = plain grid, 1..64); 0
- * for the first two means the default.  Potentials do not depend on the
- * shape (bit for bit).  Drops a captured bh_solve_graph graph.  BH_ERR_ARG
- * for values out of range (the periodic walk: one pair, plain grid). */
+ * 2), groups per take of the persistent grid (0 = plain grid, 1..64) and
+ * longest_first (1: the walk order made by the last bh_autotune, 0: the
+ * groups' own order); 0 for the first two means the default.  Potentials do
+ * not depend on the shape (bit for bit).  Drops a captured bh_solve_graph
+ * graph.  BH_ERR_ARG for values out of range (the periodic walk: one pair,
+ * plain grid, own order); BH_ERR_STATE for longest_first = 1 without an
+ * order. */
 bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
-                            int groups_per_take);
+                            int groups_per_take, int longest_first);
 
 /* bh_update_density + bh_potential as ONE CUDA graph launch: the first call
  * (or a call with a different density/out pointer, density type, theta or G)

@@ -82,7 +82,7 @@ def load(build_if_needed: bool = True):
         lib.bh_update_density.argtypes = [P, P, I]
         lib.bh_sync_status.argtypes = [P]
         lib.bh_autotune.argtypes = [P, D, P]
-        lib.bh_set_walk_shape.argtypes = [P, I, I, I]
+        lib.bh_set_walk_shape.argtypes = [P, I, I, I, I]
         lib.bh_solve_graph.argtypes = [P, P, I, D, D, P]
         lib.bh_walk_counts.argtypes = [P, D, P, P, P]
         lib.bh_tree_size.argtypes = [P, P, P, P]
@@ -197,15 +197,16 @@ def bh_sync_status(ctx) -> None:
 
 def bh_autotune(ctx, theta: float) -> tuple:
     """Returns the chosen (warps per CTA, target pairs per lane, groups per
-    take of the persistent walk; 0 = plain grid)."""
-    sh = (ctypes.c_int * 3)()
+    take of the persistent walk or 0 for a plain grid, longest first 0/1)."""
+    sh = (ctypes.c_int * 4)()
     _check(ctx, load().bh_autotune(ctx, float(theta), sh), "bh_autotune")
-    return int(sh[0]), int(sh[1]), int(sh[2])
+    return int(sh[0]), int(sh[1]), int(sh[2]), int(sh[3])
 
 
-def bh_set_walk_shape(ctx, warps: int, pairs: int, groups_per_take: int) -> None:
-    _check(ctx, load().bh_set_walk_shape(ctx, int(warps), int(pairs), int(groups_per_take)),
-           "bh_set_walk_shape")
+def bh_set_walk_shape(ctx, warps: int, pairs: int, groups_per_take: int,
+                      longest_first: int = 0) -> None:
+    _check(ctx, load().bh_set_walk_shape(ctx, int(warps), int(pairs), int(groups_per_take),
+                                         int(longest_first)), "bh_set_walk_shape")
 
 
 def bh_solve_graph(ctx, density, theta: float, G: float, out) -> None:
@@ -459,12 +460,13 @@ class Solver:
 
     def autotune(self, theta: float) -> tuple:
         """Tunes the walk's launch shape: (warps per CTA, target pairs per lane,
-        groups per take of the persistent walk or 0)."""
+        groups per take of the persistent walk or 0, longest first 0/1)."""
         return bh_autotune(self._ctx, theta)
 
-    def set_walk_shape(self, warps: int, pairs: int = 0, groups_per_take: int = 0):
+    def set_walk_shape(self, warps: int, pairs: int = 0, groups_per_take: int = 0,
+                       longest_first: int = 0):
         """Pins the walk's launch shape (see bh_set_walk_shape)."""
-        bh_set_walk_shape(self._ctx, warps, pairs, groups_per_take)
+        bh_set_walk_shape(self._ctx, warps, pairs, groups_per_take, longest_first)
 
     def solve_graph(self, density, theta: float, G: float = 1.0, out=None):
         import torch

@@ -220,7 +220,7 @@ bhg::FieldArgs field_args(bhg::Tree &t) {
 // Moments of the current geometry from a density (k_blocks + one launch per
 // level above the blocks); stream-ordered, no host synchronisation.
 bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64,
-                          bool mmax_ready = false) {
+                          bool mmax_ready = false, cudaEvent_t before_upper = nullptr) {
   bhg::Tree &t = ctx->tree;
   cudaStream_t s = ctx->stream;
   // FP64 quadrupoles for the FP64 walk, binary32 ones for the binary32 walk
@@ -234,7 +234,8 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64,
     BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa));
   }
   BH_CUDA(bhg::launch_moments(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density, density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux,
-                              t.d_lvl, q64, qrec, t.d_flags, bhg::top_args(t.d_top, t.nb_cap)));
+                              t.d_lvl, q64, qrec, t.d_flags, bhg::top_args(t.d_top, t.nb_cap),
+                              before_upper));
   return BH_OK;
 }
 
@@ -368,10 +369,22 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
                                      t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, top, t.d_pos));
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
-  BH_CUDA(bhg::launch_top_nodes(s, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart, n_nodes,
-                                t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig,
+  // the top nodes' records and child lists (needed from k_upper_tree on) on
+  // the side stream, beside k_blocks, which writes only the blocks' nodes
+  if (!ctx->side) {
+    int lo_prio = 0, hi_prio = 0;
+    BH_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    BH_CUDA(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi_prio));
+    BH_CUDA(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    BH_CUDA(cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming));
+  }
+  BH_CUDA(cudaEventRecord(ctx->fork, s));
+  BH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+  BH_CUDA(bhg::launch_top_nodes(ctx->side, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
+                                n_nodes, t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig,
                                 max_level, top));
-  if ((st = enqueue_moments(ctx, density, density_is_fp64, true)) != BH_OK) return st;
+  BH_CUDA(cudaEventRecord(ctx->join, ctx->side));
+  if ((st = enqueue_moments(ctx, density, density_is_fp64, true, ctx->join)) != BH_OK) return st;
   ctx->build_timed = timed && timing_mark(ctx, 1);
   BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
@@ -453,6 +466,12 @@ static cudaError_t enqueue_walk(bh_ctx *ctx, cudaStream_t s, double G, void *out
   if (!n_int && ctx->opt.learned == 2) return bhg::launch_walk_learned_tc(s, ctx, G, out);
   if (!n_int && ctx->opt.learned) return bhg::launch_walk_learned(s, ctx, G, out);
   shape.counter = t.d_flags + 4;  // the work counter of the persistent walk
+  {  // the groups' walk order made by bh_autotune, while it fits the tree
+    const int np = shape.pairs > 0 ? shape.pairs : 1;
+    const int64_t groups = (int64_t)t.nb * (8 / np);
+    shape.order = (shape.longest && np <= 2 && t.order_n[np - 1] == groups) ? t.d_order[np - 1]
+                                                                             : nullptr;
+  }
   return bhg::launch_walk(s, ctx->opt, t.nb, t.d_rec, t.d_mom, t.d_qrec, t.d_q64, t.d_blk,
                           t.d_orig, field_args(t), G, out, n_int, n_test, n_leaf, shape);
 }
@@ -742,7 +761,77 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
   return BH_OK;
 }
 
+// The walk order of the groups for one and for two target pairs per lane,
+// longest walk first: a group's cost is the sum over its targets of their
+// interactions and opening tests, from the counting walk at the prepared
+// theta (the decisions of every binary32 per-cell walk).  The persistent
+// walk then starts the long walks first and ends with the short ones, and
+// the plain grid's CTAs (issued in index order) do the same.  Host side:
+// the counts come back, the groups are sorted (stable, so equal costs keep
+// their Morton order) and the order goes up; only bh_autotune does this.
+static bh_status make_walk_order(bh_ctx *ctx, int npairs) {
+  bhg::Tree &t = ctx->tree;
+  const int64_t ncell = (int64_t)t.nb * bhg::kCellsPerBlock;
+  int32_t *d_cnt = nullptr;
+  BH_CUDA(bhg::dev_malloc(&d_cnt, 2 * (size_t)ncell * sizeof(int32_t)));
+  bhg::WalkShape plain;
+  cudaError_t e = enqueue_walk(ctx, ctx->stream, 0.0, nullptr, d_cnt, d_cnt + ncell, nullptr,
+                               plain);
+  std::vector<int32_t> cnt;
+  std::vector<int> orig(t.nb);
+  try {
+    cnt.resize(2 * (size_t)ncell);
+  } catch (const std::bad_alloc &) {
+    release(d_cnt);
+    return fail(ctx, BH_ERR_OOM, "bh_autotune: no host memory for the walk counts");
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cnt.data(), d_cnt, 2 * (size_t)ncell * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(orig.data(), t.d_orig, (size_t)t.nb * sizeof(int), cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  release(d_cnt);
+  BH_CUDA(e);
+  // work of each target cell (caller layout) by its octant of its sorted block
+  std::vector<int64_t> oct((size_t)t.nb * 8, 0);
+  for (int p = 0; p < t.nb; ++p) {
+    const int64_t base = (int64_t)orig[p] * bhg::kCellsPerBlock;
+    for (int m = 0; m < bhg::kCellsPerBlock; ++m) {
+      const int cx = (int)bhg::compact3(m), cy = (int)bhg::compact3(m >> 1),
+                cz = (int)bhg::compact3(m >> 2);
+      const int64_t c = base + cz * 64 + cy * 8 + cx;
+      oct[(size_t)p * 8 + (m >> 6)] += (int64_t)cnt[c] + cnt[ncell + c];
+    }
+  }
+  for (int np = 1; np <= npairs; ++np) {
+    const int64_t groups = (int64_t)t.nb * (8 / np);
+    std::vector<int64_t> cost(groups, 0);
+    for (int64_t g = 0; g < groups; ++g)
+      for (int k = 0; k < np; ++k) cost[g] += oct[(size_t)(g * np + k)];
+    std::vector<unsigned> order(groups);
+    for (int64_t g = 0; g < groups; ++g) order[g] = (unsigned)g;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](unsigned a, unsigned b) { return cost[a] > cost[b]; });
+    unsigned *&d = t.d_order[np - 1];
+    if (t.order_cap[np - 1] < groups) {
+      release(d);
+      t.order_cap[np - 1] = 0;
+      t.order_n[np - 1] = 0;
+      BH_CUDA(bhg::dev_malloc(&d, (size_t)groups * sizeof(unsigned)));
+      t.order_cap[np - 1] = groups;
+    }
+    BH_CUDA(cudaMemcpyAsync(d, order.data(), (size_t)groups * sizeof(unsigned),
+                            cudaMemcpyHostToDevice, ctx->stream));
+    BH_CUDA(cudaStreamSynchronize(ctx->stream));  // the host vector goes out of scope
+    t.order_n[np - 1] = groups;
+  }
+  return BH_OK;
+}
+
 bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
+  const Range range_("bh_autotune");
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   bh_status st = prepare(ctx, theta);
@@ -760,6 +849,8 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
       BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
       t.stage_out_bytes = out_bytes;
     }
+    const bool ordered = !ctx->opt.periodic;
+    if (ordered && (st = make_walk_order(ctx, npairs)) != BH_OK) return st;
     cudaEvent_t e0, e1;
     BH_CUDA(cudaEventCreate(&e0));
     BH_CUDA(cudaEventCreate(&e1));
@@ -771,12 +862,13 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
     best_s.warps = 4;
     best_s.pairs = 1;
     for (int np = 1; np <= npairs; ++np) {
-      for (int ti = 0; ti < nticket * 4; ++ti) {
+      for (int ti = 0; ti < nticket * 4 * (ordered ? 2 : 1); ++ti) {
         const int w = cand[ti % 4];
         bhg::WalkShape sh;
         sh.warps = w;
         sh.pairs = np;
-        sh.ticket = tickets[ti / 5];
+        sh.ticket = tickets[(ti / 4) % nticket];
+        sh.longest = ti / (4 * nticket);
         float tmin = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
           BH_CUDA(cudaEventRecord(e0, ctx->stream));
@@ -803,24 +895,31 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
     shape[0] = tunable ? t.shape.warps : 0;
     shape[1] = tunable ? t.shape.pairs : 0;
     shape[2] = tunable ? t.shape.ticket : 0;
+    shape[3] = tunable ? t.shape.longest : 0;
   }
   return BH_OK;
 }
 
 bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
-                            int groups_per_take) {
+                            int groups_per_take, int longest_first) {
   if (!ctx) return BH_ERR_ARG;
   ctx->err[0] = 0;
   if (!(warps_per_cta == 0 || (warps_per_cta >= 1 && warps_per_cta <= 16)) ||
       !(pairs_per_lane >= 0 && pairs_per_lane <= 2) ||
-      !(groups_per_take >= 0 && groups_per_take <= 64))
-    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: warps 0..16, pairs 0..2, groups 0..64");
-  if (ctx->opt.periodic && (pairs_per_lane > 1 || groups_per_take > 0))
-    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: the periodic walk has one pair per lane "
-                                 "and a plain grid");
+      !(groups_per_take >= 0 && groups_per_take <= 64) ||
+      (longest_first != 0 && longest_first != 1))
+    return fail(ctx, BH_ERR_ARG,
+                "bh_set_walk_shape: warps 0..16, pairs 0..2, groups 0..64, longest_first 0/1");
+  if (ctx->opt.periodic && (pairs_per_lane > 1 || groups_per_take > 0 || longest_first))
+    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: the periodic walk has one pair per lane, "
+                                 "a plain grid and the groups' own order");
+  const int np = pairs_per_lane > 0 ? pairs_per_lane : 1;
+  if (longest_first && ctx->tree.order_n[np - 1] == 0)
+    return fail(ctx, BH_ERR_STATE, "bh_set_walk_shape: no walk order (run bh_autotune first)");
   ctx->tree.shape.warps = warps_per_cta;
   ctx->tree.shape.pairs = pairs_per_lane;
   ctx->tree.shape.ticket = groups_per_take;
+  ctx->tree.shape.longest = longest_first;
   drop_graph(ctx->tree);  // a captured walk holds the old shape
   return BH_OK;
 }
@@ -999,6 +1098,12 @@ void bh_destroy(bh_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
   drop_graph(ctx->tree);
   free_blocks(ctx->tree);
   free_nodes(ctx->tree);
@@ -1006,6 +1111,8 @@ void bh_destroy(bh_ctx *ctx) {
   release(ctx->tree.d_stage_in);
   release(ctx->tree.d_stage_out);
   release(ctx->tree.d_flags);
+  release(ctx->tree.d_order[0]);
+  release(ctx->tree.d_order[1]);
   release(ctx->d_mlp);
   release(ctx->d_mlp_tc);
   release(ctx->d_tc_flag);

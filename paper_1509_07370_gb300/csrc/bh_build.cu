@@ -242,12 +242,27 @@ __device__ __forceinline__ double pow2d(int e) {  // 2^e for -1022 <= e <= 1023,
 }
 
 // binary64 <-> binary32 conversions of the moment kernels.  (Measured: a
-// bit-level version on the integer pipes -- 64-bit integer arithmetic is
-// several instructions a step -- made k_blocks 7 % and the level-one nodes
-// 75 % slower than the conversion instructions.)
+// general bit-level version on the integer pipes -- 64-bit integer
+// arithmetic is several instructions a step -- made k_blocks 7 % and the
+// level-one nodes 75 % slower than the conversion instructions.)
 __device__ __forceinline__ double widen(float f) { return (double)f; }
-// fl32(x 2^k), 2^k a power of two that scales x exactly
+// A positive normal binary32 value as binary64 (exact): the exponent rebased
+// from 127 to 1023 and the 23 fraction bits moved up by 29, three 32-bit
+// integer operations instead of a conversion on GB300's narrow FP64 pipe.
+// Used for cube centres, (2i + 1) 2^-(level + 1) > 0.
+__device__ __forceinline__ double widen_pos(float f) {
+  const unsigned b = __float_as_uint(f);
+  return __hiloint2double((int)((b >> 3) + ((1023u - 127u) << 20)), (int)(b << 29));
+}
+// fl32(x 2^k), 2^k a power of two that scales x exactly.  For a normal x
+// whose scaled value stays normal the product is x with k added to its
+// exponent (an integer add on the high word); zeros and the rest take the
+// FP64 multiplication.
 __device__ __forceinline__ float narrow_scaled(double x, int k) {
+  const int hi = __double2hiint(x);
+  const int E = (hi >> 20) & 0x7ff;
+  if (E > 0 && E + k > 0 && E + k < 0x7ff)
+    return __double2float_rn(__hiloint2double(hi + (k << 20), __double2loint(x)));
   return __double2float_rn(x * pow2d(k));
 }
 __device__ __forceinline__ float narrow(double x) { return __double2float_rn(x); }
@@ -417,7 +432,7 @@ __device__ __forceinline__ float centre_coord_f(int i, int level) {
   return __fmul_rn((float)(2 * i + 1), pow2f(-(level + 1)));
 }
 __device__ __forceinline__ double centre_coord(int i, int level) {
-  return widen(centre_coord_f(i, level));
+  return widen_pos(centre_coord_f(i, level));
 }
 
 // ku: the exponent of the field's inverse binary32 mass unit (the record's
@@ -439,12 +454,20 @@ __device__ __forceinline__ WalkRec make_rec(double x, double y, double z, double
 // inv_theta > 0: also the squared opening radius s2 = fl(fl(l fl(1/theta)) +
 // delta)^2 from the same binary32 l and delta as k_prepare_s2 (identical).
 // Returns the record's binary32 mass (in the field's unit).
+// keep_off: also keep the binary32 offset R - c of the centre of mass from
+// the geometric centre, x and y in the record's two spare words (z goes
+// into the quadrupole record's, store_quad_f), for the parent's quadrupole
+// shift.
 __device__ __forceinline__ float store_internal(int64_t id, int64_t skip, int level,
                                                 const Moment &r, double4_32a *mom, WalkRec *rec,
                                                 float2 *aux, uint8_t *lvl, int ku,
-                                                float inv_theta) {
+                                                float inv_theta, bool keep_off = false) {
   mom[id] = make_double4_32a(r.x, r.y, r.z, r.m);
   WalkRec w = make_rec(r.x, r.y, r.z, r.m, ku, skip);
+  if (keep_off) {
+    w.pad[0] = narrow(r.ox);
+    w.pad[1] = narrow(r.oy);
+  }
   const float l = pow2f(-level), delta = narrow(r.delta);
   if (inv_theta > 0.0f) {
     const float s = __fadd_rn(__fmul_rn(l, inv_theta), delta);
@@ -511,7 +534,9 @@ __device__ __forceinline__ void add_shifted_ff(float Q[6], const float *Qc, floa
     for (int a = 0; a < 6; ++a) Q[a] += Qc[a];
 }
 
-__device__ __forceinline__ void store_quad_f(int64_t id, const float Q[6], WalkQuad *qrec) {
+// oz: the node's binary32 offset R_z - c_z (see store_internal), or 0.
+__device__ __forceinline__ void store_quad_f(int64_t id, const float Q[6], WalkQuad *qrec,
+                                             float oz = 0.0f) {
   WalkQuad w;
   w.hxx = 0.5f * Q[0];
   w.hyy = 0.5f * Q[1];
@@ -519,7 +544,8 @@ __device__ __forceinline__ void store_quad_f(int64_t id, const float Q[6], WalkQ
   w.qxy = Q[3];
   w.qxz = Q[4];
   w.qyz = Q[5];
-  w.pad[0] = w.pad[1] = 0.0f;
+  w.pad[0] = oz;
+  w.pad[1] = 0.0f;
   qrec[id] = w;
 }
 
@@ -596,7 +622,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     const float fx = centre_coord_f(8 * B.y + cx, lc);
     const float fy = centre_coord_f(8 * B.z + cy, lc);
     const float fz = centre_coord_f(8 * B.w + cz, lc);
-    const double ux = widen(fx), uy = widen(fy), uz = widen(fz);
+    const double ux = widen_pos(fx), uy = widen_pos(fy), uz = widen_pos(fz);
     const double mass = __dmul_rn(r, vol);
     const float mu = narrow_scaled(mass, ku);
     cm[m] = mass;
@@ -636,7 +662,7 @@ __global__ void __launch_bounds__(kBlockThreads)
       accumulate(M, Sx, Sy, Sz, cm[8 * q + o], cxs[8 * q + o], cys[8 * q + o], czs[8 * q + o]);
     const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
     const int64_t id = root + 2 + 73 * (q >> 3) + 9 * (q & 7);
-    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, ku, inv_theta);
+    store_internal(id, id + 9, lb + 2, r, mom, rec, aux, lvl, ku, inv_theta, quad32);
     if (quad64) {
       double Q[6] = {0, 0, 0, 0, 0, 0};
       for (int o = 0; o < 8; ++o) {
@@ -654,7 +680,7 @@ __global__ void __launch_bounds__(kBlockThreads)
         add_shifted_ff(Q, nullptr, cmu[8 * q + o], __fsub_rn(dx, ox), __fsub_rn(dy, oy),
                        __fsub_rn(dz, oz));
       }
-      store_quad_f(id, Q, qrec);
+      store_quad_f(id, Q, qrec, oz);
     }
   }
 }
@@ -699,7 +725,8 @@ __device__ __forceinline__ void level_one_node(int lev, int ix, int iy, int iz, 
 #pragma unroll
   for (int o = 1; o < 8; ++o) accumulate(M, Sx, Sy, Sz, ch[o].w, ch[o].x, ch[o].y, ch[o].z);
   const Moment r = finish(M, Sx, Sy, Sz, cx, cy, cz);
-  store_internal(id, skip, lev, r, mom, rec, aux, lvl, ku, inv_theta);
+  const bool quad32 = qrec && !q64;
+  store_internal(id, skip, lev, r, mom, rec, aux, lvl, ku, inv_theta, quad32);
   if (q64) {
     double Q[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -715,17 +742,18 @@ __device__ __forceinline__ void level_one_node(int lev, int ix, int iy, int iz, 
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int64_t k = first + stride * o;
-      // the child's binary32 offset R - c from its own centre, as it was formed
-      const float gx = narrow(__dsub_rn(ch[o].x, centre_coord(2 * ix + (o & 1), lev + 1)));
-      const float gy = narrow(__dsub_rn(ch[o].y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
-      const float gz = narrow(__dsub_rn(ch[o].z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
+      // the child's binary32 offset R - c from its own centre, as k_blocks
+      // formed it (narrow(R - c) in FP64) and kept in its spare words
+      const WalkRec cr = rec[k];
+      const WalkQuad cq = qrec[k];
       float Qc[6];
-      load_quad_f(qrec[k], Qc);
+      load_quad_f(cq, Qc);
       const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
-      add_shifted_ff(Q, Qc, rec[k].m, __fsub_rn(__fadd_rn(dx, gx), ox),
-                     __fsub_rn(__fadd_rn(dy, gy), oy), __fsub_rn(__fadd_rn(dz, gz), oz));
+      add_shifted_ff(Q, Qc, cr.m, __fsub_rn(__fadd_rn(dx, cr.pad[0]), ox),
+                     __fsub_rn(__fadd_rn(dy, cr.pad[1]), oy),
+                     __fsub_rn(__fadd_rn(dz, cq.pad[0]), oz));
     }
-    store_quad_f(id, Q, qrec);
+    store_quad_f(id, Q, qrec, oz);
   }
 }
 
@@ -751,10 +779,14 @@ __device__ __forceinline__ void group_node(unsigned gmask, int gbase, int o, int
                                            WalkQuad *qrec) {
   const double4_32a c = CG ? ld_mom_cg(mom + child) : mom[child];
   WalkQuad qc = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, {0.0f, 0.0f}};
-  float fm = 0.0f;
+  float fm = 0.0f, gx = 0.0f, gy = 0.0f;
   if (qrec && !q64) {  // issued with the moments, used after the FP64 part
     qc = CG ? ld_quad_cg(qrec + child) : qrec[child];
     fm = CG ? __ldcg(&rec[child].m) : rec[child].m;
+    if (ROOT) {  // a level-one child's binary32 offset R - c (level_one_node kept it)
+      gx = rec[child].pad[0];
+      gy = rec[child].pad[1];
+    }
   }
   const int k = o & 3;
   double S = 0.0;
@@ -805,9 +837,7 @@ __device__ __forceinline__ void group_node(unsigned gmask, int gbase, int o, int
   float sx, sy, sz;  // this lane's child: its shift from the node's centre of mass
   if (ROOT) {
     const float hc = pow2f(-(lev + 2));
-    const float gx = narrow(__dsub_rn(c.x, centre_coord(2 * ix + (o & 1), lev + 1)));
-    const float gy = narrow(__dsub_rn(c.y, centre_coord(2 * iy + ((o >> 1) & 1), lev + 1)));
-    const float gz = narrow(__dsub_rn(c.z, centre_coord(2 * iz + ((o >> 2) & 1), lev + 1)));
+    const float gz = qc.pad[0];
     const float dx = (o & 1) ? hc : -hc, dy = (o & 2) ? hc : -hc, dz = (o & 4) ? hc : -hc;
     sx = __fsub_rn(__fadd_rn(dx, gx), narrow(r.ox));
     sy = __fsub_rn(__fadd_rn(dy, gy), narrow(r.oy));
@@ -1073,7 +1103,7 @@ cudaError_t launch_moments(cudaStream_t s, int nb, const int4 *blk, const int *o
                            const int *count, const int *prestart, const void *density, int density_is_fp64, const FieldArgs &fa,
                            int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
                            uint8_t *lvl, double *q64, WalkQuad *qrec, unsigned *flags,
-                           const TopArgs &top) {
+                           const TopArgs &top, cudaEvent_t before_upper) {
   if (density_is_fp64)
     k_blocks<double><<<nb, kBlockThreads, 0, s>>>(nb, blk, orig, count, prestart,
                                                    (const double *)density, fa.L, fa.fid,
@@ -1086,6 +1116,7 @@ cudaError_t launch_moments(cudaStream_t s, int nb, const int4 *blk, const int *o
                                                   qrec, flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (before_upper && (e = cudaStreamWaitEvent(s, before_upper, 0)) != cudaSuccess) return e;
   k_upper_tree<<<grid_for(nb, kUpperBlocks), 8 * kUpperBlocks, 0, s>>>(
       nb, fa.nfields, blk, orig, count, prestart, fa.fid, fa.mmax, fa.inv_theta, n_nodes, mom,
       rec, aux, lvl, q64, qrec, flags, top);

@@ -86,11 +86,17 @@ static_assert(sizeof(WalkQuad) == 32, "quadrupole record must be 32 bytes");
 // warp per group; ticket = k > 0 a persistent grid (as many CTAs as fit on
 // the GPU at once) whose warps take k groups at a time from `counter` (a
 // device word that the launch resets) until all are taken.  0 = defaults.
+// longest = 1: the groups are walked in the tree's walk order (longest walk
+// first, made by bh_autotune); order: that permutation of the groups (group
+// order[i] is the i-th to be walked: taken i-th from the counter, or walked
+// by warp i of a plain grid), or null for the groups' own order.
 struct WalkShape {
   int warps = 0;
   int pairs = 0;
   int ticket = 0;
+  int longest = 0;
   unsigned *counter = nullptr;
+  const unsigned *order = nullptr;
 };
 
 // Top nodes (the cubes above the blocks), by slot = their rank among the
@@ -158,6 +164,12 @@ struct Tree {
   int graph_fp64 = -1;
   double graph_theta = 0.0, graph_G = 0.0;
   WalkShape shape;              // tuned launch shape of the walk (0 = defaults)
+  // walk order of the groups made by bh_autotune, longest walk first, for one
+  // (np = 1) or two (np = 2) target pairs per lane: d_order[np - 1] holds
+  // order_n[np - 1] group indices (0 = none); used while the tree has that
+  // many groups
+  unsigned *d_order[2] = {nullptr, nullptr};
+  int64_t order_n[2] = {0, 0}, order_cap[2] = {0, 0};
   int64_t nb_cap = 0;
   // node arrays (capacity node_cap)
   double4_32a *d_mom = nullptr;
@@ -246,12 +258,14 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
 cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
                             int density_is_fp64, const FieldArgs &fa);
 // Every node's moments: cells and bottom nodes (k_blocks), then the rest of
-// the blocks and the top tree (k_upper_tree), two launches.
+// the blocks and the top tree (k_upper_tree), two launches.  before_upper:
+// an event the second launch waits for (the top-node lists made on another
+// stream), or null.
 cudaError_t launch_moments(cudaStream_t s, int nb, const int4 *blk, const int *orig,
                            const int *count, const int *prestart, const void *density, int density_is_fp64, const FieldArgs &fa,
                            int64_t n_nodes, double4_32a *mom, WalkRec *rec, float2 *aux,
                            uint8_t *lvl, double *q64, WalkQuad *qrec, unsigned *flags,
-                           const TopArgs &top);
+                           const TopArgs &top, cudaEvent_t before_upper = nullptr);
 // Raises the dynamic shared-memory limit of the learned walk (more than 48 KB)
 // on the current device; called once per context, outside any graph capture.
 cudaError_t prepare_learned_kernels();
@@ -384,6 +398,10 @@ struct bh_ctx {
   bh_options opt;
   int device = 0;
   cudaStream_t stream = nullptr;
+  // a second stream of the build: the top nodes' records and child lists are
+  // made on it while k_blocks runs on `stream` (fork / join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   bhg::Tree tree;
   bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
   bhg::MlpTc *d_mlp_tc = nullptr;   // the same network for bh_mlp_eval

@@ -386,7 +386,8 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
 // plain grid is kept.)
 template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kMaxWalkThreads)
-    k_walk_pair(unsigned nunits, const WalkRec *__restrict__ rec,
+    k_walk_pair(unsigned nunits, const unsigned *__restrict__ order,
+                const WalkRec *__restrict__ rec,
                 const WalkQuad *__restrict__ qrec, const int4 *__restrict__ blk,
                 const int *__restrict__ orig, const int4 *__restrict__ fld,
                 const double *__restrict__ invL, const unsigned long long *__restrict__ mmax,
@@ -395,19 +396,22 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
   const int lane = threadIdx.x & 31;
   const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_group<NP, KAHAN, COUNTS, QUAD>(warp, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
+  const unsigned u = order ? order[warp] : warp;
+  walk_group<NP, KAHAN, COUNTS, QUAD>(u, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
                                       n_int, n_test, n_leaf);
 }
 
 // The same walk on a persistent grid: each warp takes `per_ticket`
 // consecutive groups at a time from the work counter (one atomic add by lane
-// 0; no waiting on other warps) until every group is taken.  Consecutive
-// groups are neighbouring octants, so the warps of one CTA tend to walk
-// through the same nodes.
+// 0; no waiting on other warps) until every group is taken.  In the groups'
+// own order, consecutive groups are neighbouring octants; with `order` (the
+// groups sorted by the length of their walks, longest first) the long walks
+// start first and the short ones fill the end, so that fewer warps are left
+// running alone at the end of the launch.
 template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kMaxWalkThreads)
     k_walk_queue(unsigned nunits, unsigned per_ticket, unsigned *__restrict__ counter,
-                 const WalkRec *__restrict__ rec, const WalkQuad *__restrict__ qrec,
+                 const unsigned *__restrict__ order, const WalkRec *__restrict__ rec, const WalkQuad *__restrict__ qrec,
                  const int4 *__restrict__ blk, const int *__restrict__ orig,
                  const int4 *__restrict__ fld, const double *__restrict__ invL,
                  const unsigned long long *__restrict__ mmax, double G, float *__restrict__ out,
@@ -420,9 +424,9 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
     u0 = __shfl_sync(kFull, u0, 0);
     if (u0 >= nunits) return;
     const unsigned u1 = u0 + per_ticket < nunits ? u0 + per_ticket : nunits;
-    for (unsigned u = u0; u < u1; ++u)
-      walk_group<NP, KAHAN, COUNTS, QUAD>(u, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
-                                          n_int, n_test, n_leaf);
+    for (unsigned i = u0; i < u1; ++i)
+      walk_group<NP, KAHAN, COUNTS, QUAD>(order ? order[i] : i, lane, rec, qrec, blk, orig, fld,
+                                          invL, mmax, G, out, n_int, n_test, n_leaf);
   }
 }
 
@@ -558,13 +562,14 @@ cudaError_t go_pair_np(cudaStream_t s, int nb, const WalkRec *rec, const WalkQua
     e = cudaMemsetAsync(shape.counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     k_walk_queue<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
-        nunits, (unsigned)shape.ticket, shape.counter, rec, qrec, blk, orig, fa.fld, fa.invL,
-        fa.mmax, G, (float *)out, ni, nt, nl);
+        nunits, (unsigned)shape.ticket, shape.counter, shape.order, rec, qrec, blk, orig, fa.fld,
+        fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
     return cudaGetLastError();
   }
   const int grid = (int)((nunits + w - 1) / w);
   k_walk_pair<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
-      nunits, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
+      nunits, shape.order, rec, qrec, blk, orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni,
+      nt, nl);
   return cudaGetLastError();
 }
 

@@ -93,8 +93,9 @@ def test_update_density_graph_replay_and_autotune():
         got = s.potential(0.7)
     s.stream.synchronize()
     assert np.array_equal(got.cpu().numpy(), want)
-    w, npairs, ticket = s.autotune(0.7)
+    w, npairs, ticket, longest = s.autotune(0.7)
     assert w in (2, 4, 8, 16) and npairs in (1, 2) and ticket in (0, 1, 2, 4)
+    assert longest in (0, 1)
     out = torch.empty(s.ncells, device="cuda")
     for _ in range(3):                                  # capture once, replay twice
         out.fill_(float("nan"))
@@ -167,14 +168,42 @@ def test_every_walk_shape_gives_identical_potentials(quad):
         assert np.array_equal(out.cpu().numpy(), want), shape
 
 
+@pytest.mark.parametrize("quad", [False, True])
+def test_walk_order_keeps_every_bit(quad):
+    """bh_autotune also sorts the groups by the length of their walks
+    (longest first) for the plain and persistent grids; walking them in that
+    order changes which warp takes which group and when, not what any group
+    computes: the potentials and counts of every shape stay those of the
+    groups' own order, bit for bit."""
+    ws = _fields()
+    nb, level, ijk, lo, ln, rho = mg.concat_fields(ws)
+    d = torch.as_tensor(rho).cuda()
+    s = _solver(quadrupole=quad)
+    s.build_batch(nb, level, ijk, d, lo, ln)
+    with torch.cuda.stream(s.stream):
+        want = s.potential(0.6).cpu().numpy()
+        wi, wt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+    s.autotune(0.6)
+    for shape in SHAPES:
+        s.set_walk_shape(*shape, 1)
+        with torch.cuda.stream(s.stream):
+            got = s.potential(0.6).cpu().numpy()
+            gi, gt = (x.cpu().numpy() for x in s.walk_counts(0.6))
+        assert np.array_equal(got, want), shape
+        assert np.array_equal(gi, wi) and np.array_equal(gt, wt), shape
+
+
 def test_walk_shape_arguments_checked():
     s = _solver()
-    for bad in [(17, 1, 0), (4, 3, 0), (4, 1, 65), (-1, 1, 0)]:
+    for bad in [(17, 1, 0), (4, 3, 0), (4, 1, 65), (-1, 1, 0), (4, 1, 0, 2)]:
         with pytest.raises(B.BHError) as e:
             s.set_walk_shape(*bad)
         assert e.value.status == B.BH_ERR_ARG
+    with pytest.raises(B.BHError) as e:                        # no order before bh_autotune
+        s.set_walk_shape(4, 1, 1, 1)
+    assert e.value.status == B.BH_ERR_STATE
     p = B.Solver(periodic=True)
-    for bad in [(4, 2, 0), (4, 1, 1)]:
+    for bad in [(4, 2, 0), (4, 1, 1), (4, 1, 0, 1)]:
         with pytest.raises(B.BHError):
             p.set_walk_shape(*bad)
     p.set_walk_shape(16, 1, 0)
