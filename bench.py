@@ -1074,6 +1074,8 @@ def main():
                                "potential": float(np.mean(p_walk))},
                  "interactions_per_cell": pi / n, "tests_per_cell": pt / n,
                  "roofline_frac": pflops / (float(np.mean(p_walk)) * 1e-3) / peak,
+                 "roofline_frac_with_kahan": (pflops + 3 * (pi - pc))
+                                             / (float(np.mean(p_walk)) * 1e-3) / peak,
                  "traffic": captured_traffic(w.name, args.plain_theta, "monopole"),
                  "speedup": value / p_value}
         psolver.close()
@@ -1160,7 +1162,10 @@ def main():
             "roofline": {"bound": "alu", "kernel": "bh_potential (s2 prep + walk)",
                          "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": traffic,
-                         "frac_with_kahan": (flops + 3 * n_int) / walk_s / peak,
+                         "frac_with_kahan": (flops + 3 * (n_int - n_cell)) / walk_s / peak,
+                         "kahan_ops": ("3 per node interaction (the compensation of the "
+                                       "compensated sum; a bottom node's 8 cell terms are "
+                                       "summed plainly and folded once, not counted)"),
                          "mufu_bound_ms": n_int / (16 * props.multi_processor_count
                                                    * sm_mhz * 1e6) * 1e3,
                          "traffic_unit": "bytes per walk launch (ncu dram read+write)",

@@ -182,8 +182,9 @@ bh_status bh_sync_status(bh_ctx *ctx);
  * plain grid of one warp per group or a persistent grid (as many CTAs as the
  * GPU holds at once) whose warps take 1, 2 or 4 groups at a time from a work
  * counter; and the groups in their own (Morton) order or longest walk first
- * (the periodic walk: CTA width only) -- and keeps the fastest for later
- * walks.  For the longest-first order it first runs the counting walk at
+ * (the periodic walk: CTA width only) -- each twice, then the four fastest
+ * five times more -- and keeps the fastest for later walks.  For the
+ * longest-first order it first runs the counting walk at
  * this theta and sorts the groups by the interactions and opening tests of
  * their targets (on the host); that order is kept with the context, like
  * the shape, and used while the tree has the same number of groups (a

@@ -851,43 +851,57 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
     }
     const bool ordered = !ctx->opt.periodic;
     if (ordered && (st = make_walk_order(ctx, npairs)) != BH_OK) return st;
-    cudaEvent_t e0, e1;
-    BH_CUDA(cudaEventCreate(&e0));
-    BH_CUDA(cudaEventCreate(&e1));
+    struct Events {  // released on every return
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~Events() {
+        for (cudaEvent_t x : e)
+          if (x) cudaEventDestroy(x);
+      }
+    } ev;
+    BH_CUDA(cudaEventCreate(&ev.e[0]));
+    BH_CUDA(cudaEventCreate(&ev.e[1]));
     const int cand[4] = {2, 4, 8, 16};
     const int tickets[4] = {0, 1, 2, 4};  // plain grid, or persistent with 1/2/4 groups a grab
     const int nticket = ctx->opt.periodic ? 1 : 4;
-    float best = 1e30f;
-    bhg::WalkShape best_s;
-    best_s.warps = 4;
-    best_s.pairs = 1;
-    for (int np = 1; np <= npairs; ++np) {
+    std::vector<bhg::WalkShape> shapes;
+    for (int np = 1; np <= npairs; ++np)
       for (int ti = 0; ti < nticket * 4 * (ordered ? 2 : 1); ++ti) {
-        const int w = cand[ti % 4];
         bhg::WalkShape sh;
-        sh.warps = w;
+        sh.warps = cand[ti % 4];
         sh.pairs = np;
         sh.ticket = tickets[(ti / 4) % nticket];
         sh.longest = ti / (4 * nticket);
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          BH_CUDA(cudaEventRecord(e0, ctx->stream));
-          BH_CUDA(enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
-                               sh));
-          BH_CUDA(cudaEventRecord(e1, ctx->stream));
-          BH_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          BH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          tmin = ms < tmin ? ms : tmin;
-        }
-        if (tmin < best) {
-          best = tmin;
-          best_s = sh;
-        }
+        shapes.push_back(sh);
       }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    // the shortest of `reps` more walks in shape k, into tmin[k]
+    std::vector<float> tmin(shapes.size(), 1e30f);
+    auto time_shape = [&](size_t k, int reps) -> cudaError_t {
+      for (int rep = 0; rep < reps; ++rep) {
+        cudaError_t e = cudaEventRecord(ev.e[0], ctx->stream);
+        if (e == cudaSuccess)
+          e = enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
+                           shapes[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.e[1], ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.e[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]);
+        if (e != cudaSuccess) return e;
+        tmin[k] = ms < tmin[k] ? ms : tmin[k];
+      }
+      return cudaSuccess;
+    };
+    // every shape twice, then the four fastest five times more: the pick
+    // is the shortest walk seen, of shapes that were all timed seven times
+    for (size_t k = 0; k < shapes.size(); ++k) BH_CUDA(time_shape(k, 2));
+    std::vector<size_t> rank(shapes.size());
+    for (size_t k = 0; k < rank.size(); ++k) rank[k] = k;
+    std::stable_sort(rank.begin(), rank.end(), [&](size_t a, size_t b) { return tmin[a] < tmin[b]; });
+    const size_t finalists = rank.size() < 4 ? rank.size() : 4;
+    for (size_t i = 0; i < finalists; ++i) BH_CUDA(time_shape(rank[i], 5));
+    size_t pick = rank[0];
+    for (size_t i = 1; i < finalists; ++i)
+      if (tmin[rank[i]] < tmin[pick]) pick = rank[i];
+    const bhg::WalkShape best_s = shapes[pick];
     t.shape = best_s;
     drop_graph(t);
   }
