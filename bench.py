@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--train-fields", type=int, default=200,
                     help="--workload learned: seeded training fields")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--mlp-gates", default="0.3,0.4,0.5",
+                    help="--workload learned: gates s_min of the network also timed (comma "
+                         "list; empty for none)")
     ap.add_argument("--walk-shape", default=None,
                     help="W,P,T[,L]: the walk's launch shape (warps per CTA, target pairs "
                          "per lane, groups per take; 0 = plain grid; L = 1: the groups longest "
@@ -851,6 +854,34 @@ def learned_arm(args):
                                                  + mesh.ijk.nbytes),
                        "d2h_bytes_per_step": int(h_out.nbytes)}
         s.close()
+    # the gate: the network only for accepted nodes with s = l/d >= s_min
+    gates = [float(g) for g in args.mlp_gates.split(",") if g.strip()] if args.mlp_gates else []
+    gate_sweep = []
+    if gates:
+        s = bh.Solver(learned=True, device=local, stream=stream)
+        s.set_mlp(wts)
+        with torch.cuda.stream(stream):
+            s.build(mesh.level, mesh.ijk, d_rho)
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+        for g in gates:
+            s.set_mlp_gate(g)
+            ts = []
+            with torch.cuda.stream(stream):
+                for k in range(args.warmup + max(5, args.steps // 3)):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.potential(args.theta, 1.0, out=out)
+                    e1.record(stream)
+                    stream.synchronize()
+                    if k >= args.warmup:
+                        ts.append(e0.elapsed_time(e1))
+            phi[f"gate_{g}"] = out.double().cpu().numpy()
+            gate_sweep.append({"s_min": g, "potential_ms": float(np.median(ts)),
+                               "speedup_vs_plain": res["plain"]["phases_ms"]["potential"]
+                               / float(np.median(ts))})
+        s.close()
     L_ = res["learned"]
     walk_s = L_["phases_ms"]["potential"] * 1e-3
     n_node = L_["interactions"] - L_["cell_interactions"]
@@ -866,8 +897,13 @@ def learned_arm(args):
     all_cells = all_cells_error(
         bh, mesh, d_rho, maxlev,
         {"learned_max_rel_vs_direct": phi["learned"], "plain_max_rel_vs_direct": phi["plain"],
-         "plain_same_theta_max_rel_vs_direct": phi["same"]}, dev, stream,
+         "plain_same_theta_max_rel_vs_direct": phi["same"],
+         **{f"gate_{g}_max_rel_vs_direct": phi[f"gate_{g}"] for g in gates}}, dev, stream,
         limit=args.all_cells_limit)
+    if all_cells is not None:
+        for e in gate_sweep:
+            e["max_rel_vs_direct_all_cells"] = all_cells.pop(f"gate_{e['s_min']}_max_rel_vs_direct",
+                                                             None)
     if all_cells is not None:  # (the worst cells go to the oracle in the main arm only)
         all_cells.pop("_worst_cells", None)
         all_cells.pop("_direct_at_worst", None)
@@ -910,6 +946,10 @@ def learned_arm(args):
                           **{k: v for k, v in res["same"].items() if k != "theta"},
                           "speedup": L_["value"] / res["same"]["value"]},
         "accuracy_all_cells": all_cells,
+        "gate_sweep": {"how": "the learned walk with the network only for accepted nodes "
+                              "with s = l/d >= s_min (bh_set_mlp_gate), potential alone, "
+                              "median of the timed walks; speedup against the plain walk's "
+                              "potential at plain_theta", "runs": gate_sweep},
         "clocks": clocks, "e2e": e2e,
         "gpu_launches": 9 * args.steps,
         "cpu_baseline": cpu,

@@ -333,6 +333,15 @@ bh_status bh_mlp_adam(const float *grad, float *w, float *m, float *v, int step,
 bh_status bh_set_mlp(bh_ctx *ctx, const float *w_host);
 bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host);
 
+/* Gate of the learned walk (not in the paper): the network corrects an
+ * accepted internal node only while s = l/|d| >= s_min, since its correction
+ * (M/|d|) s^2 y shrinks with s^2.  Decided in binary32 on the opening test's
+ * d2 (see bh_options.criterion) with a fixed rounding: corrected iff
+ * d2 <= fl(g * g), g = fl(l * fl(1/s_min)); the other accepted nodes keep
+ * their plain term M/|d|.  s_min = 0 (the default) corrects every accepted
+ * internal node.  BH_ERR_ARG unless 0 <= s_min < 1. */
+bh_status bh_set_mlp_gate(bh_ctx *ctx, double s_min);
+
 /* ---- statistics (not in the paper) ---------------------------------------- */
 typedef struct {
   int64_t n_cells;           /* leaf cells of the current tree, all fields (0: no tree) */

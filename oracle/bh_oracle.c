@@ -664,6 +664,7 @@ typedef struct {
   float tf[3];
   double tu[3];
   float inv_theta;
+  float inv_smin;           /* gate: 1/s_min in binary32, +inf for no gate */
   const double *w;          /* MLP weights (walk) or NULL (pair listing) */
   neumaier sum;
   int64_t n_int, n_test;
@@ -671,6 +672,22 @@ typedef struct {
   double *feat, *eps;
   int64_t *node_out;
 } learn_state;
+
+/* The gate of the learned correction (not in the paper): an accepted node's
+ * term gets the network only while s = l/d >= s_min, decided in binary32 on
+ * the opening test's d^2 with the same kind of fixed rounding: corrected iff
+ * d2 <= fl(g * g), g = fl(l * fl(1/s_min)).  s_min = 0 (inv_smin = +inf)
+ * corrects every accepted node. */
+static int gate_f32(const onode *n, const float t[3], float inv_smin) {
+  float l = (float)ldexp(1.0, -n->level);
+  float g = l * inv_smin;
+  float g2 = g * g;
+  float dx = t[0] - (float)n->R[0];
+  float dy = t[1] - (float)n->R[1];
+  float dz = t[2] - (float)n->R[2];
+  float d2 = fmaf(dx, dx, fmaf(dz, dz, dy * dy));
+  return d2 <= g2;
+}
 
 static void walk_learned(learn_state *w, int64_t id) {
   const onode *n = &w->t->node[id];
@@ -687,7 +704,8 @@ static void walk_learned(learn_state *w, int64_t id) {
     pair_features(n, w->tu, x, &s, &mono);
     w->n_int++;
     if (w->w) {
-      nm_add(&w->sum, mono * (1.0 + s * s * mlp_forward(w->w, x)));
+      const double corr = gate_f32(n, w->tf, w->inv_smin) ? s * s * mlp_forward(w->w, x) : 0.0;
+      nm_add(&w->sum, mono * (1.0 + corr));
     } else {
       if (w->np < w->cap) {
         /* exact contribution of the node: its cells form the pre-order range
@@ -730,11 +748,14 @@ int64_t or_learn_pairs(const void *p, double theta, int64_t target, int64_t cap,
   return w.np;
 }
 
-/* Per-cell walk with the learned correction of every accepted node. */
-int or_walk_learned(const void *p, double theta, double G, const double *weights,
+/* Per-cell walk with the learned correction of every accepted node (of
+ * those with s >= s_min when s_min > 0, see gate_f32). */
+int or_walk_learned(const void *p, double theta, double G, const double *weights, double s_min,
                     int64_t ntargets, const int64_t *targets, double *phi, int nthreads) {
   const otree *t = (const otree *)p;
-  if (!check_theta(theta) || !isfinite(G) || !t->have_quad || !weights) return OR_ERR_ARG;
+  if (!check_theta(theta) || !isfinite(G) || !t->have_quad || !weights || !(s_min >= 0.0) ||
+      !(s_min < 1.0))
+    return OR_ERR_ARG;
   for (int64_t q = 0; q < ntargets; ++q)
     if (targets[q] < 0 || targets[q] >= (int64_t)t->nblocks * 512) return OR_ERR_ARG;
   float inv_theta = (float)(1.0 / theta);
@@ -749,6 +770,7 @@ int or_walk_learned(const void *p, double theta, double G, const double *weights
     w.t = t;
     w.self = t->leaf_of_cell[targets[q]];
     w.inv_theta = inv_theta;
+    w.inv_smin = s_min > 0.0 ? (float)(1.0 / s_min) : INFINITY;
     w.w = weights;
     target_position(t, w.self, w.tu, w.tf);
     walk_learned(&w, 0);

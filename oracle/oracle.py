@@ -73,7 +73,7 @@ def _load():
             lib.or_max_threads.restype = i32
             lib.or_learn_pairs.argtypes = [P, dbl, i64, i64, P, P, P]
             lib.or_learn_pairs.restype = i64
-            lib.or_walk_learned.argtypes = [P, dbl, dbl, P, i64, P, P, i32]
+            lib.or_walk_learned.argtypes = [P, dbl, dbl, P, dbl, i64, P, P, i32]
             lib.or_walk_learned.restype = i32
             lib.or_ewald_sum.argtypes = [i64, P, dbl, i32, i32, P]
             lib.or_ewald_sum.restype = i32
@@ -222,15 +222,16 @@ class Tree:
         return f[:n], e[:n], nd[:n]
 
     def walk_learned(self, theta: float, weights, G: float = 1.0, targets=None,
-                     threads: int = 0) -> np.ndarray:
+                     threads: int = 0, s_min: float = 0.0) -> np.ndarray:
         """Per-cell walk with each accepted node's term times (1 + s^2 MLP(x));
-        weights: flat FP64 vector in the layout of mlp_unflatten."""
+        weights: flat FP64 vector in the layout of mlp_unflatten.  s_min > 0:
+        only nodes with s = l/d >= s_min get the network (gate_f32)."""
         self.quadrupoles()
         t = self._targets(targets)
         w = np.ascontiguousarray(weights, dtype=np.float64)
         phi = np.empty(t.shape[0])
-        st = _load().or_walk_learned(self._h, float(theta), float(G), _ptr(w), t.shape[0],
-                                     _ptr(t), _ptr(phi), int(threads))
+        st = _load().or_walk_learned(self._h, float(theta), float(G), _ptr(w), float(s_min),
+                                     t.shape[0], _ptr(t), _ptr(phi), int(threads))
         if st != OR_OK:
             raise OracleError(st, "or_walk_learned")
         return phi

@@ -27,7 +27,8 @@ EXPORTED = ("bh_default_options", "bh_create", "bh_build", "bh_build_batch",
             "bh_potential", "bh_walk_counts", "bh_tree_size", "bh_export_nodes",
             "bh_export_quadrupoles", "bh_solve_host", "bh_solve_noalloc", "bh_learn_pairs",
             "bh_learn_targets",
-            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats",
+            "bh_mlp_grad", "bh_mlp_adam", "bh_set_mlp", "bh_get_mlp", "bh_set_mlp_gate",
+            "bh_mlp_eval", "bh_stats",
             "bh_set_ewald", "bh_ewald_eval", "bh_last_error", "bh_destroy")
 
 
@@ -96,6 +97,7 @@ def load(build_if_needed: bool = True):
         lib.bh_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, P]
         lib.bh_set_mlp.argtypes = [P, P]
         lib.bh_get_mlp.argtypes = [P, P]
+        lib.bh_set_mlp_gate.argtypes = [P, D]
         lib.bh_stats.argtypes = [P, ctypes.POINTER(bh_stats_t)]
         lib.bh_mlp_eval.argtypes = [P, ctypes.c_int64, P, P]
         lib.bh_set_ewald.argtypes = [P, I, I]
@@ -111,7 +113,8 @@ def load(build_if_needed: bool = True):
                      "bh_tree_size", "bh_export_nodes", "bh_export_quadrupoles", "bh_solve_host",
                      "bh_solve_noalloc", "bh_learn_pairs", "bh_learn_targets", "bh_mlp_grad",
                      "bh_mlp_adam",
-                     "bh_set_mlp", "bh_get_mlp", "bh_mlp_eval", "bh_stats", "bh_set_ewald",
+                     "bh_set_mlp", "bh_get_mlp", "bh_set_mlp_gate", "bh_mlp_eval", "bh_stats",
+                     "bh_set_ewald",
                      "bh_ewald_eval"):
             getattr(lib, name).restype = I
         _lib = lib
@@ -351,6 +354,10 @@ def bh_set_mlp(ctx, w_host: np.ndarray) -> None:
     _check(ctx, load().bh_set_mlp(ctx, _np_ptr(w)), "bh_set_mlp")
 
 
+def bh_set_mlp_gate(ctx, s_min: float) -> None:
+    _check(ctx, load().bh_set_mlp_gate(ctx, float(s_min)), "bh_set_mlp_gate")
+
+
 def bh_get_mlp(ctx) -> np.ndarray:
     w = np.empty(MLP_NW, dtype=np.float32)
     _check(ctx, load().bh_get_mlp(ctx, _np_ptr(w)), "bh_get_mlp")
@@ -520,6 +527,10 @@ class Solver:
 
     def set_mlp(self, w):
         bh_set_mlp(self._ctx, w)
+
+    def set_mlp_gate(self, s_min: float):
+        """Network only for accepted nodes with s = l/d >= s_min (0: all)."""
+        bh_set_mlp_gate(self._ctx, s_min)
 
     def set_ewald(self, n_grid: int = 64, n_series: int = 3):
         """Recompute the periodic walk's Ewald table (grid, series range)."""

@@ -35,6 +35,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <limits>
 #include <vector>
 
 #include "bhgrav.h"  // -I include
@@ -404,6 +405,7 @@ struct bh_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   bhg::Tree tree;
   bhg::MlpDev *d_mlp = nullptr;  // learned correction, set by bh_set_mlp
+  double mlp_s_min = 0.0;        // its gate (bh_set_mlp_gate): no network below s = l/d
   bhg::MlpTc *d_mlp_tc = nullptr;   // the same network for bh_mlp_eval
   unsigned *d_tc_flag = nullptr;    // time-out flag of bh_mlp_eval
   unsigned char *d_ewald = nullptr; // periodic boundaries: the Ewald table
@@ -420,6 +422,12 @@ struct bh_ctx {
 };
 
 namespace bhg {
+// The gate of the learned walks as the kernels take it: fl32(1/s_min), or
+// +inf (every accepted internal node corrected) for s_min = 0.
+inline float learned_inv_smin(const bh_ctx *ctx) {
+  return ctx->mlp_s_min > 0.0 ? (float)(1.0 / ctx->mlp_s_min)
+                              : std::numeric_limits<float>::infinity();
+}
 // Records a one-line reason on the context and returns st.
 bh_status ctx_fail(bh_ctx *c, bh_status st, const char *fmt, ...);
 // Checks theta and the tree, and prepares the opening radii for theta.

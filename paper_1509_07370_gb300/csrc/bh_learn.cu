@@ -484,4 +484,13 @@ bh_status bh_get_mlp(const bh_ctx *ctx, float *w_host) {
   return BH_OK;
 }
 
+bh_status bh_set_mlp_gate(bh_ctx *ctx, double s_min) {
+  if (!ctx) return BH_ERR_ARG;
+  ctx->err[0] = 0;
+  if (!(s_min >= 0.0) || !(s_min < 1.0))
+    return ctx_fail(ctx, BH_ERR_ARG, "bh_set_mlp_gate: s_min must lie in [0, 1)");
+  ctx->mlp_s_min = s_min;
+  return BH_OK;
+}
+
 }  // extern "C"

@@ -2,7 +2,10 @@
 // the learned residual correction added for every accepted internal node
 // (features and network in bhgrav.h; the correction is not in the paper).
 //
-// Every (target, accepted internal node) pair is one row of the network.  A
+// Every (target, accepted internal node) pair is one row of the network (with
+// the gate of bh_set_mlp_gate: only pairs with s = l/d >= s_min, decided in
+// binary32 on the opening test's d^2: d2 <= fl(g * g), g = fl(l fl(1/s_min));
+// inv_smin = +inf corrects every pair).  A
 // warp queues its rows in shared memory as it walks: the pair's ten features
 // as one bf16 row, the coefficient c = M s^2 / d and the target (0..63).  When
 // 64 or more rows are queued, the warp evaluates the largest multiple of 16 of
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kLWarps * 32, 3)
                    const int4 *__restrict__ blk, const int *__restrict__ orig,
                    const int4 *__restrict__ fld, const double *__restrict__ invL,
                    const unsigned long long *__restrict__ mmax, double G,
-                   const MlpDev *__restrict__ mlp, float *__restrict__ out) {
+                   const MlpDev *__restrict__ mlp, float inv_smin, float *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LearnSmem &S = *reinterpret_cast<LearnSmem *>(smem_raw);
   {
@@ -215,10 +218,13 @@ __global__ void __launch_bounds__(kLWarps * 32, 3)
       ra = take_a ? ra : 0.0f;
       rb = take_b ? rb : 0.0f;
       accumulate2<KAHAN>(sum, comp, mul2(q2, pk(ra, rb)));
-      if (s2 > 0.0f) {  // internal node: queue the accepted pairs
-        const unsigned ba = __ballot_sync(kFull, take_a), bb = __ballot_sync(kFull, take_b);
+      if (s2 > 0.0f) {  // internal node: queue the accepted pairs the gate lets through
+        const float2 lv = aux[node];  // node side, delta
+        const float g = __fmul_rn(lv.x, inv_smin);
+        const float g2 = __fmul_rn(g, g);
+        const bool qa = take_a && d2a <= g2, qb = take_b && d2b <= g2;
+        const unsigned ba = __ballot_sync(kFull, qa), bb = __ballot_sync(kFull, qb);
         if (ba | bb) {
-          const float2 lv = aux[node];  // node side, delta
           const WalkQuad q = qrec[node];
           float mf, mf2;
           upk(q2, mf, mf2);
@@ -229,12 +235,12 @@ __global__ void __launch_bounds__(kLWarps * 32, 3)
           float dxa, dxb;
           upk(dx2, dxa, dxb);
           int row = count + __popc(ba & lower) + __popc(bb & lower);
-          if (take_a) {
+          if (qa) {
             const float s = lv.x * ra;
             queue_row(Q, row++, dxa, dy, dz, ra, lv.x, dl, inv_ml2, qf, q, mf * ra * s * s,
                       2 * lane);
           }
-          if (take_b) {
+          if (qb) {
             const float s = lv.x * rb;
             queue_row(Q, row, dxb, dy, dz, rb, lv.x, dl, inv_ml2, qf, q, mf * rb * s * s,
                       2 * lane + 1);
@@ -312,16 +318,15 @@ cudaError_t launch_walk_learned(cudaStream_t s, bh_ctx *ctx, double G, void *out
   const int smem = (int)sizeof(LearnSmem);  // limit set by prepare_learned_kernels
   const bool kahan = ctx->opt.kahan != 0;
   const unsigned grid = (nunits + kLWarps - 1) / kLWarps;
+  const float inv_smin = learned_inv_smin(ctx);
   if (kahan)
     k_walk_learned<true><<<grid, kLWarps * 32, smem, s>>>(
         nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
-        ctx->d_mlp,
-        (float *)out);
+        ctx->d_mlp, inv_smin, (float *)out);
   else
     k_walk_learned<false><<<grid, kLWarps * 32, smem, s>>>(
         nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
-        ctx->d_mlp,
-        (float *)out);
+        ctx->d_mlp, inv_smin, (float *)out);
   return cudaGetLastError();
 }
 

@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(kTWarps * 32, 4)
                       const int4 *__restrict__ blk, const int *__restrict__ orig,
                       const int4 *__restrict__ fld, const double *__restrict__ invL,
                       const unsigned long long *__restrict__ mmax, double G,
-                      const MlpTc *__restrict__ wts, float *__restrict__ out, unsigned *flags) {
+                      const MlpTc *__restrict__ wts, float inv_smin, float *__restrict__ out,
+                      unsigned *flags) {
   extern __shared__ unsigned char smem_raw[];
   TcWalkSmem &S = *reinterpret_cast<TcWalkSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -140,10 +141,13 @@ __global__ void __launch_bounds__(kTWarps * 32, 4)
       ra = take_a ? ra : 0.0f;
       rb = take_b ? rb : 0.0f;
       accumulate2<KAHAN>(sum, comp, mul2(q2, pk(ra, rb)));
-      if (s2 > 0.0f) {  // internal node: queue the accepted pairs
-        const unsigned ba = __ballot_sync(kFull, take_a), bb = __ballot_sync(kFull, take_b);
+      if (s2 > 0.0f) {  // internal node: queue the accepted pairs the gate lets through
+        const float2 lv = aux[node];
+        const float g = __fmul_rn(lv.x, inv_smin);  // the gate, as in k_walk_learned
+        const float g2 = __fmul_rn(g, g);
+        const bool qa = take_a && d2a <= g2, qb = take_b && d2b <= g2;
+        const unsigned ba = __ballot_sync(kFull, qa), bb = __ballot_sync(kFull, qb);
         if (ba | bb) {
-          const float2 lv = aux[node];
           const WalkQuad q = qrec[node];
           float mf, mf2;
           upk(q2, mf, mf2);
@@ -154,12 +158,12 @@ __global__ void __launch_bounds__(kTWarps * 32, 4)
           float dxa, dxb;
           upk(dx2, dxa, dxb);
           int k = count + __popc(ba & lower) + __popc(bb & lower);
-          if (take_a) {
+          if (qa) {
             const float s = lv.x * ra;
             tc_queue_row(Q, (head + k++) & (kTRing - 1), dxa, dy, dz, ra, lv.x, dl, inv_ml2, qf,
                          q, mf * ra * s * s, 2 * lane);
           }
-          if (take_b) {
+          if (qb) {
             const float s = lv.x * rb;
             tc_queue_row(Q, (head + k) & (kTRing - 1), dxb, dy, dz, rb, lv.x, dl, inv_ml2, qf, q,
                          mf * rb * s * s, 2 * lane + 1);
@@ -310,14 +314,15 @@ cudaError_t launch_walk_learned_tc(cudaStream_t s, bh_ctx *ctx, double G, void *
   const Tree &t = ctx->tree;
   const unsigned nunits = (unsigned)t.nb * 8u;
   const unsigned grid = (nunits + kTWarps - 1) / kTWarps;
+  const float inv_smin = learned_inv_smin(ctx);
   if (ctx->opt.kahan)
     k_walk_learned_tc<true><<<grid, kTWarps * 32, kTcWalkSmem, s>>>(
         nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
-        ctx->d_mlp_tc, (float *)out, t.d_flags);
+        ctx->d_mlp_tc, inv_smin, (float *)out, t.d_flags);
   else
     k_walk_learned_tc<false><<<grid, kTWarps * 32, kTcWalkSmem, s>>>(
         nunits, t.d_rec, t.d_qrec, t.d_aux, t.d_blk, t.d_orig, t.d_fld, t.d_invL, t.d_mmax, G,
-        ctx->d_mlp_tc, (float *)out, t.d_flags);
+        ctx->d_mlp_tc, inv_smin, (float *)out, t.d_flags);
   return cudaGetLastError();
 }
 

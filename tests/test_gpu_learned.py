@@ -101,6 +101,44 @@ def test_learned_walk_matches_oracle():
     assert np.all(np.abs(phi[tg] - learned) <= 0.02 * corr.max() + 1e-5 * np.abs(learned))
 
 
+def test_gated_learned_walk_matches_oracle():
+    """The gate (network only for accepted nodes with s = l/d >= s_min,
+    decided in binary32 on the opening test's d^2 on both sides): at s_min =
+    0.4 the learned walk, in both tensor-core forms, against the oracle's
+    gated walk with the same bf16 weights (the bar of the ungated test); at
+    s_min = 0.999 no accepted node is corrected (s < theta < 1), which is the
+    oracle's plain monopole walk within the binary32 bar; bad gates are
+    refused."""
+    w = _field()
+    wts = L.init_weights(3)
+    t = O.Tree.from_workload(w)
+    tg = np.random.default_rng(5).choice(w.ncells, 600, replace=False)
+    mono = t.walk(0.8, targets=tg)[0]
+    rho = torch.as_tensor(w.density.reshape(-1)).cuda()
+    for mode in (1, 2):
+        s = B.Solver(learned=mode)
+        s.build(w.mesh.level, w.mesh.ijk, rho)
+        s.set_mlp(wts)
+        wb = s.get_mlp().astype(np.float64)
+        s.set_mlp_gate(0.4)
+        phi = s.potential(0.8).cpu().numpy()
+        s.sync_status()
+        gated = t.walk_learned(0.8, wb, targets=tg, s_min=0.4)
+        full = t.walk_learned(0.8, wb, targets=tg)
+        corr = np.abs(gated - mono)
+        assert corr.max() > 1e-6 * np.abs(mono).max()       # some pairs pass the gate
+        assert np.any(np.abs(full - gated) > 1e-9 * np.abs(mono))  # and some do not
+        assert np.all(np.abs(phi[tg] - gated) <= 0.02 * corr.max() + 1e-5 * np.abs(gated))
+        s.set_mlp_gate(0.999)
+        phi = s.potential(0.8).cpu().numpy()
+        assert np.max(np.abs(phi[tg] / mono - 1.0)) <= 1e-5
+        for bad in (-0.1, 1.0, float("nan")):
+            with pytest.raises(B.BHError) as e:
+                s.set_mlp_gate(bad)
+            assert e.value.status == B.BH_ERR_ARG
+        s.close()
+
+
 def test_trained_network_beats_the_plain_walk_at_the_same_theta():
     xs, zs = [], []
     for i in range(24):

@@ -486,6 +486,47 @@ def test_learned_walk_with_zero_network_is_the_monopole_walk(tiny):
     assert np.all(np.abs(lw) > np.abs(mono))      # every node term grows by s^2/2
 
 
+def test_learned_gate_corrects_exactly_the_pairs_with_s_at_least_s_min(tiny):
+    """The gate (no network for accepted nodes with s = l/d < s_min): s_min
+    = 0 is the ungated walk; s_min near 1 gates every accepted node off (an
+    accepted node has d > l/theta >= l, so s < 1), which is the monopole walk;
+    in between, with a constant network (y = 1/2 for every pair), the
+    correction is (M/d) s^2/2 summed over exactly the accepted pairs with s
+    >= s_min, which the pair listing gives independently of the walk."""
+    m, rho = tiny["diag_refined"]
+    t = _tree(m, rho)
+    tg = np.arange(0, m.ncells, 151)
+    rng = np.random.default_rng(4)
+    w = rng.normal(0, 0.2, O.MLP_NW)
+    assert np.array_equal(t.walk_learned(0.8, w, targets=tg, s_min=0.0),
+                          t.walk_learned(0.8, w, targets=tg))
+    mono = t.walk(0.8, targets=tg)[0]
+    assert np.allclose(t.walk_learned(0.8, w, targets=tg, s_min=0.999), mono, rtol=1e-14, atol=0)
+    e = t.export()
+    u, _ = _cell_geometry(m)
+    c = np.zeros(O.MLP_NW)
+    c[-1] = 0.5
+    s_all = np.concatenate([t.learn_pairs(0.8, q)[0][:, 3] for q in tg])
+    # s_min halfway across the widest relative gap between distinct s values
+    # in the middle 80 % of them: no pair lies near the boundary, where the
+    # gate's binary32 d^2 (from binary32 centres of mass) and the listing's
+    # FP64 s could disagree (relative differences of order 1e-6)
+    sv = np.unique(s_all)
+    lo, hi = len(sv) // 10, 9 * len(sv) // 10
+    k = lo + int(np.argmax(np.diff(sv[lo:hi + 1]) / sv[lo:hi]))
+    s_min = 0.5 * (sv[k] + sv[k + 1])
+    gap = np.min(np.abs(s_all - s_min)) / s_min
+    assert gap > 1e-4, gap
+    got = t.walk_learned(0.8, c, targets=tg, s_min=s_min)
+    for k, q in enumerate(tg):
+        f, _, nodes = t.learn_pairs(0.8, q)
+        mn = e["M"][nodes] / np.linalg.norm(u[q] - e["R"][nodes], axis=1)
+        on = f[:, 3] >= s_min
+        want = mono[k] - np.sum(mn[on] * 0.5 * f[on, 3] ** 2)   # Phi = -G (sum), G = 1
+        assert abs(got[k] / want - 1.0) < 1e-12, (q, got[k], want)
+    assert np.any(got != mono)
+
+
 def test_exact_residuals_turn_the_walk_into_the_direct_sum(tiny):
     """walk + sum over accepted nodes of (M/d) eps = direct sum, per target:
     eps is each node's exact error against its monopole."""
