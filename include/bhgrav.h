@@ -184,11 +184,11 @@ bh_status bh_sync_status(bh_ctx *ctx);
  * counter; and the groups in their own (Morton) order or longest walk first
  * (the periodic walk: CTA width only) -- each twice, then the four fastest
  * five times more -- and keeps the fastest for later walks.  For the
- * longest-first order it first runs the counting walk at
- * this theta and sorts the groups by the interactions and opening tests of
- * their targets (on the host); that order is kept with the context, like
- * the shape, and used while the tree has the same number of groups (a
- * permutation of the groups: it can only change the speed).  All shapes
+ * longest-first order it first walks the tree once at this theta on the
+ * persistent grid, recording the SM clock cycles of every group's walk, and
+ * sorts the groups by them (on the host); that order is kept with the
+ * context, like the shape, and used while the tree has the same number of
+ * groups (a permutation of the groups: it can only change the speed).  All shapes
  * give bit-identical potentials.  shape (may be NULL) receives four ints:
  * {warps per CTA, target pairs per lane, groups per take (0 = plain grid),
  * longest first (0/1)}; all 0 for walk modes with a fixed launch shape.

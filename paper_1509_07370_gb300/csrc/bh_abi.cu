@@ -762,58 +762,43 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
 }
 
 // The walk order of the groups for one and for two target pairs per lane,
-// longest walk first: a group's cost is the sum over its targets of their
-// interactions and opening tests, from the counting walk at the prepared
-// theta (the decisions of every binary32 per-cell walk).  The persistent
-// walk then starts the long walks first and ends with the short ones, and
-// the plain grid's CTAs (issued in index order) do the same.  Host side:
-// the counts come back, the groups are sorted (stable, so equal costs keep
-// their Morton order) and the order goes up; only bh_autotune does this.
+// longest walk first: one walk of the tree at the prepared theta on the
+// persistent grid (4-warp CTAs, one group per take) records the SM clock
+// cycles of each group's walk, under the load of a whole launch; the groups
+// are sorted by them on the host (stable, so equal times keep their Morton
+// order) and the order goes up.  The persistent walk then starts the long
+// walks first and ends with the short ones, and the plain grid's CTAs
+// (issued in index order) do the same.  Only bh_autotune does this; the
+// potentials it writes to the scratch output are not used.
 static bh_status make_walk_order(bh_ctx *ctx, int npairs) {
   bhg::Tree &t = ctx->tree;
-  const int64_t ncell = (int64_t)t.nb * bhg::kCellsPerBlock;
-  int32_t *d_cnt = nullptr;
-  BH_CUDA(bhg::dev_malloc(&d_cnt, 2 * (size_t)ncell * sizeof(int32_t)));
-  bhg::WalkShape plain;
-  cudaError_t e = enqueue_walk(ctx, ctx->stream, 0.0, nullptr, d_cnt, d_cnt + ncell, nullptr,
-                               plain);
-  std::vector<int32_t> cnt;
-  std::vector<int> orig(t.nb);
-  try {
-    cnt.resize(2 * (size_t)ncell);
-  } catch (const std::bad_alloc &) {
-    release(d_cnt);
-    return fail(ctx, BH_ERR_OOM, "bh_autotune: no host memory for the walk counts");
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(cnt.data(), d_cnt, 2 * (size_t)ncell * sizeof(int32_t),
-                        cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(orig.data(), t.d_orig, (size_t)t.nb * sizeof(int), cudaMemcpyDeviceToHost,
-                        ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  release(d_cnt);
-  BH_CUDA(e);
-  // work of each target cell (caller layout) by its octant of its sorted block
-  std::vector<int64_t> oct((size_t)t.nb * 8, 0);
-  for (int p = 0; p < t.nb; ++p) {
-    const int64_t base = (int64_t)orig[p] * bhg::kCellsPerBlock;
-    for (int m = 0; m < bhg::kCellsPerBlock; ++m) {
-      const int cx = (int)bhg::compact3(m), cy = (int)bhg::compact3(m >> 1),
-                cz = (int)bhg::compact3(m >> 2);
-      const int64_t c = base + cz * 64 + cy * 8 + cx;
-      oct[(size_t)p * 8 + (m >> 6)] += (int64_t)cnt[c] + cnt[ncell + c];
-    }
-  }
   for (int np = 1; np <= npairs; ++np) {
     const int64_t groups = (int64_t)t.nb * (8 / np);
-    std::vector<int64_t> cost(groups, 0);
-    for (int64_t g = 0; g < groups; ++g)
-      for (int k = 0; k < np; ++k) cost[g] += oct[(size_t)(g * np + k)];
+    std::vector<unsigned long long> cyc;
+    try {
+      cyc.resize(groups);
+    } catch (const std::bad_alloc &) {
+      return fail(ctx, BH_ERR_OOM, "bh_autotune: no host memory for the group times");
+    }
+    unsigned long long *d_cyc = nullptr;
+    BH_CUDA(bhg::dev_malloc(&d_cyc, (size_t)groups * sizeof(unsigned long long)));
+    bhg::WalkShape sh;
+    sh.warps = 4;
+    sh.pairs = np;
+    sh.ticket = 1;
+    sh.cycles = d_cyc;
+    cudaError_t e = enqueue_walk(ctx, ctx->stream, 1.0, t.d_stage_out, nullptr, nullptr, nullptr,
+                                 sh);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cyc.data(), d_cyc, (size_t)groups * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    release(d_cyc);
+    BH_CUDA(e);
     std::vector<unsigned> order(groups);
     for (int64_t g = 0; g < groups; ++g) order[g] = (unsigned)g;
     std::stable_sort(order.begin(), order.end(),
-                     [&](unsigned a, unsigned b) { return cost[a] > cost[b]; });
+                     [&](unsigned a, unsigned b) { return cyc[a] > cyc[b]; });
     unsigned *&d = t.d_order[np - 1];
     if (t.order_cap[np - 1] < groups) {
       release(d);

@@ -90,7 +90,9 @@ static_assert(sizeof(WalkQuad) == 32, "quadrupole record must be 32 bytes");
 // longest = 1: the groups are walked in the tree's walk order (longest walk
 // first, made by bh_autotune); order: that permutation of the groups (group
 // order[i] is the i-th to be walked: taken i-th from the counter, or walked
-// by warp i of a plain grid), or null for the groups' own order.
+// by warp i of a plain grid), or null for the groups' own order.  cycles
+// (persistent grid only, else null): receives the SM clock cycles each
+// group's walk took, per group.
 struct WalkShape {
   int warps = 0;
   int pairs = 0;
@@ -98,6 +100,7 @@ struct WalkShape {
   int longest = 0;
   unsigned *counter = nullptr;
   const unsigned *order = nullptr;
+  unsigned long long *cycles = nullptr;
 };
 
 // Top nodes (the cubes above the blocks), by slot = their rank among the

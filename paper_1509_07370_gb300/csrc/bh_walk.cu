@@ -405,13 +405,15 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
 // consecutive groups at a time from the work counter (one atomic add by lane
 // 0; no waiting on other warps) until every group is taken.  In the groups'
 // own order, consecutive groups are neighbouring octants; with `order` (the
-// groups sorted by the length of their walks, longest first) the long walks
+// groups sorted by the time of their walks, longest first) the long walks
 // start first and the short ones fill the end, so that fewer warps are left
-// running alone at the end of the launch.
+// running alone at the end of the launch.  cycles (or null): the SM clock
+// cycles of each group's walk, the measurement that order is made from.
 template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kMaxWalkThreads)
     k_walk_queue(unsigned nunits, unsigned per_ticket, unsigned *__restrict__ counter,
-                 const unsigned *__restrict__ order, const WalkRec *__restrict__ rec, const WalkQuad *__restrict__ qrec,
+                 const unsigned *__restrict__ order, unsigned long long *__restrict__ cycles,
+                 const WalkRec *__restrict__ rec, const WalkQuad *__restrict__ qrec,
                  const int4 *__restrict__ blk, const int *__restrict__ orig,
                  const int4 *__restrict__ fld, const double *__restrict__ invL,
                  const unsigned long long *__restrict__ mmax, double G, float *__restrict__ out,
@@ -424,9 +426,13 @@ __global__ void __launch_bounds__(kMaxWalkThreads)
     u0 = __shfl_sync(kFull, u0, 0);
     if (u0 >= nunits) return;
     const unsigned u1 = u0 + per_ticket < nunits ? u0 + per_ticket : nunits;
-    for (unsigned i = u0; i < u1; ++i)
-      walk_group<NP, KAHAN, COUNTS, QUAD>(order ? order[i] : i, lane, rec, qrec, blk, orig, fld,
-                                          invL, mmax, G, out, n_int, n_test, n_leaf);
+    for (unsigned i = u0; i < u1; ++i) {
+      const unsigned u = order ? order[i] : i;
+      const long long c0 = cycles ? clock64() : 0;
+      walk_group<NP, KAHAN, COUNTS, QUAD>(u, lane, rec, qrec, blk, orig, fld, invL, mmax, G, out,
+                                          n_int, n_test, n_leaf);
+      if (cycles && lane == 0) cycles[u] = (unsigned long long)(clock64() - c0);
+    }
   }
 }
 
@@ -562,8 +568,8 @@ cudaError_t go_pair_np(cudaStream_t s, int nb, const WalkRec *rec, const WalkQua
     e = cudaMemsetAsync(shape.counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     k_walk_queue<NP, KAHAN, COUNTS, QUAD><<<grid, 32 * w, 0, s>>>(
-        nunits, (unsigned)shape.ticket, shape.counter, shape.order, rec, qrec, blk, orig, fa.fld,
-        fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
+        nunits, (unsigned)shape.ticket, shape.counter, shape.order, shape.cycles, rec, qrec, blk,
+        orig, fa.fld, fa.invL, fa.mmax, G, (float *)out, ni, nt, nl);
     return cudaGetLastError();
   }
   const int grid = (int)((nunits + w - 1) / w);
