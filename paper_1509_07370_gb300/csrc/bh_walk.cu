@@ -4,10 +4,11 @@
 // an all() vote on the opening test (Sec. 3.3).  This walk needs no stack:
 // nodes are stored in pre-order, so a node's first child is the next node and
 // its subtree ends at its skip index.  Every target cell keeps `next`, the
-// first node it still has to visit (0 = the root at the start).  At each step
-// the warp takes the smallest `next` over its lanes (one __reduce_min_sync),
-// all lanes load that node (one broadcast 256-bit load), and the targets whose
-// `next` equals it apply the opening test of Eq. 4:
+// first node it still has to visit (0 = the root at the start).  In the
+// one-target-per-lane walk (k_walk_scalar) the warp takes the smallest `next`
+// over its lanes at each step (one __reduce_min_sync), all lanes load that
+// node (one broadcast load), and the targets whose `next` equals it apply the
+// opening test of Eq. 4:
 //   accepted -> add M / d, next = skip (the whole subtree is done)
 //   opened   -> next = node + 1 (descend into the first child)
 // Cells carry s2 = 0: the test accepts every other cell (d2 > 0) and rejects
@@ -17,15 +18,20 @@
 // the per-cell result of the recursive definition; targets whose `next` lies
 // further ahead wait (masked) for the warp to get there.  `next` only grows,
 // so a walk ends after at most n_nodes steps.  With the warp vote (paper mode)
-// all lanes share `next`.
+// all lanes share `next`.  The per-cell pair walk (walk_group) takes the same
+// decisions in two modes that need no reduction: one vote per node while all
+// targets sit at the same node, a lazy per-target `next` inside a subtree
+// they disagree on.
 //
 // Work layout.
-//  * Per-cell binary32 walk (the default, k_walk_pair): one warp per 4x4x4
-//    octant of a block (64 cells, local Morton indices 64o .. 64o+63); lane l
-//    owns the two x-neighbours 64o+2l and 64o+2l+1.  They share ty, tz and
-//    so dy, dz; their dx, d2, 1/d products and Kahan sums run as packed
-//    f32x2 operations (two binary32 results per instruction, each rounded as
-//    its scalar counterpart).  A CTA of 8 warps is one whole block.
+//  * Per-cell binary32 walk (the default, k_walk_pair / k_walk_queue): one
+//    warp per 4x4x4 octant of a block (64 cells, local Morton indices 64o ..
+//    64o+63), lane l owning the two x-neighbours 64o+2l and 64o+2l+1, or per
+//    8x4x4 slab (128 cells, two such pairs per lane).  A lane's targets share
+//    ty, tz and so dy, dz; their dx, d2, 1/d products and Kahan sums run as
+//    packed f32x2 operations (two binary32 results per instruction, each
+//    rounded as its scalar counterpart).  CTAs of 2 to 16 warps, on a plain
+//    grid or a persistent one fed by a work counter (the launch shape).
 //  * binary64 interactions and the paper's warp vote (k_walk_scalar): one
 //    warp per 32-cell brick (4x4x2, local Morton 32q .. 32q+31), one target
 //    per lane, as the paper groups its cells (Sec. 3.1.1, Sec. 3.3).
@@ -38,7 +44,7 @@
 namespace bhg {
 namespace {
 
-constexpr int kWalkThreads = 256;               // default CTA: 8 warps = one block
+constexpr int kWalkThreads = 256;               // CTA of the scalar walk: 8 bricks = half a block
 constexpr int kWarpsPerCta = kWalkThreads / 32;
 constexpr int kMaxWalkThreads = 512;            // largest tunable CTA
 // Default launch shape of the per-cell walk (the fastest on GB300 for the
@@ -380,10 +386,10 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
   }
 }
 
-// One warp per target group (8 / NP groups per block).  (A
-// persistent SM-affine schedule with work stealing raised the L1 hit rate
-// from 44 % to 57 % but ran 8 % slower on GB300, so the hardware schedule of a
-// plain grid is kept.)
+// One warp per target group (8 / NP groups per block), group order[warp] when
+// an order is given.  (Schedules that keep an SM's warps on neighbouring
+// octants -- SM- or CTA-affine ranges with stealing -- share more of the near
+// field in L1 but ran 2-8 % slower on GB300.)
 template <int NP, bool KAHAN, bool COUNTS, bool QUAD>
 __global__ void __launch_bounds__(kMaxWalkThreads)
     k_walk_pair(unsigned nunits, const unsigned *__restrict__ order,
