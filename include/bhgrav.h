@@ -253,10 +253,13 @@ bh_status bh_export_quadrupoles(const bh_ctx *ctx, double *Q);
 
 /* One-call form for callers whose data live in HOST memory: copies the
  * density (float or double per density_is_fp64) to the device, builds the
- * tree, walks it and copies the potential back to out_host (float or double
- * per the context precision), then synchronises the stream.  Host buffers
- * should be pinned for full copy bandwidth.  Same errors as the calls it
- * makes. */
+ * tree, walks it and writes the potential to out_host (float or double per
+ * the context precision), then synchronises the stream.  A pinned out_host
+ * (cudaMallocHost / cudaHostAlloc / cudaHostRegister) is written by the walk
+ * directly through its device address; a pageable one receives a copy from a
+ * device staging buffer (allocated once, kept by the context).  The density
+ * goes through a device staging buffer; pinned, it copies at full bandwidth.
+ * Same errors as the calls it makes. */
 bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
                         const double *box_lo, double box_len, const void *density_host,
                         int density_is_fp64, double theta, double G, void *out_host);

@@ -999,7 +999,20 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
     BH_CUDA(bhg::dev_malloc(&t.d_stage_in, in_bytes));
     t.stage_in_bytes = in_bytes;
   }
-  if (t.stage_out_bytes < out_bytes) {
+  // A pinned (page-locked, mapped) output buffer is written by the walk
+  // itself, through its device address: on GB300 the stores cross the
+  // NVLink chip-to-chip link to the Grace host memory while the walk runs,
+  // instead of a copy after it.  Other output buffers get the staged copy.
+  // (The density is copied in either way: read twice by the build's kernels
+  // across the link, it made the call slower than one copy to HBM.)
+  void *direct = nullptr;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) direct = pa.devicePointer;
+  } else {
+    cudaGetLastError();  // not a pointer CUDA knows: pageable memory
+  }
+  if (!direct && t.stage_out_bytes < out_bytes) {
     release(t.d_stage_out);
     t.stage_out_bytes = 0;
     BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
@@ -1009,10 +1022,11 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
                           ctx->stream));
   st = bh_build(ctx, nblocks, level, ijk, box_lo, box_len, t.d_stage_in, density_is_fp64);
   if (st != BH_OK) return st;
-  st = bh_potential(ctx, theta, G, t.d_stage_out);
+  st = bh_potential(ctx, theta, G, direct ? direct : t.d_stage_out);
   if (st != BH_OK) return st;
-  BH_CUDA(cudaMemcpyAsync(out_host, t.d_stage_out, out_bytes, cudaMemcpyDeviceToHost,
-                          ctx->stream));
+  if (!direct)
+    BH_CUDA(cudaMemcpyAsync(out_host, t.d_stage_out, out_bytes, cudaMemcpyDeviceToHost,
+                            ctx->stream));
   BH_CUDA(cudaStreamSynchronize(ctx->stream));
   return BH_OK;
 }

@@ -210,6 +210,14 @@ def test_deterministic_and_host_path_identical():
     assert np.array_equal(a, b)
     h = _solver().solve_host(mesh.level, mesh.ijk, rho.reshape(-1).copy(), 0.5)
     assert np.array_equal(a, h)
+    # a pinned output buffer: written by the walk through its device address
+    pinned = torch.empty(mesh.ncells, dtype=torch.float32).pin_memory()
+    pinned.fill_(float("nan"))
+    q = _solver()
+    B.bh_solve_host(q._ctx, mesh.level, mesh.ijk, (0.0, 0.0, 0.0), 1.0,
+                    torch.as_tensor(rho.reshape(-1).copy()).pin_memory().numpy(), 0.5, 1.0,
+                    pinned.numpy())
+    assert np.array_equal(a, pinned.numpy())
 
 
 # ----------------------------------------------------- full-size meshes ---
