@@ -371,12 +371,26 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   BH_CUDA(bhg::launch_prestart_scan(s, nb, t.d_count, t.d_prestart, t.d_flags));
   // the top nodes' records and child lists (needed from k_upper_tree on) on
   // the side stream, beside k_blocks, which writes only the blocks' nodes
-  if (!ctx->side) {
+  if (!ctx->side || !ctx->fork || !ctx->join) {  // made once, all three or none
     int lo_prio = 0, hi_prio = 0;
-    BH_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
-    BH_CUDA(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi_prio));
-    BH_CUDA(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
-    BH_CUDA(cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming));
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (join) cudaEventDestroy(join);
+      if (fork) cudaEventDestroy(fork);
+      if (side) cudaStreamDestroy(side);
+    }
+    BH_CUDA(e);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    ctx->side = side;
+    ctx->fork = fork;
+    ctx->join = join;
   }
   BH_CUDA(cudaEventRecord(ctx->fork, s));
   BH_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
