@@ -242,6 +242,27 @@ def test_maclaurin_full_size_sampled(theta):
     assert np.all(np.isfinite(phi)) and np.all(phi < 0)
 
 
+def test_autotuned_walk_at_full_size_keeps_every_bit():
+    """The benchmark's tuning at full size: bh_autotune times every launch
+    shape and, for the longest-first order, walks the tree once recording
+    each group's time; whatever shape and order it keeps, and the
+    longest-first persistent walk pinned directly, give the default walk's
+    potentials bit for bit (monopole at theta 0.24, the plain comparison,
+    and with the quadrupole term at theta 0.75, the headline)."""
+    mesh, rho = _mesh("maclaurin")
+    for quad, theta in ((False, 0.24), (True, 0.75)):
+        ref = _build(B.Solver(quadrupole=quad), mesh, rho)
+        want = ref.potential(theta).cpu().numpy()
+        ref.close()
+        s = _build(B.Solver(quadrupole=quad), mesh, rho)
+        shape = s.autotune(theta)
+        assert shape[3] in (0, 1)
+        assert np.array_equal(s.potential(theta).cpu().numpy(), want), shape
+        s.set_walk_shape(16, 1, 1, 1)
+        assert np.array_equal(s.potential(theta).cpu().numpy(), want)
+        s.close()
+
+
 @pytest.mark.parametrize("theta", [0.72, 0.75])
 def test_against_the_analytic_potentials(theta):
     """The two configurations that state an analytic reference: the 32^3
