@@ -1203,6 +1203,8 @@ def main():
                          "achieved": flops / walk_s / 1e12, "peak": peak / 1e12,
                          "unit": "TFLOP/s", "frac": flops / walk_s / peak, "traffic": traffic,
                          "frac_with_kahan": (flops + 3 * (n_int - n_cell)) / walk_s / peak,
+                         "frac_monopole_count": (FLOP_PER_INTERACTION * n_int
+                                                 + FLOP_PER_TEST * n_test) / walk_s / peak,
                          "kahan_ops": ("3 per node interaction (the compensation of the "
                                        "compensated sum; a bottom node's 8 cell terms are "
                                        "summed plainly and folded once, not counted)"),
