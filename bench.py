@@ -253,9 +253,9 @@ def captured_traffic(workload_name, theta, mode):
     import hashlib
     import re
     profile, files = {
-        "quadrupole": ("walk_pair_quadrupole_theta0.75_maclaurin_2M.md",
+        "quadrupole": ("walk_queue_quadrupole_theta0.75_maclaurin_2M.md",
                        ("bh_walk.cu", "bh_walk_common.cuh")),
-        "monopole": ("walk_pair_monopole_theta0.24_maclaurin_2M.md",
+        "monopole": ("walk_queue_monopole_theta0.24_maclaurin_2M.md",
                      ("bh_walk.cu", "bh_walk_common.cuh")),
         "periodic64": ("walk_periodic_theta0.7_maclaurin_2M.md",
                        ("bh_walk_periodic.cu", "bh_ewald.cuh", "bh_walk_common.cuh")),

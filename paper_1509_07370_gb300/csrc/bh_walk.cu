@@ -105,11 +105,13 @@ __device__ __forceinline__ u64 node_term2(u64 mm, u64 rr, u64 dx2, u64 w0, float
   return mul2(rr, fma2(hq, mul2(r2, r2), mm));
 }
 
-// Loads the quadrupole record of node and forms its shared parts.
-__device__ __forceinline__ void quad_shared(const WalkQuad *qr, float dy, float dz, u64 &w0,
-                                            float &qu, float &qc) {
-  u64 w1, w2, w3;
-  load_quad(qr, w0, w1, w2, w3);
+// The shared parts of a node's quadrupole term from its record (loaded with
+// the node's walk record at the start of the step, so that its latency
+// overlaps the opening test; w0 = {Qxx/2, Qxx/2}, w1 = {Qyy/2, Qzz/2},
+// w2 = {Qxy, Qxz}, w3 = {Qyz, 0}).
+__device__ __forceinline__ void quad_parts(u64 v0, u64 w1, u64 w2, u64 w3, float dy, float dz,
+                                           u64 &w0, float &qu, float &qc) {
+  w0 = v0;
   float hyy, hzz, qxy, qxz, qyz, unused;
   upk(w1, hyy, hzz);
   upk(w2, qxy, qxz);
@@ -238,6 +240,8 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
     // ---- converged: every target is at `node`, an internal node ----
     u64 q0, q1, q2, q3;
     load_rec(rec + node, q0, q1, q2, q3);
+    u64 p0 = 0ull, p1 = 0ull, p2 = 0ull, p3 = 0ull;
+    if (QUAD && !COUNTS) load_quad(qrec + node, p0, p1, p2, p3);
     float s2, skf;
     upk(q3, s2, skf);
     const unsigned skip = __float_as_uint(skf);
@@ -266,7 +270,7 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
     float qu = 0.0f, qc = 0.0f;
     if (__all_sync(kFull, all)) {  // every target accepts the node
       if (!COUNTS) {
-        if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+        if (QUAD) quad_parts(p0, p1, p2, p3, dy, dz, w0, qu, qc);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
           const u64 rr = pk(rsqrt_approx(d2a[k]), rsqrt_approx(d2b[k]));
@@ -278,7 +282,7 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
     }
     const bool any_take = __any_sync(kFull, any);
     if (!COUNTS && any_take) {
-      if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+      if (QUAD) quad_parts(p0, p1, p2, p3, dy, dz, w0, qu, qc);
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         float ra = rsqrt_approx(d2a[k]), rb = rsqrt_approx(d2b[k]);
@@ -310,6 +314,7 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
     node = node + 1;  // some target opened the node
     while (node < end) {
       load_rec(rec + node, q0, q1, q2, q3);
+      if (QUAD && !COUNTS) load_quad(qrec + node, p0, p1, p2, p3);
       upk(q3, s2, skf);
       const unsigned skp = __float_as_uint(skf);
       const float hd = dyz_part(ty, tz, q1, dy, dz);
@@ -334,7 +339,7 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
         }
       }
       if (!COUNTS && __any_sync(kFull, any_tk)) {
-        if (QUAD) quad_shared(qrec + node, dy, dz, w0, qu, qc);
+        if (QUAD) quad_parts(p0, p1, p2, p3, dy, dz, w0, qu, qc);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
           float ra = rsqrt_approx(d2a[k]), rb = rsqrt_approx(d2b[k]);
