@@ -18,10 +18,13 @@
  *     potential and every other array argument are DEVICE pointers on the
  *     context's device, owned by the caller.  The library owns its tree
  *     buffers from bh_build until the next bh_build or bh_destroy.
- *   - Work is issued on the context's CUDA stream.  bh_build returns after
- *     the tree is complete and validated (it synchronises the stream once to
- *     report geometry and density errors).  bh_potential only enqueues: the
- *     output is ready once the stream reaches that point.
+ *   - Work is issued on the context's CUDA stream.  bh_build returns once
+ *     the geometry and the density are validated (it waits once, for the
+ *     build's first kernels, to report their errors); the moments are then
+ *     still being computed on the stream.  bh_potential only enqueues: the
+ *     output is ready once the stream reaches that point.  Device inputs are
+ *     read in stream order: keep them unchanged until the stream has passed
+ *     the call that reads them.
  *   - No exceptions cross this boundary.  Every call returns a bh_status;
  *     bh_last_error() gives a one-line reason for the last failure on that
  *     context.  A context must not be used from two threads at once;
@@ -123,7 +126,8 @@ bh_status bh_create(bh_ctx **out, const bh_options *opt, int device, void *cuda_
  *   box_lo, box_len  HOST double[3] lower corner and the side (> 0) of the box
  *   density          DEVICE array of nblocks*512 values, float (density_is_fp64
  *                    = 0) or double (1); every value finite and >= 0.  Cell
- *                    mass is density * cell volume.  Read only during the call.
+ *                    mass is density * cell volume.  Read on the stream until
+ *                    the build's last kernel, which may run after the return.
  * Errors: BH_ERR_ARG, BH_ERR_GEOMETRY (nothing usable is kept: a later
  * bh_potential returns BH_ERR_STATE), BH_ERR_OOM, BH_ERR_CUDA. */
 bh_status bh_build(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,

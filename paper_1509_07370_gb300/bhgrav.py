@@ -445,8 +445,15 @@ class Solver:
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
 
+    def _keep(self, density):
+        """The build's kernels read the density on the library's stream after
+        the call returns: keep its memory from being reused before that."""
+        if hasattr(density, "record_stream"):
+            density.record_stream(self.stream)
+
     def build(self, level, ijk, density, box_lo=(0.0, 0.0, 0.0), box_len=1.0):
         bh_build(self._ctx, level, ijk, box_lo, box_len, density)
+        self._keep(density)
         self.ncells = 512 * len(level)
         return self
 
@@ -456,11 +463,13 @@ class Solver:
         box_lo = np.zeros((nf, 3)) if box_lo is None else box_lo
         box_len = np.ones(nf) if box_len is None else box_len
         bh_build_batch(self._ctx, nblocks, level, ijk, box_lo, box_len, density)
+        self._keep(density)
         self.ncells = 512 * int(np.sum(nblocks))
         return self
 
     def update_density(self, density):
         bh_update_density(self._ctx, density)
+        self._keep(density)
 
     def sync_status(self):
         bh_sync_status(self._ctx)

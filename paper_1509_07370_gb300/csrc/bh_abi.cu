@@ -217,8 +217,8 @@ bhg::FieldArgs field_args(bhg::Tree &t) {
   return fa;
 }
 
-// Moments of the current geometry from a density (k_blocks + one launch per
-// level above the blocks); stream-ordered, no host synchronisation.
+// Moments of the current geometry from a density (k_blocks, then
+// k_upper_tree); stream-ordered, no host synchronisation.
 bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64,
                           bool mmax_ready = false, cudaEvent_t before_upper = nullptr) {
   bhg::Tree &t = ctx->tree;
@@ -231,7 +231,7 @@ bh_status enqueue_moments(bh_ctx *ctx, const void *density, int density_is_fp64,
   // first kernel found it, then the moments
   if (!mmax_ready) {
     BH_CUDA(cudaMemsetAsync(t.d_mmax, 0, (size_t)t.nfields * sizeof(unsigned long long), s));
-    BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa));
+    BH_CUDA(bhg::launch_mass_max(s, t.nb, t.d_level, density, density_is_fp64, fa, t.d_flags));
   }
   BH_CUDA(bhg::launch_moments(s, t.nb, t.d_blk, t.d_orig, t.d_count, t.d_prestart, density, density_is_fp64, fa, t.n_nodes, t.d_mom, t.d_rec, t.d_aux,
                               t.d_lvl, q64, qrec, t.d_flags, bhg::top_args(t.d_top, t.nb_cap),
@@ -397,11 +397,20 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   BH_CUDA(bhg::launch_top_nodes(ctx->side, nb, t.d_key[0], t.d_blk, t.d_count, t.d_prestart,
                                 n_nodes, t.d_rec, t.d_aux, t.d_lvl, t.d_flags, fa, t.d_orig,
                                 max_level, top));
+  // Every check of the input is done by now (levels, coordinates and density
+  // in k_keys_mass, the tiling in k_tile_and_count, the top-node count in
+  // k_prestart_scan, top indexes in k_top_nodes/k_top_children): the flags go
+  // to the host from the side stream while k_blocks runs, and the host waits
+  // for them alone, so that the walk the caller enqueues next follows the
+  // moments with no gap.  (k_blocks may set bits of its own meanwhile; the
+  // copy then sees them or not, and they are set only on a failed geometry or
+  // density, which the copied bits already report.)
+  BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                          ctx->side));
   BH_CUDA(cudaEventRecord(ctx->join, ctx->side));
   if ((st = enqueue_moments(ctx, density, density_is_fp64, true, ctx->join)) != BH_OK) return st;
   ctx->build_timed = timed && timing_mark(ctx, 1);
-  BH_CUDA(cudaMemcpyAsync(t.h_flags, t.d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  BH_CUDA(cudaStreamSynchronize(s));
+  BH_CUDA(cudaEventSynchronize(ctx->join));
   const unsigned e = t.h_flags[0];
   if (e & (bhg::kErrLevel | bhg::kErrCoord))
     return fail(ctx, BH_ERR_GEOMETRY, "%s: a block coordinate lies outside its level", who);

@@ -971,18 +971,24 @@ __global__ void __launch_bounds__(8 * kUpperBlocks)
 // Largest cell mass m = rho h^3 of each field (FP64, rounded as in k_blocks),
 // as an atomic max on its bits (a non-negative double orders like its bits):
 // the part of caller block b (level lb, field f), by all threads of a CTA.
-// Invalid densities are skipped here and reported by k_blocks.
+// Invalid densities (negative, NaN, infinite) are skipped and flagged here,
+// in the build's first kernel, so that the host can report them before the
+// moments are done (k_blocks flags them too).
 template <typename T>
 __device__ __forceinline__ void block_mass_max(int b, int field, int lb,
                                                const T *__restrict__ density,
                                                const double *__restrict__ Lf,
-                                               unsigned long long *__restrict__ mmax) {
+                                               unsigned long long *__restrict__ mmax,
+                                               unsigned *flags) {
   const T *rho = density + (int64_t)b * kCellsPerBlock;
   T mx = 0;  // the largest density, in its own precision (max is exact)
+  bool bad = false;
   for (int i = threadIdx.x; i < kCellsPerBlock; i += kBlockThreads) {
     const T r = rho[i];
     if (r >= T(0) && !isinf(r)) mx = r > mx ? r : mx;
+    else bad = true;
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kErrDensity);
   for (int o = 16; o > 0; o >>= 1) {
     const T v = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = v > mx ? v : mx;
@@ -1008,11 +1014,11 @@ template <typename T>
 __global__ void __launch_bounds__(kBlockThreads)
     k_mass_max(int nb, const int *__restrict__ level, const T *__restrict__ density,
                const double *__restrict__ Lf, const int *__restrict__ fid,
-               unsigned long long *__restrict__ mmax) {
+               unsigned long long *__restrict__ mmax, unsigned *flags) {
   const int b = blockIdx.x;
   const int lb = level[b];
   if (lb < 0 || lb > kMaxBlockLevel) return;
-  block_mass_max(b, fid[b], lb, density, Lf, mmax);
+  block_mass_max(b, fid[b], lb, density, Lf, mmax, flags);
 }
 
 // The build's first kernel: block keys and the largest cell mass together,
@@ -1029,7 +1035,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   if (threadIdx.x == 0) key_of_block(b, f, level, ijk, key, idx, flags, fstart, fid);
   const int lb = level[b];
   if (lb < 0 || lb > kMaxBlockLevel) return;
-  block_mass_max(b, f, lb, density, Lf, mmax);
+  block_mass_max(b, f, lb, density, Lf, mmax, flags);
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -1089,13 +1095,13 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
 }
 
 cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
-                            int density_is_fp64, const FieldArgs &fa) {
+                            int density_is_fp64, const FieldArgs &fa, unsigned *flags) {
   if (density_is_fp64)
     k_mass_max<double><<<nb, kBlockThreads, 0, s>>>(nb, level, (const double *)density, fa.L,
-                                                     fa.fid, fa.mmax);
+                                                     fa.fid, fa.mmax, flags);
   else
     k_mass_max<float><<<nb, kBlockThreads, 0, s>>>(nb, level, (const float *)density, fa.L,
-                                                    fa.fid, fa.mmax);
+                                                    fa.fid, fa.mmax, flags);
   return cudaGetLastError();
 }
 

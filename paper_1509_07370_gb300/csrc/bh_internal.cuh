@@ -259,8 +259,9 @@ cudaError_t launch_top_nodes(cudaStream_t s, int nb, const unsigned long long *k
                              unsigned *flags, const FieldArgs &fa, const int *orig,
                              int max_level, const TopArgs &top);
 // Largest cell mass of every field alone (a new density on the same tree).
+// Negative or non-finite densities set kErrDensity in flags.
 cudaError_t launch_mass_max(cudaStream_t s, int nb, const int *level, const void *density,
-                            int density_is_fp64, const FieldArgs &fa);
+                            int density_is_fp64, const FieldArgs &fa, unsigned *flags);
 // Every node's moments: cells and bottom nodes (k_blocks), then the rest of
 // the blocks and the top tree (k_upper_tree), two launches.  before_upper:
 // an event the second launch waits for (the top-node lists made on another

@@ -499,6 +499,32 @@ def test_errors_reported():
     assert np.all(np.isfinite(s.potential(0.5).cpu().numpy()))   # still usable
 
 
+def test_build_reports_every_bad_density_before_its_moments():
+    """bh_build returns once its first kernels have checked the input, with
+    the moments still running: a bad value anywhere (the last cell of the
+    last block, either precision, a field of a batch) is still reported by
+    the call itself, and the tree that follows a good build is complete."""
+    import torch
+    mesh, rho = _mesh("eight_blocks")
+    s = _solver()
+    for dt in (torch.float32, torch.float64):
+        for bad_v in (-1e-30, float("inf"), float("-inf"), float("nan")):
+            d = torch.as_tensor(rho.reshape(-1), dtype=dt, device="cuda").clone()
+            d[-1] = bad_v
+            with pytest.raises(B.BHError) as e:
+                s.build(mesh.level, mesh.ijk, d, mesh.box_lo, mesh.box_len)
+            assert e.value.status == B.BH_ERR_ARG, (dt, bad_v)
+        got = _build(s, mesh, rho, dt).potential(0.5).cpu().numpy()    # after the failures
+        want = _build(_solver(), mesh, rho, dt).potential(0.5).cpu().numpy()
+        assert np.array_equal(got, want)
+    two = _cuda(np.concatenate([rho.reshape(-1), rho.reshape(-1)]))
+    two[512 * len(mesh.level) + 3] = float("nan")          # a cell of the second field
+    nb = np.array([len(mesh.level)] * 2, dtype=np.int32)
+    with pytest.raises(B.BHError) as e:
+        s.build_batch(nb, np.concatenate([mesh.level] * 2), np.concatenate([mesh.ijk] * 2), two)
+    assert e.value.status == B.BH_ERR_ARG
+
+
 def test_stats_sizes_timings_and_work_totals():
     """bh_stats: tree sizes equal bh_tree_size, device times with the timing
     option are positive (and -1 without it), the work totals equal the sums
