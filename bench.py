@@ -1132,6 +1132,10 @@ def main():
             host_solver.set_ewald(args.ewald_grid, 3)
         for _ in range(max(1, args.warmup)):
             host_solver.solve_host(mesh.level, mesh.ijk, h_rho, args.theta, 1.0, h_out)
+        # the device arm's launch shape (bh_autotune makes this context's own
+        # group order on the tree the warm-up built; untimed)
+        host_solver.autotune(args.theta)
+        host_solver.set_walk_shape(*shape)
         ts = []
         for _ in range(args.steps):
             flush.zero_()
@@ -1142,7 +1146,8 @@ def main():
         e2e_s = max_over_ranks(float(np.sum(ts)), dev)
         e2e = {"value": job_rate(world, n, args.steps, e2e_s * 1e3), "unit": "cells/s",
                "h2d_bytes_per_step": int(rho32.nbytes + mesh.level.nbytes + mesh.ijk.nbytes),
-               "d2h_bytes_per_step": int(h_out.nbytes)}
+               "d2h_bytes_per_step": int(h_out.nbytes),
+               "walk_shape": list(shape)}
         host_solver.close()
 
     all_cells = None
