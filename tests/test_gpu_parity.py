@@ -220,6 +220,31 @@ def test_deterministic_and_host_path_identical():
     assert np.array_equal(a, pinned.numpy())
 
 
+def test_host_path_reads_pinned_density_once_and_keeps_every_bit():
+    """bh_solve_host with a pinned density (read by the build's first kernel
+    through its device address, which leaves the copy the moment kernels
+    read) and with a pageable one (copied in first): both bit-identical to
+    bh_build + bh_potential on the device, in either density precision, at
+    full size; a bad value in the pinned density is still reported."""
+    mesh, rho = _mesh("maclaurin")
+    for dt, npdt in ((torch.float32, np.float32), (torch.float64, np.float64)):
+        r = rho.reshape(-1).astype(npdt)
+        want = _build(_solver(), mesh, r, dt).potential(0.75).cpu().numpy()
+        s = _solver()
+        out = torch.empty(mesh.ncells, dtype=torch.float32).pin_memory()
+        for dens in (torch.as_tensor(r).pin_memory().numpy(), r.copy()):
+            out.fill_(float("nan"))
+            s.solve_host(mesh.level, mesh.ijk, dens, 0.75, 1.0, out.numpy(),
+                         mesh.box_lo, mesh.box_len)
+            assert np.array_equal(out.numpy(), want), (dt, dens.flags)
+    bad = torch.as_tensor(rho.reshape(-1).astype(np.float32)).pin_memory()
+    bad[mesh.ncells // 2] = float("nan")
+    with pytest.raises(B.BHError) as e:
+        _solver().solve_host(mesh.level, mesh.ijk, bad.numpy(), 0.75, 1.0, None,
+                             mesh.box_lo, mesh.box_len)
+    assert e.value.status == B.BH_ERR_ARG
+
+
 # ----------------------------------------------------- full-size meshes ---
 def _sample(ncells, k, seed):
     rng = np.random.default_rng(seed)
