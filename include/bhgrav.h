@@ -262,9 +262,8 @@ bh_status bh_export_quadrupoles(const bh_ctx *ctx, double *Q);
  * (cudaMallocHost / cudaHostAlloc / cudaHostRegister) is written by the walk
  * directly through its device address; a pageable one receives a copy from a
  * device staging buffer (allocated once, kept by the context).  The density
- * lands in a device staging buffer too: a pinned one is read once through its
- * device address by the build's first kernel, which writes that copy; a
- * pageable one is copied in first.  Same errors as the calls it makes. */
+ * goes through a device staging buffer; pinned, it copies at full bandwidth.
+ * Same errors as the calls it makes. */
 bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const int32_t *ijk,
                         const double *box_lo, double box_len, const void *density_host,
                         int density_is_fp64, double theta, double G, void *out_host);

@@ -285,16 +285,11 @@ __global__ void k_sum_counts(int64_t n, const int32_t *__restrict__ a,
   }
 }
 
-// Tree and moments of nfields meshes (one field = bh_build).  Waits once,
-// for the input checks of the first kernels, to report geometry and density
-// errors; the moments are still running on return.  With `stage` (a device
-// buffer of the density's size), `density` is read once, by the first
-// kernel, which copies it there for the moment kernels (a density in mapped
-// host memory).
+// Tree and moments of nfields meshes (one field = bh_build).  Synchronises
+// once to report geometry and density errors.
 bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
                        const int32_t *ijk, const double *box_lo, const double *box_len,
-                       const void *density, int density_is_fp64, const char *who,
-                       void *stage = nullptr) {
+                       const void *density, int density_is_fp64, const char *who) {
   bhg::Tree &t = ctx->tree;
   t.built = false;
   drop_graph(t);
@@ -369,8 +364,7 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   BH_CUDA(cudaMemcpyAsync(t.d_geo, t.h_geo, g.ijk + 12 * (size_t)nb, cudaMemcpyHostToDevice, s));
   BH_CUDA(cudaEventRecord(t.geo_done, s));
   BH_CUDA(bhg::launch_keys_mass(s, nb, t.d_level, t.d_ijk, t.d_key[0], t.d_idx[0], t.d_flags, fa,
-                                density, density_is_fp64, stage));
-  if (stage) density = stage;  // what the moment kernels read
+                                density, density_is_fp64));
   BH_CUDA(bhg::launch_sort_blocks(s, t.d_key, t.d_idx, t.d_flags, fa));
   BH_CUDA(bhg::launch_tile_and_count(s, nb, t.d_key[0], t.d_idx[0], t.d_level, t.d_ijk,
                                      t.d_count, t.d_blk, t.d_orig, t.d_flags, fa, top, t.d_pos));
@@ -1032,35 +1026,24 @@ bh_status bh_solve_host(bh_ctx *ctx, int nblocks, const int32_t *level, const in
   // itself, through its device address: on GB300 the stores cross the
   // NVLink chip-to-chip link to the Grace host memory while the walk runs,
   // instead of a copy after it.  Other output buffers get the staged copy.
-  // A pinned density is read across the link once, by the build's first
-  // kernel, which leaves a copy in HBM for the moment kernels (reading it
-  // twice across the link made the call slower than one copy to HBM); any
-  // other density is copied in first.
-  auto mapped = [](const void *p) -> void * {
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
-      cudaGetLastError();  // not a pointer CUDA knows: pageable memory
-      return nullptr;
-    }
-    return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
-  };
-  void *direct = mapped(out_host);
-  const void *density_dev = mapped(density_host);
+  // (The density is copied in either way: read twice by the build's kernels
+  // across the link, it made the call slower than one copy to HBM.)
+  void *direct = nullptr;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) direct = pa.devicePointer;
+  } else {
+    cudaGetLastError();  // not a pointer CUDA knows: pageable memory
+  }
   if (!direct && t.stage_out_bytes < out_bytes) {
     release(t.d_stage_out);
     t.stage_out_bytes = 0;
     BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
     t.stage_out_bytes = out_bytes;
   }
-  if (density_dev) {
-    const int32_t nb = nblocks;
-    st = build_fields(ctx, 1, &nb, level, ijk, box_lo, &box_len, density_dev, density_is_fp64,
-                      "bh_solve_host", t.d_stage_in);
-  } else {
-    BH_CUDA(cudaMemcpyAsync(t.d_stage_in, density_host, in_bytes, cudaMemcpyHostToDevice,
-                            ctx->stream));
-    st = bh_build(ctx, nblocks, level, ijk, box_lo, box_len, t.d_stage_in, density_is_fp64);
-  }
+  BH_CUDA(cudaMemcpyAsync(t.d_stage_in, density_host, in_bytes, cudaMemcpyHostToDevice,
+                          ctx->stream));
+  st = bh_build(ctx, nblocks, level, ijk, box_lo, box_len, t.d_stage_in, density_is_fp64);
   if (st != BH_OK) return st;
   st = bh_potential(ctx, theta, G, direct ? direct : t.d_stage_out);
   if (st != BH_OK) return st;

@@ -974,24 +974,17 @@ __global__ void __launch_bounds__(8 * kUpperBlocks)
 // Invalid densities (negative, NaN, infinite) are skipped and flagged here,
 // in the build's first kernel, so that the host can report them before the
 // moments are done (k_blocks flags them too).
-// With `stage`, every value read is also stored there (the density read
-// once from host memory mapped into the device's address space, the moment
-// kernels then reading the copy in HBM).
 template <typename T>
 __device__ __forceinline__ void block_mass_max(int b, int field, int lb,
                                                const T *__restrict__ density,
                                                const double *__restrict__ Lf,
                                                unsigned long long *__restrict__ mmax,
-                                               unsigned *flags, T *__restrict__ stage = nullptr) {
+                                               unsigned *flags) {
   const T *rho = density + (int64_t)b * kCellsPerBlock;
   T mx = 0;  // the largest density, in its own precision (max is exact)
   bool bad = false;
-  static_assert(kCellsPerBlock % kBlockThreads == 0, "whole rounds of the CTA");
-#pragma unroll
-  for (int j = 0; j < kCellsPerBlock / kBlockThreads; ++j) {  // all loads in flight at once
-    const int i = threadIdx.x + j * kBlockThreads;
+  for (int i = threadIdx.x; i < kCellsPerBlock; i += kBlockThreads) {
     const T r = rho[i];
-    if (stage) stage[(int64_t)b * kCellsPerBlock + i] = r;
     if (r >= T(0) && !isinf(r)) mx = r > mx ? r : mx;
     else bad = true;
   }
@@ -1029,21 +1022,20 @@ __global__ void __launch_bounds__(kBlockThreads)
 }
 
 // The build's first kernel: block keys and the largest cell mass together,
-// one CTA per caller block (thread 0 forms the key); with `stage`, the
-// density is also copied there.
+// one CTA per caller block (thread 0 forms the key).
 template <typename T>
 __global__ void __launch_bounds__(kBlockThreads)
     k_keys_mass(int nb, const int *__restrict__ level, const int *__restrict__ ijk,
                 unsigned long long *__restrict__ key, int *__restrict__ idx, unsigned *flags,
                 int nfields, const int *__restrict__ fstart, int *__restrict__ fid,
                 const T *__restrict__ density, const double *__restrict__ Lf,
-                unsigned long long *__restrict__ mmax, T *__restrict__ stage) {
+                unsigned long long *__restrict__ mmax) {
   const int b = blockIdx.x;
   const int f = field_of(b, nfields, fstart);
   if (threadIdx.x == 0) key_of_block(b, f, level, ijk, key, idx, flags, fstart, fid);
   const int lb = level[b];
   if (lb < 0 || lb > kMaxBlockLevel) return;
-  block_mass_max(b, f, lb, density, Lf, mmax, flags, stage);
+  block_mass_max(b, f, lb, density, Lf, mmax, flags);
 }
 
 inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -1052,16 +1044,15 @@ inline int grid_for(int64_t n, int threads) { return (int)((n + threads - 1) / t
 
 cudaError_t launch_keys_mass(cudaStream_t s, int nb, const int *level, const int *ijk,
                              unsigned long long *key, int *idx, unsigned *flags,
-                             const FieldArgs &fa, const void *density, int density_is_fp64,
-                             void *stage) {
+                             const FieldArgs &fa, const void *density, int density_is_fp64) {
   if (density_is_fp64)
     k_keys_mass<double><<<nb, kBlockThreads, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
                                                       fa.fstart, fa.fid, (const double *)density,
-                                                      fa.L, fa.mmax, (double *)stage);
+                                                      fa.L, fa.mmax);
   else
     k_keys_mass<float><<<nb, kBlockThreads, 0, s>>>(nb, level, ijk, key, idx, flags, fa.nfields,
                                                      fa.fstart, fa.fid, (const float *)density,
-                                                     fa.L, fa.mmax, (float *)stage);
+                                                     fa.L, fa.mmax);
   return cudaGetLastError();
 }
 

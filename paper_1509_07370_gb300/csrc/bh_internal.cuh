@@ -239,13 +239,10 @@ __host__ __device__ inline double pow2i(int e) {
 // ---- build kernels (bh_build.cu) -------------------------------------------
 // Every launcher returns the cudaError_t of its launch.
 // Block keys (caller order, fid too) and the largest cell mass of every field
-// (atomic max on fa.mmax, which the caller zeroes first): one launch.  Also
-// checks the density (kErrDensity) and, if stage is not null, copies it
-// there (nb * 512 values of the density's type).
+// (atomic max on fa.mmax, which the caller zeroes first): one launch.
 cudaError_t launch_keys_mass(cudaStream_t s, int nb, const int *level, const int *ijk,
                              unsigned long long *key, int *idx, unsigned *flags,
-                             const FieldArgs &fa, const void *density, int density_is_fp64,
-                             void *stage = nullptr);
+                             const FieldArgs &fa, const void *density, int density_is_fp64);
 cudaError_t launch_sort_blocks(cudaStream_t s, unsigned long long *key[2], int *idx[2],
                                unsigned *flags, const FieldArgs &fa);
 cudaError_t launch_tile_and_count(cudaStream_t s, int nb, const unsigned long long *key,

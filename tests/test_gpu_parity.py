@@ -220,12 +220,11 @@ def test_deterministic_and_host_path_identical():
     assert np.array_equal(a, pinned.numpy())
 
 
-def test_host_path_reads_pinned_density_once_and_keeps_every_bit():
-    """bh_solve_host with a pinned density (read by the build's first kernel
-    through its device address, which leaves the copy the moment kernels
-    read) and with a pageable one (copied in first): both bit-identical to
-    bh_build + bh_potential on the device, in either density precision, at
-    full size; a bad value in the pinned density is still reported."""
+def test_host_path_keeps_every_bit_at_full_size():
+    """bh_solve_host with a pinned and with a pageable density, into a pinned
+    output (written by the walk through its device address): bit-identical
+    to bh_build + bh_potential on the device, in either density precision,
+    at full size; a bad value in the density is still reported."""
     mesh, rho = _mesh("maclaurin")
     for dt, npdt in ((torch.float32, np.float32), (torch.float64, np.float64)):
         r = rho.reshape(-1).astype(npdt)
