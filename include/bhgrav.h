@@ -186,10 +186,11 @@ bh_status bh_sync_status(bh_ctx *ctx);
  * plain grid of one warp per group or a persistent grid (as many CTAs as the
  * GPU holds at once) whose warps take 1, 2 or 4 groups at a time from a work
  * counter; and the groups in their own (Morton) order or longest walk first
- * (the periodic walk: CTA width only) -- each twice, then the four fastest
- * five times more -- and keeps the fastest for later walks.  For the
- * longest-first order it first walks the tree once at this theta on the
- * persistent grid, recording the SM clock cycles of every group's walk, and
+ * (the periodic walk: CTA width and order, one pair per lane, plain grid) --
+ * each twice, then the four fastest five times more -- and keeps the fastest
+ * for later walks.  For the longest-first order it first walks the tree once
+ * at this theta (the persistent grid; the periodic walk on its plain grid),
+ * recording the SM clock cycles of every group's walk, and
  * sorts the groups by them (on the host); that order is kept with the
  * context, like the shape, and used while the tree has the same number of
  * groups (a permutation of the groups: it can only change the speed).  All shapes
@@ -207,8 +208,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape);
  * groups' own order); 0 for the first two means the default.  Potentials do
  * not depend on the shape (bit for bit).  Drops a captured bh_solve_graph
  * graph.  BH_ERR_ARG for values out of range (the periodic walk: one pair,
- * plain grid, own order); BH_ERR_STATE for longest_first = 1 without an
- * order. */
+ * plain grid); BH_ERR_STATE for longest_first = 1 without an order. */
 bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
                             int groups_per_take, int longest_first);
 

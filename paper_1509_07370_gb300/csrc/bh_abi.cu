@@ -482,10 +482,13 @@ static cudaError_t enqueue_walk(bh_ctx *ctx, cudaStream_t s, double G, void *out
                                 int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
                                 bhg::WalkShape shape) {
   bhg::Tree &t = ctx->tree;
-  if (ctx->opt.periodic)
+  if (ctx->opt.periodic) {  // one pair per lane, a plain grid, optionally longest first
+    const int64_t groups = (int64_t)t.nb * 8;
+    const unsigned *order = shape.longest && t.order_n[0] == groups ? t.d_order[0] : nullptr;
     return bhg::launch_walk_periodic(s, ctx->opt, t.nb, t.d_rec, t.d_blk, t.d_orig,
                                      field_args(t), ctx->d_ewald, ctx->ewald_n, G, out, n_int,
-                                     n_test, n_leaf, shape.warps);
+                                     n_test, n_leaf, shape.warps, order, shape.cycles);
+  }
   if (!n_int && ctx->opt.learned == 2) return bhg::launch_walk_learned_tc(s, ctx, G, out);
   if (!n_int && ctx->opt.learned) return bhg::launch_walk_learned(s, ctx, G, out);
   shape.counter = t.d_flags + 4;  // the work counter of the persistent walk
@@ -786,7 +789,8 @@ bh_status bh_export_quadrupoles(const bh_ctx *cctx, double *Q) {
 
 // The walk order of the groups for one and for two target pairs per lane,
 // longest walk first: one walk of the tree at the prepared theta on the
-// persistent grid (4-warp CTAs, one group per take) records the SM clock
+// persistent grid (4-warp CTAs, one group per take; the periodic walk: its
+// plain grid of 4-warp CTAs, one pair per lane) records the SM clock
 // cycles of each group's walk, under the load of a whole launch; the groups
 // are sorted by them on the host (stable, so equal times keep their Morton
 // order) and the order goes up.  The persistent walk then starts the long
@@ -847,7 +851,8 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
   bhg::Tree &t = ctx->tree;
   const bool tunable = ctx->opt.precision == BH_PREC_F32 &&
                        ctx->opt.criterion == BH_CRIT_PER_CELL && !ctx->opt.learned;
-  // the periodic walk has one target pair per lane; only its CTA width is tuned
+  // the periodic walk has one target pair per lane and a plain grid: its CTA
+  // width and the octants' order are tuned
   const int npairs = ctx->opt.periodic ? 1 : 2;
   if (tunable) {
     const int64_t out_bytes = (int64_t)t.nb * bhg::kCellsPerBlock * sizeof(float);
@@ -857,8 +862,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
       BH_CUDA(bhg::dev_malloc(&t.d_stage_out, out_bytes));
       t.stage_out_bytes = out_bytes;
     }
-    const bool ordered = !ctx->opt.periodic;
-    if (ordered && (st = make_walk_order(ctx, npairs)) != BH_OK) return st;
+    if ((st = make_walk_order(ctx, npairs)) != BH_OK) return st;
     struct Events {  // released on every return
       cudaEvent_t e[2] = {nullptr, nullptr};
       ~Events() {
@@ -873,7 +877,7 @@ bh_status bh_autotune(bh_ctx *ctx, double theta, int *shape) {
     const int nticket = ctx->opt.periodic ? 1 : 4;
     std::vector<bhg::WalkShape> shapes;
     for (int np = 1; np <= npairs; ++np)
-      for (int ti = 0; ti < nticket * 4 * (ordered ? 2 : 1); ++ti) {
+      for (int ti = 0; ti < nticket * 4 * 2; ++ti) {  // CTA width x schedule x order
         bhg::WalkShape sh;
         sh.warps = cand[ti % 4];
         sh.pairs = np;
@@ -932,9 +936,9 @@ bh_status bh_set_walk_shape(bh_ctx *ctx, int warps_per_cta, int pairs_per_lane,
       (longest_first != 0 && longest_first != 1))
     return fail(ctx, BH_ERR_ARG,
                 "bh_set_walk_shape: warps 0..16, pairs 0..2, groups 0..64, longest_first 0/1");
-  if (ctx->opt.periodic && (pairs_per_lane > 1 || groups_per_take > 0 || longest_first))
-    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: the periodic walk has one pair per lane, "
-                                 "a plain grid and the groups' own order");
+  if (ctx->opt.periodic && (pairs_per_lane > 1 || groups_per_take > 0))
+    return fail(ctx, BH_ERR_ARG, "bh_set_walk_shape: the periodic walk has one pair per lane "
+                                 "and a plain grid");
   const int np = pairs_per_lane > 0 ? pairs_per_lane : 1;
   if (longest_first && ctx->tree.order_n[np - 1] == 0)
     return fail(ctx, BH_ERR_STATE, "bh_set_walk_shape: no walk order (run bh_autotune first)");

@@ -389,12 +389,15 @@ cudaError_t launch_ewald_table(cudaStream_t s, int n, int N, double *scratch,
 cudaError_t launch_ewald_eval(cudaStream_t s, int64_t npts, const float *r,
                               const unsigned char *tab, int n, float *out);
 // The binary32 per-cell walk with periodic boundaries; counts as launch_walk.
+// wpc: warps per CTA (0 = default); order: the octants' walk order or null;
+// cycles (potential only, else null): each octant's walk time in SM cycles.
 cudaError_t launch_walk_periodic(cudaStream_t s, const bh_options &opt, int nb,
                                  const WalkRec *rec, const int4 *blk, const int *orig,
                                  const FieldArgs &fa, const unsigned char *tab, int n,
                                  double G,
                                  void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
-                                 int wpc);
+                                 int wpc, const unsigned *order = nullptr,
+                                 unsigned long long *cycles = nullptr);
 
 }  // namespace bhg
 

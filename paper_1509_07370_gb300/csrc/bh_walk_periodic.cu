@@ -192,9 +192,15 @@ __device__ __forceinline__ void walk_octant_periodic(
   }
 }
 
+// One warp per octant: octant order[warp] when an order is given (the
+// octants sorted by the time of their walks, longest first, so that the
+// CTAs, issued in index order, start with the long walks and each holds
+// octants of about equal length).  With `cycles`, lane 0 stores the SM clock
+// cycles its octant's walk took.
 template <bool KAHAN, bool COUNTS>
 __global__ void __launch_bounds__(kPMaxThreads)
-    k_walk_periodic(unsigned nunits, const WalkRec *__restrict__ rec,
+    k_walk_periodic(unsigned nunits, const unsigned *__restrict__ order,
+                    unsigned long long *__restrict__ cycles, const WalkRec *__restrict__ rec,
                     const int4 *__restrict__ blk, const int *__restrict__ orig,
                     const int4 *__restrict__ fld, const double *__restrict__ invL,
                     const unsigned long long *__restrict__ mmax, const unsigned char *__restrict__ tab,
@@ -203,20 +209,24 @@ __global__ void __launch_bounds__(kPMaxThreads)
   const int lane = threadIdx.x & 31;
   const unsigned warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (warp >= nunits) return;  // whole warps only
-  walk_octant_periodic<KAHAN, COUNTS>(warp, lane, rec, blk, orig, fld, invL, mmax, tab, n, G,
+  const unsigned u = order ? order[warp] : warp;
+  const long long t0 = cycles ? clock64() : 0;
+  walk_octant_periodic<KAHAN, COUNTS>(u, lane, rec, blk, orig, fld, invL, mmax, tab, n, G,
                                       out, n_int, n_test, n_leaf);
+  if (cycles && lane == 0) cycles[u] = (unsigned long long)(clock64() - t0);
 }
 
 template <bool KAHAN, bool COUNTS>
 cudaError_t go_periodic(cudaStream_t s, int nb, const WalkRec *rec, const int4 *blk,
                         const int *orig, const FieldArgs &fa, const unsigned char *tab, int n, double G,
-                        void *out, int32_t *ni, int32_t *nt, int32_t *nl, int wpc) {
+                        void *out, int32_t *ni, int32_t *nt, int32_t *nl, int wpc,
+                        const unsigned *order, unsigned long long *cycles) {
   const unsigned nunits = (unsigned)nb * 8u;
   const int w = wpc > 0 ? wpc : kPWarpsPerCta;
   const int grid = (int)((nunits + w - 1) / w);
-  k_walk_periodic<KAHAN, COUNTS><<<grid, 32 * w, 0, s>>>(nunits, rec, blk, orig, fa.fld, fa.invL,
-                                                         fa.mmax, tab, n, G, (float *)out, ni, nt,
-                                                         nl);
+  k_walk_periodic<KAHAN, COUNTS><<<grid, 32 * w, 0, s>>>(nunits, order, cycles, rec, blk, orig,
+                                                         fa.fld, fa.invL, fa.mmax, tab, n, G,
+                                                         (float *)out, ni, nt, nl);
   return cudaGetLastError();
 }
 
@@ -226,14 +236,14 @@ cudaError_t launch_walk_periodic(cudaStream_t s, const bh_options &opt, int nb,
                                  const WalkRec *rec, const int4 *blk, const int *orig,
                                  const FieldArgs &fa, const unsigned char *tab, int n, double G,
                                  void *out, int32_t *n_int, int32_t *n_test, int32_t *n_leaf,
-                                 int wpc) {
+                                 int wpc, const unsigned *order, unsigned long long *cycles) {
   if (n_int)
     return go_periodic<false, true>(s, nb, rec, blk, orig, fa, tab, n, G, out, n_int, n_test,
-                                    n_leaf, wpc);
+                                    n_leaf, wpc, order, nullptr);
   return opt.kahan ? go_periodic<true, false>(s, nb, rec, blk, orig, fa, tab, n, G, out, nullptr,
-                                              nullptr, nullptr, wpc)
+                                              nullptr, nullptr, wpc, order, cycles)
                    : go_periodic<false, false>(s, nb, rec, blk, orig, fa, tab, n, G, out,
-                                               nullptr, nullptr, nullptr, wpc);
+                                               nullptr, nullptr, nullptr, wpc, order, cycles);
 }
 
 }  // namespace bhg

@@ -203,7 +203,11 @@ def test_walk_shape_arguments_checked():
         s.set_walk_shape(4, 1, 1, 1)
     assert e.value.status == B.BH_ERR_STATE
     p = B.Solver(periodic=True)
-    for bad in [(4, 2, 0), (4, 1, 1), (4, 1, 0, 1)]:
-        with pytest.raises(B.BHError):
+    for bad in [(4, 2, 0), (4, 1, 1)]:
+        with pytest.raises(B.BHError) as e:
             p.set_walk_shape(*bad)
+        assert e.value.status == B.BH_ERR_ARG
+    with pytest.raises(B.BHError) as e:                        # no order before bh_autotune
+        p.set_walk_shape(4, 1, 0, 1)
+    assert e.value.status == B.BH_ERR_STATE
     p.set_walk_shape(16, 1, 0)

@@ -150,6 +150,26 @@ def test_full_size_sampled_against_oracle():
     assert np.all(np.isfinite(phi))
 
 
+def test_autotuned_order_keeps_every_bit():
+    """bh_autotune times the periodic walk once per octant and may run the
+    octants longest first: every CTA width, in either order, gives the
+    potentials and counts of the octants' own order, bit for bit, at full
+    size."""
+    w = mg.maclaurin()
+    s = _solver(w.mesh, w.density)
+    want = s.potential(0.7).cpu().numpy()
+    wi, wt = (x.cpu().numpy() for x in s.walk_counts(0.7))
+    shape = s.autotune(0.7)
+    assert shape[1:3] == (1, 0) and shape[3] in (0, 1), shape
+    for warps in (2, 4, 8, 16):
+        for longest in (0, 1):
+            s.set_walk_shape(warps, 1, 0, longest)
+            assert np.array_equal(s.potential(0.7).cpu().numpy(), want), (warps, longest)
+    s.set_walk_shape(4, 1, 0, 1)
+    gi, gt = (x.cpu().numpy() for x in s.walk_counts(0.7))
+    assert np.array_equal(gi, wi) and np.array_equal(gt, wt)
+
+
 def test_zero_field_and_one_block():
     """Edge cases: an all-zero density gives exactly zero (every term carries
     its mass), and a mesh of one block (the whole box one 8^3 block, every
