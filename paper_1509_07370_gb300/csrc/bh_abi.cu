@@ -285,8 +285,9 @@ __global__ void k_sum_counts(int64_t n, const int32_t *__restrict__ a,
   }
 }
 
-// Tree and moments of nfields meshes (one field = bh_build).  Synchronises
-// once to report geometry and density errors.
+// Tree and moments of nfields meshes (one field = bh_build).  Waits once,
+// for the input checks of the first kernels, to report geometry and density
+// errors; the moments are still running on the stream when it returns.
 bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const int32_t *level,
                        const int32_t *ijk, const double *box_lo, const double *box_len,
                        const void *density, int density_is_fp64, const char *who) {
@@ -348,7 +349,8 @@ bh_status build_fields(bh_ctx *ctx, int nfields, const int32_t *nblocks, const i
   const bhg::FieldArgs fa = field_args(t);
   const bhg::TopArgs top = bhg::top_args(t.d_top, t.nb_cap);
   // the host geometry, with zeroed largest masses, into the pinned mirror and
-  // up in one copy (the last build's copy ended at its synchronisation)
+  // up in one copy (the last build's copy ended before its wait on the
+  // flags returned)
   const GeoLayout g = geo_layout(t.nf_cap, t.geo_nb_cap);
   if (t.geo_done) BH_CUDA(cudaEventSynchronize(t.geo_done));  // a copy left by a failed build
   else BH_CUDA(cudaEventCreateWithFlags(&t.geo_done, cudaEventDisableTiming));
