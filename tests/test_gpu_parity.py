@@ -371,6 +371,24 @@ def test_cloud_core_full_size_sampled():
     assert np.all(np.isfinite(phi)) and np.all(phi < 0)
 
 
+def test_cloud_core_quadrupole_autotuned_full_size_sampled():
+    """The 16.3M-cell cloud core with quadrupole nodes at the headline's
+    theta, in the launch shape and group order bh_autotune picks for it:
+    decisions bit-exact and potentials within 1e-5 of the oracle's walk on
+    sampled cells."""
+    mesh, rho = _mesh("cloud_core")
+    s = _build(B.Solver(quadrupole=True), mesh, rho.astype(np.float32), torch.float32)
+    s.autotune(0.75)
+    phi = s.potential(0.75).cpu().numpy()
+    ni, nt = (x.cpu().numpy() for x in s.walk_counts(0.75))
+    tg = _sample(mesh.ncells, 1500, seed=75)
+    t = _oracle(mesh, rho.astype(np.float32).astype(np.float64))
+    ref, oi, ot = t.walk(0.75, targets=tg, quad=True)
+    assert _rel(phi[tg], ref).max() <= F32_TOL
+    assert np.array_equal(ni[tg], oi) and np.array_equal(nt[tg], ot)
+    assert np.all(np.isfinite(phi)) and np.all(phi < 0)
+
+
 # ----------------------------------------------------- quadrupole term ---
 @pytest.mark.parametrize("name", ["refined_twice", "c1", "maclaurin_small"])
 @pytest.mark.parametrize("prec,tol", [(B.BH_PREC_F64, 1e-12), (B.BH_PREC_F32, 1e-5)])
