@@ -40,6 +40,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# the batched arm's 64 fields (meshgen.batch_fields), as its walk profile names them
+BATCH_WORKLOAD = "batched64_16-128_seeds5000-5063"
 sys.path.insert(0, ROOT)
 
 FP32_LANES_PER_SM = 128
@@ -259,6 +261,8 @@ def captured_traffic(workload_name, theta, mode):
                      ("bh_walk.cu", "bh_walk_common.cuh")),
         "periodic64": ("walk_periodic_theta0.7_maclaurin_2M.md",
                        ("bh_walk_periodic.cu", "bh_ewald.cuh", "bh_walk_common.cuh")),
+        "batched_monopole": ("walk_queue_batched64_theta0.5.md",
+                             ("bh_walk.cu", "bh_walk_common.cuh")),
     }.get(mode, (None, None))
     if profile is None:
         return None
@@ -701,7 +705,8 @@ def batched_arm(args):
     roofline = {"bound": "alu", "kernel": "bh_potential walk of all 64 fields (one launch)",
                 "walk_ms": walk_ms, "achieved": flops / (walk_ms * 1e-3) / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": flops / (walk_ms * 1e-3) / peak,
-                "traffic": None, "ops": "8 per interaction, 7 per test (monopole)",
+                "traffic": captured_traffic(BATCH_WORKLOAD, theta, "batched_monopole"),
+                "ops": "8 per interaction, 7 per test (monopole)",
                 "interactions_per_cell": n_int / n, "tests_per_cell": n_test / n}
     cpu = None
     if not args.no_cpu_baseline:  # the oracle on the largest field of the batch

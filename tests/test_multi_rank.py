@@ -79,5 +79,7 @@ def test_committed_walk_profiles_match_the_sources():
     assert bench.captured_traffic(w, 0.7, "periodic64") is not None
     assert bench.captured_traffic(w, 0.7, "quadrupole") is None
     assert bench.captured_traffic(w, 0.24, "monopole") is not None
+    assert bench.captured_traffic(bench.BATCH_WORKLOAD, 0.5, "batched_monopole") is not None
+    assert bench.captured_traffic(bench.BATCH_WORKLOAD, 0.7, "batched_monopole") is None
     assert bench.captured_traffic(w, 0.72, "monopole") is None
     assert bench.captured_traffic("cloud_core", 0.72, "quadrupole") is None
