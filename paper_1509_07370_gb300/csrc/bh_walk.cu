@@ -122,8 +122,9 @@ __device__ __forceinline__ void quad_parts(u64 v0, u64 w1, u64 w2, u64 w3, float
 }
 
 // The 8 cells of a bottom node (node + 1 .. node + 8) for the targets that
-// opened it (bit 2k of `open` for target a of pair k, bit 2k + 1 for target
-// b): every cell but the target's own (d2 > 0).
+// opened it (oa[k] for target a of pair k, ob[k] for target b; kept as
+// predicates, not packed into a bit mask, which took a few more instructions
+// a step): every cell but the target's own (d2 > 0).
 // Cells 2j and 2j + 1 are x-neighbours with the same y and z, so they share
 // dy, dz and h too.  The 8 positive cell terms are summed plainly (a
 // relative error of at most 7 units in the last place of their sum) and the
@@ -132,7 +133,8 @@ __device__ __forceinline__ void quad_parts(u64 v0, u64 w1, u64 w2, u64 w3, float
 // factor on the mass instead of a compare and select per cell, took 8 more
 // registers and made the walk slower.)
 template <int NP, bool KAHAN, bool COUNTS>
-__device__ __forceinline__ void bottom_cells(unsigned node, unsigned open,
+__device__ __forceinline__ void bottom_cells(unsigned node, const bool (&oa)[NP],
+                                             const bool (&ob)[NP],
                                              const WalkRec *__restrict__ rec, float ty,
                                              float tz, Lanes<NP> &L) {
   u64 part[NP];
@@ -153,8 +155,8 @@ __device__ __forceinline__ void bottom_cells(unsigned node, unsigned open,
         const u64 dx2 = sub2(L.tx2[k], px);
         float e2a, e2b;
         upk(fma2(dx2, dx2, pk(h, h)), e2a, e2b);
-        const bool la = ((open >> (2 * k)) & 1u) && e2a > 0.0f;
-        const bool lb = ((open >> (2 * k + 1)) & 1u) && e2b > 0.0f;
+        const bool la = oa[k] && e2a > 0.0f;
+        const bool lb = ob[k] && e2b > 0.0f;
         if (COUNTS) {
           L.ni[2 * k] += la;
           L.ni[2 * k + 1] += lb;
@@ -293,10 +295,13 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
       }
     }
     if (skip == node + 9u) {  // bottom node: the openers meet its cells; all go on at skip
-      unsigned open = 0u;
+      bool oa[NP], ob[NP];
 #pragma unroll
-      for (int k = 0; k < NP; ++k) open |= (ta[k] ? 0u : 1u << (2 * k)) | (tb[k] ? 0u : 2u << (2 * k));
-      bottom_cells<NP, KAHAN, COUNTS>(node, open, rec, ty, tz, L);
+      for (int k = 0; k < NP; ++k) {
+        oa[k] = !ta[k];
+        ob[k] = !tb[k];
+      }
+      bottom_cells<NP, KAHAN, COUNTS>(node, oa, ob, rec, ty, tz, L);
       node = skip;
       continue;
     }
@@ -319,8 +324,8 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
       const unsigned skp = __float_as_uint(skf);
       const float hd = dyz_part(ty, tz, q1, dy, dz);
       bool ma_[NP], mb_[NP];
-      unsigned open = 0u;
-      bool any_tk = false;
+      bool oa[NP], ob[NP];
+      bool any_tk = false, any_op = false;
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
         dx2[k] = sub2(L.tx2[k], q0);
@@ -329,7 +334,9 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
         mb_[k] = L.next_b[k] <= node;
         ta[k] = ma_[k] && d2a[k] > s2;
         tb[k] = mb_[k] && d2b[k] > s2;
-        open |= (ma_[k] && !ta[k] ? 1u << (2 * k) : 0u) | (mb_[k] && !tb[k] ? 2u << (2 * k) : 0u);
+        oa[k] = ma_[k] && !ta[k];
+        ob[k] = mb_[k] && !tb[k];
+        any_op = any_op || oa[k] || ob[k];
         any_tk = any_tk || ta[k] || tb[k];
         if (COUNTS) {  // internal: cells are only reached through bottom nodes
           L.ni[2 * k] += ta[k];
@@ -349,9 +356,9 @@ __device__ __forceinline__ void walk_group(unsigned u, int lane, const WalkRec *
                              node_term2<QUAD>(q2, pk(ra, rb), dx2[k], w0, qu, qc));
         }
       }
-      const bool opened = __any_sync(kFull, open != 0u);
+      const bool opened = __any_sync(kFull, any_op);
       if (skp == node + 9u) {  // bottom node: all go on at skip
-        if (opened) bottom_cells<NP, KAHAN, COUNTS>(node, open, rec, ty, tz, L);
+        if (opened) bottom_cells<NP, KAHAN, COUNTS>(node, oa, ob, rec, ty, tz, L);
         node = skp;
       } else if (opened) {  // takers of a node others open move ahead of the warp
 #pragma unroll
